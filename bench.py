@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Benchmark of the FSPB D_ij path: voxel-beamlet pairs/s and 9-field latency.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload prostate_256|slabs_128|water_32]
+
+One step = the whole path (beamlet set-up, Siddon depth tables, VOI
+enumeration, FSPB evaluation, threshold + CSR compaction) for the 9-field
+synthetic prostate plan (256x256x100 voxels at 2x2x2.5 mm, 9 fields of 16x16
+beamlets of 5 mm), inputs resident in HBM.  K steps are timed with CUDA events
+on the launching stream; a 256 MB buffer is written between steps so every
+step starts with a cold L2.  Under torchrun each rank computes its own plan
+on its own GPU (independent replicas, no data-path collective); the timing is
+the max over ranks.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(the only reference this method has) on a bounded row sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP32 operations of one voxel-beamlet pair as the model defines it (FMA = 2):
+# geometry 20, depth 7, beam-model table 15, three erf-pair terms 51 + 12 erf
+# evaluations x 20, inverse square and product 4.
+F_PAIR = 337
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="prostate_256")
+    p.add_argument("--cpu-sample-stride", type=int, default=4)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(w, stride):
+    """Oracle pairs/s on every `stride`-th row of the workload (all host cores)."""
+    import numpy as np
+    from oracle import oracle as O
+    rows = np.arange(0, w.nrows, stride, dtype=np.int64)
+    t = time.perf_counter()
+    r = O.compute_workload(w, rows=rows)
+    dt = time.perf_counter() - t
+    return {"value": r.pairs / dt, "unit": "pairs/s", "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{rows.size} of {w.nrows} rows (every {stride}th), {r.pairs} pairs, {dt:.2f} s",
+            "seconds": dt, "pairs": int(r.pairs)}
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1].split()[0]))
+                mx.append(float(r[2].split()[0]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id(props, index):
+    """nvidia-smi --id for this CUDA device: its UUID when torch exposes it."""
+    u = getattr(props, "uuid", None)
+    if u:
+        u = str(u)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis:
+        return vis.split(",")[index]
+    return str(index)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_0908_4417_gb300 import phantoms as P
+    from oracle import oracle as O
+    O.build()
+    w = P.get(args.workload)
+    vals = []
+    for _ in range(max(1, args.warmup // 3)):
+        oracle_sample(w, args.cpu_sample_stride * 4)
+    tot_pairs, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        s = oracle_sample(w, args.cpu_sample_stride * 4)
+        tot_pairs += s["pairs"]
+        tot_s += s["seconds"]
+        vals.append(s)
+    v = tot_pairs / tot_s
+    out = {"impl": "reference", "metric": "voxel-beamlet pairs/s", "value": v, "unit": "pairs/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "rows": w.nrows, "fields": len(w.beams), "grid": list(w.grid.shape[::-1])},
+           "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": vals[0]["cores"], "kind": "oracle",
+                            "sample": vals[0]["sample"] + f" per step, {args.steps} steps"},
+           "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_0908_4417_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_0908_4417_gb300 import dsc, phantoms as P
+    dsc.lib()
+    w = P.get(args.workload)
+    stream = torch.cuda.Stream(dev)
+    sp = stream.cuda_stream
+
+    # cpu baseline first (host cores, before the timed GPU work), rank 0 at N=1 only
+    cpu = None
+    if rank == 0 and world == 1:
+        from oracle import oracle as O
+        O.build()
+        cpu = oracle_sample(w, args.cpu_sample_stride)
+
+    g = dsc.dsc_create_geometry(w.grid, w.density, False, w.model, sp)
+    for b in w.beams:
+        dsc.dsc_add_beam(g, b)
+    timing = dsc.compute_opts(w.tau, w.value_dtype, w.h_frac, dsc.DSC_FLAG_TIMING)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            r = dsc.dsc_compute_dij(g, timing, sp)
+            dsc.dsc_result_wait(r)
+            v = dsc.dsc_get_csr(r, False)
+            pairs, nnz, nrows, nbeams = int(v.pairs), int(v.nnz), int(v.nrows), int(v.nbeams)
+            dsc.dsc_release_result(r)
+        # ---- timed region: K steps, device time ----
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = Clocks(gpu_id(props, local if world > 1 else 0))
+        n0 = dsc.dsc_launch_count()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        results = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            evs[k][0].record(stream)
+            results.append(dsc.dsc_compute_dij(g, timing, sp))
+            evs[k][1].record(stream)
+        stream.synchronize()
+        launches = dsc.dsc_launch_count() - n0
+        clocks = clk.stop()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        stages = [dsc.dsc_get_stage_times(r) for r in results]
+        for r in results:
+            dsc.dsc_release_result(r)
+        total_s = sum(step_ms) / 1e3
+        if world > 1:
+            t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_s = float(t.item())
+
+        # ---- end to end through the C ABI with pinned host buffers ----
+        host_rho = torch.from_numpy(np.ascontiguousarray(w.density)).pin_memory()
+        vsize = 2 if w.value_dtype == dsc.DSC_VALUE_BF16 else 4
+        h_rp = torch.empty(nrows + 1, dtype=torch.int64).pin_memory()
+        h_col = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
+        h_val = torch.empty(max(nnz, 1) * vsize, dtype=torch.uint8).pin_memory()
+        h_sc = torch.empty(max(nbeams, 1), dtype=torch.float32).pin_memory()
+        plain = dsc.compute_opts(w.tau, w.value_dtype, w.h_frac, 0)
+        e2e_steps = max(3, args.steps // 2)
+        for k in range(e2e_steps + 2):
+            if k == 2:
+                stream.synchronize()
+                t0 = time.perf_counter()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            dsc.dsc_upload_density(g, host_rho.data_ptr(), False, sp)
+            r = dsc.dsc_compute_dij(g, plain, sp)
+            dsc.dsc_copy_csr_to_host(r, h_rp.data_ptr(), h_col.data_ptr(), h_val.data_ptr(), h_sc.data_ptr(), sp)
+            dsc.dsc_release_result(r)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e1.record(stream)
+        stream.synchronize()
+        e2e_s = e0.elapsed_time(e1) / 1e3
+        wall_s = time.perf_counter() - t0
+
+    dsc.dsc_destroy_geometry(g)
+    if rank != 0:
+        return
+    ms = 1e3 * total_s / args.steps
+    value = world * pairs * args.steps / total_s
+    eval_ms = statistics.mean(s["eval"] for s in stages)
+    achieved = F_PAIR * pairs / (eval_ms / 1e3) / 1e12
+    peak_mhz = 2070.0
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak_mhz = float(mp.get("sm_max_mhz", peak_mhz))
+    except (OSError, ValueError):
+        pass
+    peak = 2 * FP32_LANES_PER_SM * props.multi_processor_count * peak_mhz * 1e6 / 1e12
+    stage_ms = {k: round(statistics.mean(s[k] for s in stages), 4) for k in stages[0]}
+    h2d = int(host_rho.numel() * 4)
+    d2h = int((nrows + 1) * 8 + nnz * 4 + nnz * vsize + nbeams * 4)
+    out = {
+        "metric": "voxel-beamlet pairs/s",
+        "value": value,
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "grid": [w.grid.nx, w.grid.ny, w.grid.nz],
+                   "spacing_mm": [w.grid.dx, w.grid.dy, w.grid.dz], "fields": len(w.beams), "rows": nrows,
+                   "pairs_per_step": pairs, "nnz_per_step": nnz, "value_dtype": "f32" if vsize == 4 else "bf16",
+                   "rel_threshold": w.tau, "l2": "flushed between steps (256 MB write)",
+                   "latency_ms_9field": ms, "stage_ms": stage_ms},
+        "e2e": {"value": world * pairs * e2e_steps / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps,
+                "host_wall_ms_per_step": 1e3 * wall_s / e2e_steps},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_eval",
+                     "flop_per_pair": F_PAIR, "eval_ms": eval_ms,
+                     "peak_basis": f"FP32 FMA 2x{FP32_LANES_PER_SM} lanes x {props.multi_processor_count} SMs "
+                                   f"x {peak_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"},
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * dsc.h -- C ABI of libdsc, a GB300 (sm_103a) engine for IMRT dose-deposition
+ * coefficients D_ij with a finite-size pencil beam (FSPB) model, after Gu et
+ * al., "GPU-based ultra fast dose calculation using a finite pencil beam
+ * model" (2009).
+ *
+ * The problem statement follows the paper: a CT density grid in the smallest
+ * rectangular prism that holds the patient (Fig. 1), beams from point
+ * sources (Section 2.2) divided into a x b beamlets (Section 2.1, Eq. 3), an
+ * FSPB kernel D^p = A(theta, d) F(x', d, z', C) (Eq. 2) with the three-term
+ * erf profile F (Eq. 3), and the output D_ij: the dose from beamlet i to voxel
+ * j (Eq. 1).  Radiological depth d comes from a lookup table along each
+ * beamlet axis built from the exact density integral (Siddon ray tracing,
+ * Section 2.2) and interpolated linearly at the projection O' of the voxel
+ * centre.  Only voxels inside the beamlet's volume of interest (VOI: a
+ * co-axial beamlet with 6x the side, Section 2.1) are evaluated.  Entries
+ * below a relative threshold of the row maximum are dropped and the rest is
+ * compacted into CSR (rows = beamlets, columns = voxels).
+ *
+ * Conventions (units mm, angles degrees):
+ *  - Density is FP32 [nz][ny][nx], x fastest.  grid.origin is the outer
+ *    corner of voxel (0,0,0); voxel centres are origin + (i + 1/2) * spacing.
+ *  - Beam frame: gantry g rotates about +z; source S = iso + SAD (sin g,
+ *    -cos g, 0); broad-beam axis (iso - S)/SAD; u = (cos g, sin g, 0);
+ *    v = (0, 0, 1).  Beamlet (iu, iv) is centred on the isocentre plane at
+ *    iso + (iu + 1/2 - n_u/2) a u + (iv + 1/2 - n_v/2) b v; a, b are the
+ *    beamlet sides at the isocentre plane and scale as t/SAD along the axis.
+ *  - Row order: beams in dsc_add_beam order, then iv, then iu.  Column of
+ *    voxel (ix, iy, iz) = ix + nx (iy + ny iz).  Columns ascend within a row.
+ *  - A(theta, d) = T(d) (SAD/t)^2: T is the tabulated depth-dose, t the
+ *    distance from S to O' along the beamlet axis.
+ *
+ * Errors: every entry point returns a dsc_status; no exception or signal
+ * crosses the ABI.  dsc_last_error() returns a thread-local description of
+ * the last failure on the calling thread.  Handles are not thread-safe
+ * unless stated; distinct handles may be used from distinct threads.
+ * Nothing in this library falls back to the CPU: with no usable CUDA device
+ * every compute entry point fails with DSC_E_CUDA.
+ */
+#ifndef DSC_H
+#define DSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSC_ABI_VERSION 1
+
+typedef enum {
+    DSC_OK = 0,
+    DSC_E_INVAL = 1,         /* bad argument: null pointer, size <= 0, source inside the grid, ... */
+    DSC_E_NOMEM = 2,         /* a device or pinned-host allocation failed */
+    DSC_E_NOMEM_BUDGET = 3,  /* a request's HBM footprint exceeds the server budget */
+    DSC_E_CUDA = 4,          /* CUDA runtime error; text in dsc_last_error() */
+    DSC_E_TIMEOUT = 5,       /* a bounded device-side wait expired (status word set by a kernel) */
+    DSC_E_STATE = 6,         /* call not valid in the handle's current state */
+    DSC_E_NOTFOUND = 7,      /* unknown request id */
+    DSC_E_BUSY = 8           /* result not ready (non-blocking poll) */
+} dsc_status;
+
+typedef struct dsc_geometry dsc_geometry;   /* device-resident density + beam model + beam list */
+typedef struct dsc_result dsc_result;       /* device-resident CSR D_ij and per-row statistics */
+typedef struct dsc_server dsc_server;       /* continuous-batching request server */
+
+/* CT grid (Fig. 1: the smallest prism that holds the CT). */
+typedef struct {
+    int32_t nx, ny, nz;      /* voxels per axis, each >= 1; nx*ny*nz < 2^31 */
+    double dx, dy, dz;       /* voxel sides, > 0 */
+    double origin[3];        /* outer corner of voxel (0,0,0) */
+} dsc_grid_desc;
+
+/* Lateral cutoff: which voxels of a beamlet are evaluated at all. */
+enum {
+    DSC_CUTOFF_VOI6 = 0,     /* |x'| <= 3 a_t and |z'| <= 3 b_t: VOI of 6x the side (Section 2.1) */
+    DSC_CUTOFF_SIGMA = 1,    /* |x'| <= a_t/2 + k c3_1(d), same in z' */
+    DSC_CUTOFF_NONE = 2      /* every voxel in front of the source */
+};
+
+/* FSPB beam model (Eq. 2-3).  table4 holds n rows {T(d), c3_1(d), c3_2(d),
+ * c3_3(d)} at n equally spaced depths on [0, d_max]; values are interpolated
+ * linearly and clamped to the last row beyond d_max.  c1, c2 are the
+ * depth-independent weights and width factors of the three erf terms.  The
+ * table is copied; the caller keeps ownership of table4. */
+typedef struct {
+    int32_t n;               /* 2 <= n <= 4096 */
+    double d_max;            /* > 0 */
+    const float* table4;     /* host pointer, n*4 floats */
+    double c1[3];
+    double c2[3];
+    int32_t cutoff_mode;     /* DSC_CUTOFF_* */
+    double cutoff_k;         /* k of DSC_CUTOFF_SIGMA */
+} dsc_fspb_model;
+
+/* One broad beam from a point source, divided into n_u x n_v beamlets. */
+typedef struct {
+    double gantry_deg;
+    double sad;              /* source-axis distance, > 0; the source must lie outside the grid */
+    double iso[3];           /* isocentre */
+    double a, b;             /* beamlet sides at the isocentre plane (along u and v), > 0 */
+    int32_t n_u, n_v;        /* >= 1 */
+} dsc_beam_desc;
+
+enum { DSC_VALUE_F32 = 0, DSC_VALUE_BF16 = 1 };
+enum {
+    DSC_FLAG_TIMING = 1      /* record CUDA events around each stage (dsc_get_stage_times) */
+};
+
+typedef struct {
+    double rel_threshold;    /* keep D_ij > 0 with D_ij >= rel_threshold * max_j' D_ij' (row max); >= 0 */
+    int32_t value_dtype;     /* DSC_VALUE_F32, or DSC_VALUE_BF16: value / beam_scale[beam] rounded to bf16 */
+    double h_frac;           /* depth-table spacing / min voxel side, (0, 1]; the paper uses 1/2 */
+    int32_t flags;           /* DSC_FLAG_* */
+} dsc_compute_opts;
+
+/* A view of a result's CSR.  On-device pointers stay valid until
+ * dsc_release_result; host pointers (copy_to_host = 1) are owned by the
+ * result.  val is float (DSC_VALUE_F32) or bf16 bits (uint16_t, DSC_VALUE_BF16);
+ * with bf16, D_ij = bf16_to_float(val) * beam_scale[beam of the row]. */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    const int64_t* row_ptr;  /* nrows + 1 */
+    const int32_t* col;      /* nnz */
+    const void* val;         /* nnz */
+    int32_t value_dtype;
+    int32_t nbeams;
+    const float* beam_scale; /* nbeams (1.0 for DSC_VALUE_F32) */
+    int64_t pairs;           /* voxel-beamlet pairs evaluated (inside the lateral cutoff) */
+    int32_t on_device;
+} dsc_csr_view;
+
+/* --- library ------------------------------------------------------------ */
+const char* dsc_status_str(dsc_status s);
+const char* dsc_last_error(void);
+int32_t dsc_abi_version(void);
+/* kernels this library has launched in this process (for launch accounting) */
+int64_t dsc_launch_count(void);
+
+/* --- geometry (Fig. 1, Section 2.2) -------------------------------------- */
+/* Copies the grid, density and model to the current device on `stream`
+ * (a cudaStream_t, NULL = legacy default stream).  density is a host pointer
+ * (density_on_device = 0) or a device pointer read stream-ordered (= 1).  The
+ * geometry starts with no beams. */
+dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float* density, int32_t density_on_device,
+                               const dsc_fspb_model* model, void* stream, dsc_geometry** out);
+/* Replaces the density (same grid) -- a new CT of the same patient set-up. */
+dsc_status dsc_upload_density(dsc_geometry* geom, const float* density, int32_t density_on_device, void* stream);
+/* Appends a beam; its rows follow the rows of the beams added before it. */
+dsc_status dsc_add_beam(dsc_geometry* geom, const dsc_beam_desc* beam, int32_t* beam_index_out);
+dsc_status dsc_clear_beams(dsc_geometry* geom);
+/* Frees the geometry after all work queued on it has finished. */
+void dsc_destroy_geometry(dsc_geometry* geom);
+
+/* --- computation --------------------------------------------------------- */
+/* D_ij of every beamlet of every beam of `geom` (Eq. 1-3).  All work is
+ * queued on `stream`; the call returns without waiting except for one
+ * stream-ordered read of the total candidate count the first time a
+ * geometry/beam set is planned.  The result is usable on `stream` at once;
+ * host views need dsc_get_csr, which waits. */
+dsc_status dsc_compute_dij(dsc_geometry* geom, const dsc_compute_opts* opts, void* stream, dsc_result** out);
+/* Many independent geometries (re-plan instances) in one launch sequence:
+ * each kernel stage runs once over all instances, the evaluation is one
+ * persistent kernel over a shared work queue, and the sequence is captured
+ * in a CUDA graph that is replayed while the set of geometries, their beams
+ * and the options stay the same.  outs[k] receives instance k's result. */
+dsc_status dsc_compute_dij_batch(dsc_geometry* const* geoms, int32_t n, const dsc_compute_opts* opts,
+                                 void* stream, dsc_result** outs);
+/* Blocks until the result's device work has finished; returns DSC_E_TIMEOUT
+ * if a bounded device wait expired, DSC_E_CUDA on a device error. */
+dsc_status dsc_result_wait(dsc_result* res);
+/* copy_to_host = 0: device view (waits only for nnz); 1: copies to
+ * result-owned pinned host buffers and waits. */
+dsc_status dsc_get_csr(dsc_result* res, int32_t copy_to_host, dsc_csr_view* out);
+/* Copies the CSR into caller-provided host buffers (ideally pinned) on
+ * `stream` and waits for the copy.  Sizes come from dsc_get_csr(res, 0, ...):
+ * row_ptr nrows+1, col nnz, val nnz * (4 or 2) bytes, beam_scale nbeams (may be NULL). */
+dsc_status dsc_copy_csr_to_host(dsc_result* res, int64_t* row_ptr, int32_t* col, void* val, float* beam_scale,
+                                void* stream);
+void dsc_release_result(dsc_result* res);
+
+/* --- stage inspection (per-step parity and timing) ---------------------- */
+/* Per row 16 doubles: S[3] e[3] x'[3] z'[3] tA tB hit n_table. */
+dsc_status dsc_get_beamlets(dsc_result* res, double* out, int64_t cap_rows);
+/* Depth tables, row-major [nrows][n_max] floats (entries past a row's n_table are 0). */
+dsc_status dsc_get_depth_tables(dsc_result* res, float* out, int64_t cap, int32_t* n_max_out);
+/* Per row: max D over the row's candidates and the candidate count. */
+dsc_status dsc_get_row_stats(dsc_result* res, float* row_max, int64_t* row_cand);
+/* Milliseconds per stage (needs DSC_FLAG_TIMING): [setup, siddon, count+scan,
+ * eval, beam-scale, compact count+scan, compact write, total]. n >= 8. */
+dsc_status dsc_get_stage_times(dsc_result* res, float* ms, int32_t n);
+
+/* --- serving: continuous batching of re-plan requests -------------------- */
+/* hbm_budget_bytes: cap on the summed device footprint of admitted requests;
+ * max_inflight: concurrent device slots (streams); max_batch: requests fused
+ * into one batched launch. */
+dsc_status dsc_server_create(size_t hbm_budget_bytes, int32_t max_inflight, int32_t max_batch, dsc_server** out);
+/* Queues D_ij for `geom` with an explicit beam set (the geometry's own beam
+ * list is not used).  Never blocks; DSC_E_NOMEM_BUDGET if the request could
+ * never fit the budget. */
+dsc_status dsc_server_submit(dsc_server* srv, dsc_geometry* geom, const dsc_beam_desc* beams, int32_t nbeams,
+                             const dsc_compute_opts* opts, uint64_t* req_id);
+/* Waits up to wait_ms (0 = do not wait, < 0 = forever) for request req_id;
+ * on DSC_OK *out is the caller's to release.  DSC_E_BUSY if not finished. */
+dsc_status dsc_server_poll(dsc_server* srv, uint64_t req_id, int32_t wait_ms, dsc_result** out);
+/* Latency (submit -> device completion) statistics in ms over finished requests. */
+dsc_status dsc_server_stats(dsc_server* srv, double* p50_ms, double* p99_ms, int64_t* n_done, int64_t* pairs_done);
+/* Drains queued work, then frees the server. */
+void dsc_server_destroy(dsc_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSC_H */

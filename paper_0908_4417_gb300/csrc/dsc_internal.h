@@ -1,0 +1,119 @@
+// dsc_internal.h -- device-side data layout of libdsc (host and device code).
+//
+// Flat layout over all instances of a launch: instances (geometries) own rows
+// (beamlets, Eq. 1 index i); rows own work items; items own candidate pairs.
+// Every buffer lives in HBM for the life of a plan and is indexed by these
+// flat ids, so one kernel launch covers a whole batch of re-plan instances.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dsc {
+
+constexpr int kEvalThreads = 256;     // threads per CTA of the evaluation / compaction kernels
+constexpr int kMaxLinesPerItem = 256; // x-lines handled by one work item
+constexpr int kWindow = 2048;         // candidates mapped to lines per pass of an item
+constexpr int kSiddonWarps = 4;       // rays (warps) per CTA of the depth-table kernel
+constexpr int kScanBlocks = 1024;     // blocks of the device-wide scan
+constexpr int kScanThreads = 256;
+
+// float-float value: hi + lo with |lo| <= ulp(hi)/2 (compensated FP32)
+struct ff { float hi, lo; };
+
+// One geometry of a launch.
+struct DInst {
+  const float* rho;        // density [nz][ny][nx]
+  const float4* lut;       // n_lut rows {T, c3_1, c3_2, c3_3}
+  int nx, ny, nz;
+  int n_lut;
+  double dx, dy, dz;
+  double ox, oy, oz;       // outer corner of voxel (0,0,0)
+  float lut_scale;         // (n_lut - 1) / d_max
+  float c3max;             // max of c3_1 over the table (SIGMA superset)
+  float c1q[3];            // c1 / 4
+  float c2h[3];            // c2 / 2
+  int cutoff_mode;
+  float cutoff_k;
+  int row_base, nrows;     // rows of this instance in the flat row list
+  int beam_base, nbeams;
+  float h;                 // depth-table spacing
+  float inv_h;
+  double hd;
+};
+
+// One beam of a launch (Section 2.1: broad beam from a point source).
+struct DBeam {
+  int inst;
+  int row_base;
+  int n_u, n_v;
+  double gantry_deg, sad, iso[3], a, b;
+};
+
+// One beamlet row: frame, ray and the constants of its voxel loop.
+struct DRow {
+  // Siddon ray (FP64 crossing parameters)
+  double S[3];             // source
+  double e[3];             // unit beamlet axis
+  double x[3], z[3];       // lateral unit axes (x', z' directions)
+  double tA, tB;           // entry A and exit B along the axis
+  // voxel loop, compensated FP32: value at voxel (0,0,0) and per-index slopes
+  ff S0, X0, Z0;           // s = t - tA, x', z' at voxel (0,0,0)
+  ff Ss[3], Xs[3], Zs[3];  // change of s, x', z' per step in ix, iy, iz
+  float tA_f;
+  float kx, kz, bx, bz;    // lateral cutoff |x'| <= kx t + bx, |z'| <= kz t + bz
+  float a_sad, b_sad;      // a / SAD, b / SAD (a_t = a_sad * t)
+  float sad;
+  int inst, beam;
+  int hit;                 // the axis crosses the grid prism
+  int n_table;             // depth-table entries (0 when !hit)
+  int iy0, iy1, iz0, iz1;  // voxel box of the VOI (lines to visit)
+  int ix0, ix1;
+  int lpc;                 // lines per work item
+  int nitems;
+};
+
+struct EvalParams {
+  const DInst* inst;
+  const DRow* rows;
+  const float* tables;      // [nrows][table_stride]
+  int table_stride;
+  const long long* row_item_base;  // nrows + 1
+  int nrows;
+  const long long* item_off;       // n_items + 1: first candidate of each item
+  const long long* n_items;        // device scalar (= row_item_base[nrows])
+  float* vals;                     // candidate values (D, or -1 outside the SIGMA cutoff)
+  unsigned* row_max;               // float bits, atomicMax
+  int* item_counter;               // persistent-kernel work queue head
+};
+
+// Output pointers of the computation in flight.  Kernels read them from this
+// device-side slot so that a captured launch sequence can be replayed into
+// freshly allocated result buffers.
+struct OutSlot {
+  long long* row_ptr;      // per instance (nrows + 1), relative to the instance's first entry
+  int* col;
+  void* val;               // float or bf16
+  float* beam_scale;       // per beam
+  unsigned* row_max;       // per row, float bits
+  long long* row_cand;     // per row
+  long long* inst_begin;   // per instance: first output slot; [ninst] = total
+};
+
+struct CompactParams {
+  const DInst* inst;
+  const DRow* rows;
+  const long long* row_item_base;
+  int nrows;
+  const long long* item_off;
+  const long long* n_items;
+  const float* vals;
+  const unsigned* row_max;
+  float tau;
+  int* item_kept;                 // count pass output
+  long long* row_cand;            // candidates inside the cutoff per row (atomic)
+  const long long* item_out;      // write pass: first output slot of each item
+  int value_dtype;
+  const OutSlot* slot;
+};
+
+}  // namespace dsc

@@ -1,0 +1,334 @@
+"""ctypes binding of libdsc (include/dsc.h), same entry-point names.
+
+Argument marshalling only: every step of the D_ij path runs in the library's
+sm_103a kernels.  There is no CPU fallback -- if libdsc.so is missing or no
+CUDA device is present, calls raise.
+
+Device buffers handed to the library (density_on_device=1) are torch CUDA
+tensors' ``data_ptr()``; streams are ``torch.cuda.Stream.cuda_stream`` (or 0
+for the legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdsc.so")
+
+DSC_OK = 0
+DSC_E_BUSY = 8
+DSC_CUTOFF_VOI6, DSC_CUTOFF_SIGMA, DSC_CUTOFF_NONE = 0, 1, 2
+DSC_VALUE_F32, DSC_VALUE_BF16 = 0, 1
+DSC_FLAG_TIMING = 1
+STAGES = ("setup", "siddon", "count", "eval", "beam_scale", "compact_count", "compact_write", "total")
+
+EXPORTS = [
+    "dsc_status_str", "dsc_last_error", "dsc_abi_version", "dsc_launch_count",
+    "dsc_create_geometry", "dsc_upload_density", "dsc_add_beam", "dsc_clear_beams", "dsc_destroy_geometry",
+    "dsc_compute_dij", "dsc_compute_dij_batch", "dsc_result_wait", "dsc_get_csr", "dsc_copy_csr_to_host",
+    "dsc_release_result", "dsc_get_beamlets", "dsc_get_depth_tables", "dsc_get_row_stats", "dsc_get_stage_times",
+    "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
+]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("origin", C.c_double * 3)]
+
+
+class FspbModel(C.Structure):
+    _fields_ = [("n", C.c_int32), ("d_max", C.c_double), ("table4", C.c_void_p),
+                ("c1", C.c_double * 3), ("c2", C.c_double * 3), ("cutoff_mode", C.c_int32), ("cutoff_k", C.c_double)]
+
+
+class BeamDesc(C.Structure):
+    _fields_ = [("gantry_deg", C.c_double), ("sad", C.c_double), ("iso", C.c_double * 3),
+                ("a", C.c_double), ("b", C.c_double), ("n_u", C.c_int32), ("n_v", C.c_int32)]
+
+
+class ComputeOpts(C.Structure):
+    _fields_ = [("rel_threshold", C.c_double), ("value_dtype", C.c_int32), ("h_frac", C.c_double),
+                ("flags", C.c_int32)]
+
+
+class CsrView(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("ncols", C.c_int64), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+                ("value_dtype", C.c_int32), ("nbeams", C.c_int32), ("beam_scale", C.c_void_p),
+                ("pairs", C.c_int64), ("on_device", C.c_int32)]
+
+
+class DscError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"dsc status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libdsc.so (built by build.py).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdsc.so not built ({LIB_PATH}); run paper_0908_4417_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P, V, I32, I64, U64 = C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+        sig = {
+            "dsc_status_str": (C.c_char_p, [C.c_int]),
+            "dsc_last_error": (C.c_char_p, []),
+            "dsc_abi_version": (I32, []),
+            "dsc_launch_count": (I64, []),
+            "dsc_create_geometry": (C.c_int, [C.POINTER(GridDesc), P, I32, C.POINTER(FspbModel), P, C.POINTER(P)]),
+            "dsc_upload_density": (C.c_int, [P, P, I32, P]),
+            "dsc_add_beam": (C.c_int, [P, C.POINTER(BeamDesc), C.POINTER(I32)]),
+            "dsc_clear_beams": (C.c_int, [P]),
+            "dsc_destroy_geometry": (None, [P]),
+            "dsc_compute_dij": (C.c_int, [P, C.POINTER(ComputeOpts), P, C.POINTER(P)]),
+            "dsc_compute_dij_batch": (C.c_int, [C.POINTER(P), I32, C.POINTER(ComputeOpts), P, C.POINTER(P)]),
+            "dsc_result_wait": (C.c_int, [P]),
+            "dsc_get_csr": (C.c_int, [P, I32, C.POINTER(CsrView)]),
+            "dsc_copy_csr_to_host": (C.c_int, [P, P, P, P, P, P]),
+            "dsc_release_result": (None, [P]),
+            "dsc_get_beamlets": (C.c_int, [P, P, I64]),
+            "dsc_get_depth_tables": (C.c_int, [P, P, I64, C.POINTER(I32)]),
+            "dsc_get_row_stats": (C.c_int, [P, P, P]),
+            "dsc_get_stage_times": (C.c_int, [P, P, I32]),
+            "dsc_server_create": (C.c_int, [C.c_size_t, I32, I32, C.POINTER(P)]),
+            "dsc_server_submit": (C.c_int, [P, P, C.POINTER(BeamDesc), I32, C.POINTER(ComputeOpts), C.POINTER(U64)]),
+            "dsc_server_poll": (C.c_int, [P, U64, I32, C.POINTER(P)]),
+            "dsc_server_stats": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(I64),
+                                           C.POINTER(I64)]),
+            "dsc_server_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != DSC_OK:
+        raise DscError(st, lib().dsc_last_error().decode(errors="replace"))
+
+
+# ---------------------------------------------------------------------------
+# descriptors from plain objects (phantom dataclasses or anything alike)
+# ---------------------------------------------------------------------------
+def grid_desc(g) -> GridDesc:
+    return GridDesc(int(g.nx), int(g.ny), int(g.nz), float(g.dx), float(g.dy), float(g.dz),
+                    (C.c_double * 3)(*[float(v) for v in g.origin]))
+
+
+def beam_desc(b) -> BeamDesc:
+    return BeamDesc(float(b.gantry_deg), float(b.sad), (C.c_double * 3)(*[float(v) for v in b.iso]),
+                    float(b.a), float(b.b), int(b.n_u), int(b.n_v))
+
+
+def compute_opts(tau=1e-3, value_dtype=DSC_VALUE_F32, h_frac=0.5, flags=0) -> ComputeOpts:
+    return ComputeOpts(float(tau), int(value_dtype), float(h_frac), int(flags))
+
+
+class _ModelRef:
+    def __init__(self, m):
+        self.table = np.ascontiguousarray(m.lut, dtype=np.float32)
+        self.s = FspbModel(int(self.table.shape[0]), float(m.d_max), self.table.ctypes.data,
+                           (C.c_double * 3)(*[float(v) for v in m.c1]), (C.c_double * 3)(*[float(v) for v in m.c2]),
+                           int(m.cutoff_mode), float(m.cutoff_k))
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def dsc_abi_version() -> int:
+    return int(lib().dsc_abi_version())
+
+
+def dsc_launch_count() -> int:
+    return int(lib().dsc_launch_count())
+
+
+def dsc_create_geometry(grid, density, density_on_device: bool, model, stream=0):
+    """density: numpy float32 [nz][ny][nx] (host) or a device pointer (int)."""
+    g = grid_desc(grid)
+    mr = _ModelRef(model)
+    if density_on_device:
+        ptr = int(density)
+    else:
+        density = np.ascontiguousarray(density, dtype=np.float32)
+        assert density.shape == (grid.nz, grid.ny, grid.nx)
+        ptr = density.ctypes.data
+    out = C.c_void_p()
+    _check(lib().dsc_create_geometry(C.byref(g), ptr, int(bool(density_on_device)), C.byref(mr.s), stream,
+                                     C.byref(out)))
+    return out.value
+
+
+def dsc_upload_density(geom, density, density_on_device: bool, stream=0):
+    if density_on_device:
+        ptr = int(density)
+    else:
+        density = np.ascontiguousarray(density, dtype=np.float32)
+        ptr = density.ctypes.data
+    _check(lib().dsc_upload_density(geom, ptr, int(bool(density_on_device)), stream))
+
+
+def dsc_add_beam(geom, beam) -> int:
+    idx = C.c_int32()
+    _check(lib().dsc_add_beam(geom, C.byref(beam_desc(beam)), C.byref(idx)))
+    return idx.value
+
+
+def dsc_clear_beams(geom):
+    _check(lib().dsc_clear_beams(geom))
+
+
+def dsc_destroy_geometry(geom):
+    lib().dsc_destroy_geometry(geom)
+
+
+def dsc_compute_dij(geom, opts: ComputeOpts, stream=0):
+    out = C.c_void_p()
+    _check(lib().dsc_compute_dij(geom, C.byref(opts), stream, C.byref(out)))
+    return out.value
+
+
+def dsc_compute_dij_batch(geoms, opts: ComputeOpts, stream=0):
+    n = len(geoms)
+    arr = (C.c_void_p * n)(*geoms)
+    outs = (C.c_void_p * n)()
+    _check(lib().dsc_compute_dij_batch(arr, n, C.byref(opts), stream, outs))
+    return [outs[i] for i in range(n)]
+
+
+def dsc_result_wait(res):
+    _check(lib().dsc_result_wait(res))
+
+
+def dsc_get_csr(res, copy_to_host: bool = False) -> CsrView:
+    v = CsrView()
+    _check(lib().dsc_get_csr(res, int(bool(copy_to_host)), C.byref(v)))
+    return v
+
+
+def dsc_copy_csr_to_host(res, row_ptr, col, val, beam_scale=None, stream=0):
+    """Arguments are host buffers (numpy arrays or pinned torch tensors: pass data pointers as ints)."""
+    def ptr(a):
+        if a is None:
+            return None
+        return a if isinstance(a, int) else (a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+    _check(lib().dsc_copy_csr_to_host(res, ptr(row_ptr), ptr(col), ptr(val), ptr(beam_scale), stream))
+
+
+def dsc_release_result(res):
+    lib().dsc_release_result(res)
+
+
+def dsc_get_beamlets(res, nrows: int) -> np.ndarray:
+    out = np.zeros((max(nrows, 1), 16), dtype=np.float64)
+    _check(lib().dsc_get_beamlets(res, out.ctypes.data, nrows))
+    return out[:nrows]
+
+
+def dsc_get_depth_tables(res, nrows: int) -> np.ndarray:
+    n_max = C.c_int32()
+    _check(lib().dsc_get_depth_tables(res, None, 0, C.byref(n_max)))
+    out = np.zeros((nrows, n_max.value), dtype=np.float32)
+    _check(lib().dsc_get_depth_tables(res, out.ctypes.data, out.size, C.byref(n_max)))
+    return out
+
+
+def dsc_get_row_stats(res, nrows: int):
+    rm = np.zeros(max(nrows, 1), dtype=np.float32)
+    rc = np.zeros(max(nrows, 1), dtype=np.int64)
+    _check(lib().dsc_get_row_stats(res, rm.ctypes.data, rc.ctypes.data))
+    return rm[:nrows], rc[:nrows]
+
+
+def dsc_get_stage_times(res) -> dict:
+    ms = np.zeros(8, dtype=np.float32)
+    _check(lib().dsc_get_stage_times(res, ms.ctypes.data, 8))
+    return dict(zip(STAGES, ms.tolist()))
+
+
+def dsc_server_create(hbm_budget_bytes: int, max_inflight: int = 2, max_batch: int = 8):
+    out = C.c_void_p()
+    _check(lib().dsc_server_create(int(hbm_budget_bytes), int(max_inflight), int(max_batch), C.byref(out)))
+    return out.value
+
+
+def dsc_server_submit(srv, geom, beams, opts: ComputeOpts) -> int:
+    arr = (BeamDesc * len(beams))(*[beam_desc(b) for b in beams])
+    rid = C.c_uint64()
+    _check(lib().dsc_server_submit(srv, geom, arr, len(beams), C.byref(opts), C.byref(rid)))
+    return rid.value
+
+
+def dsc_server_poll(srv, req_id: int, wait_ms: int = -1):
+    """Returns the result handle, or None if not finished within wait_ms."""
+    out = C.c_void_p()
+    st = lib().dsc_server_poll(srv, int(req_id), int(wait_ms), C.byref(out))
+    if st == DSC_E_BUSY:
+        return None
+    _check(st)
+    return out.value
+
+
+def dsc_server_stats(srv):
+    p50, p99 = C.c_double(), C.c_double()
+    n, pairs = C.c_int64(), C.c_int64()
+    _check(lib().dsc_server_stats(srv, C.byref(p50), C.byref(p99), C.byref(n), C.byref(pairs)))
+    return {"p50_ms": p50.value, "p99_ms": p99.value, "n_done": n.value, "pairs_done": pairs.value}
+
+
+def dsc_server_destroy(srv):
+    lib().dsc_server_destroy(srv)
+
+
+# ---------------------------------------------------------------------------
+# conveniences on top of the entry points
+# ---------------------------------------------------------------------------
+class HostCSR:
+    """A result's CSR copied to host numpy arrays (values as float32)."""
+
+    def __init__(self, res):
+        v = dsc_get_csr(res, False)
+        self.nrows, self.ncols, self.nnz, self.pairs = int(v.nrows), int(v.ncols), int(v.nnz), int(v.pairs)
+        self.value_dtype = int(v.value_dtype)
+        self.row_ptr = np.zeros(self.nrows + 1, dtype=np.int64)
+        self.col = np.zeros(max(self.nnz, 1), dtype=np.int32)
+        raw = np.zeros(max(self.nnz, 1), dtype=np.uint16 if self.value_dtype == DSC_VALUE_BF16 else np.float32)
+        self.beam_scale = np.zeros(max(int(v.nbeams), 1), dtype=np.float32)
+        dsc_copy_csr_to_host(res, self.row_ptr, self.col, raw, self.beam_scale)
+        self.col = self.col[:self.nnz]
+        raw = raw[:self.nnz]
+        if self.value_dtype == DSC_VALUE_BF16:
+            self.raw = raw
+            self.val = (raw.astype(np.uint32) << 16).view(np.float32)
+        else:
+            self.val = raw
+
+    def row(self, r):
+        a, b = self.row_ptr[r], self.row_ptr[r + 1]
+        return self.col[a:b], self.val[a:b]
+
+
+def geometry_from_workload(w, stream=0):
+    g = dsc_create_geometry(w.grid, w.density, False, w.model, stream)
+    for b in w.beams:
+        dsc_add_beam(g, b)
+    return g
+
+
+def compute_workload(w, stream=0, flags=0, value_dtype=None):
+    """One-shot: geometry, D_ij, host CSR.  Returns (HostCSR, result handle, geometry handle)."""
+    g = geometry_from_workload(w, stream)
+    dt = w.value_dtype if value_dtype is None else value_dtype
+    res = dsc_compute_dij(g, compute_opts(w.tau, dt, w.h_frac, flags), stream)
+    return HostCSR(res), res, g

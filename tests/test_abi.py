@@ -1,0 +1,54 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/dsc.h declares.  CPU only: no compute call needs a GPU here."""
+import os
+import re
+
+import pytest
+
+from paper_0908_4417_gb300 import build as B
+from paper_0908_4417_gb300 import dsc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "dsc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dsc_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return dsc.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(dsc.EXPORTS) == names
+
+
+def test_library_metadata(lib):
+    assert dsc.dsc_abi_version() == 1
+    assert lib.dsc_status_str(0) == b"ok"
+    assert lib.dsc_status_str(5) == b"device wait timed out"
+    assert dsc.dsc_launch_count() >= 0
+
+
+def test_null_arguments_are_rejected(lib):
+    import ctypes as C
+    out = C.c_void_p()
+    assert lib.dsc_create_geometry(None, None, 0, None, None, C.byref(out)) == 1
+    assert b"null" in lib.dsc_last_error()
+    assert lib.dsc_compute_dij(None, None, None, C.byref(out)) == 1
+
+
+def test_struct_layouts_match_header():
+    import ctypes as C
+    assert C.sizeof(dsc.GridDesc) == 3 * 4 + 4 + 6 * 8
+    assert C.sizeof(dsc.BeamDesc) == 8 * 7 + 8
+    assert C.sizeof(dsc.ComputeOpts) == 32
+    assert C.sizeof(dsc.CsrView) == 3 * 8 + 3 * 8 + 8 + 8 + 8 + 8

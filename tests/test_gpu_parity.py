@@ -1,0 +1,301 @@
+"""Parity of the sm_103a path (through the C ABI) against the FP64 oracle.
+
+Acceptance: CSR structure identical outside the oracle's ambiguity bands
+(+-1e-6 relative of the threshold, 1e-3 mm of the lateral cutoff); FP32
+values within 1e-4 maximum relative error; BF16 values (scaled per beam)
+within 2^-8 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0908_4417_gb300 import phantoms as P
+from tests.csr_compare import compare
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dsc():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_0908_4417_gb300 import build as B
+    B.build()
+    from paper_0908_4417_gb300 import dsc as D
+    D.lib()
+    torch.cuda.init()
+    return D
+
+
+def gpu_rows(csr, rows):
+    return [csr.row(int(r)) for r in rows]
+
+
+def run(dsc, w, **kw):
+    csr, res, g = dsc.compute_workload(w, **kw)
+    return csr, res, g
+
+
+def cleanup(dsc, res, g):
+    dsc.dsc_release_result(res)
+    dsc.dsc_destroy_geometry(g)
+
+
+# ---------------------------------------------------------------------------
+# whole workloads
+# ---------------------------------------------------------------------------
+def test_water_32_full(dsc):
+    w = P.water_32()
+    csr, res, g = run(dsc, w)
+    orc = O.compute_workload(w)
+    st = compare(gpu_rows(csr, range(w.nrows)), orc, TOL)
+    assert csr.nnz > 100000
+    assert abs(csr.pairs - orc.pairs) <= len(orc.amb_row)
+    print("water_32", st)
+    cleanup(dsc, res, g)
+
+
+def test_slabs_128_fp32_full(dsc):
+    w = P.slabs_128(value_dtype=P.VALUE_F32)
+    csr, res, g = run(dsc, w)
+    orc = O.compute_workload(w)
+    st = compare(gpu_rows(csr, range(w.nrows)), orc, TOL)
+    assert abs(csr.pairs - orc.pairs) <= len(orc.amb_row)
+    print("slabs_128 fp32", st)
+    cleanup(dsc, res, g)
+
+
+def test_slabs_128_bf16_error_report(dsc):
+    """BF16 storage: value = bf16(D / s_b) * s_b, s_b = beam maximum.  Relative
+    error against the FP64 oracle is bounded by bf16 rounding (2^-9) plus the
+    FP32 error; reported per config."""
+    w = P.slabs_128(value_dtype=P.VALUE_BF16)
+    csr, res, g = run(dsc, w)
+    orc = O.compute_workload(w)
+    scale = csr.beam_scale[0]
+    assert abs(scale / orc.row_max.max() - 1) < 1e-5
+    rows = [(c, v * scale) for c, v in gpu_rows(csr, range(w.nrows))]
+    st = compare(rows, orc, 2.0 ** -8)
+    print("slabs_128 bf16 max_rel", st["max_rel"])
+    cleanup(dsc, res, g)
+
+
+def test_prostate_full_size_sampled_rows(dsc):
+    """The benchmark workload at full size (9 fields, 2304 rows) in the same
+    launch configuration; 72 rows spread over all beams are checked against
+    oracle rows computed one by one."""
+    w = P.prostate_256()
+    csr, res, g = run(dsc, w)
+    rng = np.random.default_rng(7)
+    rows = np.sort(np.concatenate([b * 256 + rng.choice(256, 8, replace=False) for b in range(9)]))
+    orc = O.compute_workload(w, rows=rows)
+    st = compare(gpu_rows(csr, rows), orc, TOL)
+    print("prostate sampled", st)
+    # whole-matrix invariants at full size
+    assert csr.row_ptr[0] == 0 and np.all(np.diff(csr.row_ptr) >= 0) and csr.row_ptr[-1] == csr.nnz
+    assert csr.col.min() >= 0 and csr.col.max() < w.grid.nvox
+    assert np.all(csr.val > 0)
+    rm, rc = dsc.dsc_get_row_stats(res, w.nrows)
+    assert np.allclose(rm[rows], orc.row_max, rtol=TOL)
+    assert np.all(np.abs(rc[rows] - orc.row_cand) <= 64)
+    assert rc.sum() == csr.pairs
+    cleanup(dsc, res, g)
+
+
+# ---------------------------------------------------------------------------
+# per-step parity: frames and depth tables
+# ---------------------------------------------------------------------------
+def test_beamlet_setup_matches_oracle(dsc):
+    w = P.prostate_256()
+    csr, res, g = run(dsc, w)
+    gb = dsc.dsc_get_beamlets(res, w.nrows)
+    ob = O.beamlets(w.grid, w.beams, w.h_frac)
+    assert np.allclose(gb[:, 0:12], ob[:, 0:12], rtol=0, atol=1e-9)
+    assert np.allclose(gb[:, 12:14], ob[:, 12:14], rtol=0, atol=1e-7)
+    assert np.array_equal(gb[:, 14], ob[:, 15]) and np.array_equal(gb[:, 15], ob[:, 16])
+    cleanup(dsc, res, g)
+
+
+@pytest.mark.parametrize("name", ["prostate_256", "slabs_128"])
+def test_depth_tables_match_oracle(dsc, name):
+    w = P.get(name)
+    csr, res, g = run(dsc, w)
+    tabs = dsc.dsc_get_depth_tables(res, w.nrows)
+    rng = np.random.default_rng(3)
+    for r in rng.choice(w.nrows, 24, replace=False):
+        b, local = divmod(int(r), w.beams[0].nbeamlets)
+        iv, iu = divmod(local, w.beams[b].n_u)
+        ref = O.row_table(w.grid, w.density, w.beams[b], iu, iv, w.h_frac)
+        got = tabs[r, :ref.size].astype(np.float64)
+        # FP32 storage of a value up to ~500 mm: 1 ulp; Siddon sums in FP64
+        assert np.all(np.abs(got - ref) <= 2 * np.spacing(np.float32(np.maximum(ref, 1.0))) + 1e-6), r
+    cleanup(dsc, res, g)
+
+
+# ---------------------------------------------------------------------------
+# edge cases: ragged grids, oblique/anisotropic, cutoff modes, misses, empties
+# ---------------------------------------------------------------------------
+def edge_cases():
+    cases = []
+    for seed in range(5):
+        r = P._Draw(500 + seed)
+        n = (r.randint(3, 41), r.randint(3, 37), r.randint(1, 23))
+        sp = (1.0 + 3.0 * r.u(), 1.0 + 3.0 * r.u(), 1.0 + 3.0 * r.u())
+        g = P.centred_grid(*n, *sp, centre=(10 * r.u() - 5, 10 * r.u() - 5, 10 * r.u() - 5))
+        rho = P.random_grid_density(seed, g.shape, 0.0, 2.0)
+        mode = [P.CUTOFF_VOI6, P.CUTOFF_SIGMA, P.CUTOFF_NONE][seed % 3]
+        m = P.synthetic_model(cutoff_mode=mode, cutoff_k=2.5)
+        beams = [P.Beam(360 * r.u(), 300.0 + 700 * r.u(), (0.0, 0.0, 0.0), 1.0 + 6 * r.u(), 1.0 + 6 * r.u(),
+                        r.randint(1, 9), r.randint(1, 7)) for _ in range(r.randint(1, 3))]
+        hf = [0.5, 1.0, 0.25, 1.0 / 3.0, 0.5][seed]
+        cases.append(P.Workload(f"edge{seed}", g, rho, m, beams, tau=[1e-3, 0.0, 1e-2, 1e-3, 0.5][seed], h_frac=hf))
+    # a field wider than the grid: outer beamlet axes miss the prism (empty rows)
+    g = P.centred_grid(8, 8, 6, 2.0, 2.0, 2.0)
+    cases.append(P.Workload("misses", g, np.ones(g.shape, np.float32), P.synthetic_model(),
+                            [P.Beam(30.0, 500.0, (0.0, 0.0, 0.0), 6.0, 6.0, 8, 6)]))
+    # one voxel
+    g = P.centred_grid(1, 1, 1, 3.0, 3.0, 3.0)
+    cases.append(P.Workload("one_voxel", g, np.ones(g.shape, np.float32), P.synthetic_model(),
+                            [P.Beam(0.0, 100.0, (0.0, 0.0, 0.0), 2.0, 2.0, 1, 1)]))
+    return cases
+
+
+@pytest.mark.parametrize("idx", range(7))
+def test_edge_cases(dsc, idx):
+    w = edge_cases()[idx]
+    csr, res, g = run(dsc, w)
+    orc = O.compute_workload(w)
+    st = compare(gpu_rows(csr, range(w.nrows)), orc, TOL)
+    assert abs(csr.pairs - orc.pairs) <= len(orc.amb_row)
+    print(w.name, st, csr.nnz)
+    cleanup(dsc, res, g)
+
+
+def test_rows_that_miss_are_empty(dsc):
+    w = edge_cases()[5]
+    csr, res, g = run(dsc, w)
+    bl = O.beamlets(w.grid, w.beams)
+    miss = np.flatnonzero(bl[:, 15] == 0)
+    assert miss.size > 0
+    assert np.all(np.diff(csr.row_ptr)[miss] == 0)
+    cleanup(dsc, res, g)
+
+
+def test_threshold_extremes(dsc):
+    w = P.water_32()
+    g = dsc.geometry_from_workload(w)
+    r0 = dsc.dsc_compute_dij(g, dsc.compute_opts(0.0, 0, 0.5))
+    r1 = dsc.dsc_compute_dij(g, dsc.compute_opts(1.0, 0, 0.5))
+    c0, c1 = dsc.HostCSR(r0), dsc.HostCSR(r1)
+    assert c0.nnz == c0.pairs                       # tau = 0 keeps every positive candidate
+    counts = np.diff(c1.row_ptr)
+    assert np.all(counts >= 1)                      # tau = 1 keeps the row maximum (ties kept)
+    for r in range(0, w.nrows, 37):
+        cc, vv = c0.row(r)
+        assert c1.row(r)[1].max() == vv.max()
+    for x in (r0, r1):
+        dsc.dsc_release_result(x)
+    dsc.dsc_destroy_geometry(g)
+
+
+# ---------------------------------------------------------------------------
+# determinism, batch and serving
+# ---------------------------------------------------------------------------
+def test_repeat_is_bit_identical_and_graph_replay(dsc):
+    w = P.slabs_128(value_dtype=P.VALUE_F32)
+    g = dsc.geometry_from_workload(w)
+    opts = dsc.compute_opts(w.tau, 0, w.h_frac)
+    a = dsc.dsc_compute_dij(g, opts)
+    b = dsc.dsc_compute_dij(g, opts)       # replays the captured graph
+    t = dsc.dsc_compute_dij(g, dsc.compute_opts(w.tau, 0, w.h_frac, dsc.DSC_FLAG_TIMING))  # eager launches
+    ca, cb, ct = dsc.HostCSR(a), dsc.HostCSR(b), dsc.HostCSR(t)
+    for c in (cb, ct):
+        assert np.array_equal(ca.row_ptr, c.row_ptr) and np.array_equal(ca.col, c.col)
+        assert np.array_equal(ca.val, c.val)
+    times = dsc.dsc_get_stage_times(t)
+    assert times["eval"] > 0 and times["total"] >= times["eval"]
+    for x in (a, b, t):
+        dsc.dsc_release_result(x)
+    dsc.dsc_destroy_geometry(g)
+
+
+def small_instances(n):
+    out = []
+    for k in range(n):
+        r = P._Draw(900 + k)
+        g = P.centred_grid(r.randint(24, 48), r.randint(24, 48), r.randint(12, 24), 4.0, 4.0, 4.0)
+        rho = P.prostate_density(g, 900 + k, scale_x=0.35 * g.nx * 4 / 180, scale_y=0.23 * g.ny * 4 / 120,
+                                 scale_r=0.3)
+        bs = r.choice([2.5, 5.0, 10.0])
+        nb = int(80 / bs)
+        beams = [P.Beam(360 * r.u(), 1000.0, (0.0, 0.0, 0.0), bs, bs, nb, nb) for _ in range(r.randint(2, 4))]
+        out.append(P.Workload(f"inst{k}", g, rho, P.synthetic_model(), beams))
+    return out
+
+
+def test_batch_equals_single_and_oracle(dsc):
+    ws = small_instances(4)
+    gs = [dsc.geometry_from_workload(w) for w in ws]
+    opts = dsc.compute_opts(1e-3, 0, 0.5)
+    batch = dsc.dsc_compute_dij_batch(gs, opts)
+    for k, w in enumerate(ws):
+        cb = dsc.HostCSR(batch[k])
+        single = dsc.dsc_compute_dij(gs[k], opts)
+        cs = dsc.HostCSR(single)
+        assert np.array_equal(cb.row_ptr, cs.row_ptr) and np.array_equal(cb.col, cs.col)
+        assert np.array_equal(cb.val, cs.val)
+        orc = O.compute_workload(w)
+        compare(gpu_rows(cb, range(w.nrows)), orc, TOL)
+        dsc.dsc_release_result(single)
+    again = dsc.dsc_compute_dij_batch(gs, opts)      # graph replay of the batch
+    for k in range(4):
+        a, b = dsc.HostCSR(batch[k]), dsc.HostCSR(again[k])
+        assert np.array_equal(a.col, b.col) and np.array_equal(a.val, b.val)
+    for r in batch + again:
+        dsc.dsc_release_result(r)
+    for g in gs:
+        dsc.dsc_destroy_geometry(g)
+
+
+def test_server_results_same_alone_and_in_mix(dsc):
+    ws = small_instances(3)
+    gs = [dsc.geometry_from_workload(w) for w in ws]
+    opts = dsc.compute_opts(1e-3, 0, 0.5)
+    alone = []
+    for k, w in enumerate(ws):
+        r = dsc.dsc_compute_dij(gs[k], opts)
+        alone.append(dsc.HostCSR(r))
+        dsc.dsc_release_result(r)
+    srv = dsc.dsc_server_create(8 << 30, max_inflight=2, max_batch=4)
+    ids = []
+    for rep in range(3):
+        for k, w in enumerate(ws):
+            ids.append((k, dsc.dsc_server_submit(srv, gs[k], w.beams, opts)))
+    for k, rid in ids:
+        res = dsc.dsc_server_poll(srv, rid, -1)
+        c = dsc.HostCSR(res)
+        assert np.array_equal(c.row_ptr, alone[k].row_ptr) and np.array_equal(c.col, alone[k].col)
+        assert np.array_equal(c.val, alone[k].val)
+        dsc.dsc_release_result(res)
+    st = dsc.dsc_server_stats(srv)
+    assert st["n_done"] == 9 and st["p99_ms"] >= st["p50_ms"] > 0
+    dsc.dsc_server_destroy(srv)
+    for g in gs:
+        dsc.dsc_destroy_geometry(g)
+
+
+def test_server_budget_rejects_and_throttles(dsc):
+    ws = small_instances(2)
+    g = dsc.geometry_from_workload(ws[0])
+    opts = dsc.compute_opts(1e-3, 0, 0.5)
+    srv = dsc.dsc_server_create(1 << 10, 1, 1)
+    with pytest.raises(dsc.DscError) as e:
+        dsc.dsc_server_submit(srv, g, ws[0].beams, opts)
+    assert e.value.status == 3
+    dsc.dsc_server_destroy(srv)
+    dsc.dsc_destroy_geometry(g)
