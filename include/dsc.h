@@ -209,6 +209,37 @@ dsc_status dsc_server_stats(dsc_server* srv, double* p50_ms, double* p99_ms, int
 /* Drains queued work, then frees the server. */
 void dsc_server_destroy(dsc_server* srv);
 
+/* --- computation without allocation -------------------------------------- */
+/* dsc_compute_dij without any memory allocation by the library, for callers
+ * that must not allocate device memory while they run (loops that reserve
+ * every byte before treatment starts, processes held to a fixed GPU memory
+ * quota, code running where cudaMalloc is not allowed).  This entry point has
+ * no counterpart in the paper; it is the same computation and the same
+ * kernels as dsc_compute_dij for one geometry, FP32 values only.
+ *
+ * Inputs: grid, density_dev (device pointer, FP32 [nz][ny][nx]), model (its
+ * table4 on the host), beams[nbeams] (host), opts (value_dtype must be
+ * DSC_VALUE_F32).  Outputs, caller-allocated device buffers: row_ptr_dev
+ * (nrows + 1 int64), col_dev and val_dev (capacity entries each).  On
+ * DSC_OK, *nnz_out holds the number of kept entries and the CSR is complete
+ * (the call waits for its work on `stream`).
+ *
+ * Working memory is a fixed array of 64 MiB inside the library's device
+ * image, present on every GPU that loads the library until the process
+ * exits.  A request whose working set (set-up, depth tables, work items and
+ * 4 bytes per candidate pair) exceeds it fails with DSC_E_INVAL and says so
+ * in dsc_last_error(); so does an output capacity below the kept count
+ * (nothing is written to the outputs then).  The first call on a device
+ * looks up the array's device address; make that first call before any
+ * stream capture.  Every call reuses the array from the start: calls whose
+ * device work overlaps race and must not be issued (keep them on one stream,
+ * one host thread at a time).  The call allocates no device or host memory
+ * on its success path. */
+dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const float* density_dev, const dsc_fspb_model* model,
+                                   const dsc_beam_desc* beams, int32_t nbeams, const dsc_compute_opts* opts,
+                                   int64_t* row_ptr_dev, int32_t* col_dev, float* val_dev, int64_t capacity,
+                                   int64_t* nnz_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

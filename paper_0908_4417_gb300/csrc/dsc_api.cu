@@ -280,6 +280,7 @@ extern "C" const char* dsc_status_str(dsc_status s) {
   return "unknown status";
 }
 extern "C" const char* dsc_last_error(void) { return g_err.c_str(); }
+void dsc::set_error(const char* msg) { g_err = msg; }
 extern "C" int32_t dsc_abi_version(void) { return DSC_ABI_VERSION; }
 extern "C" int64_t dsc_launch_count(void) { return g_launches.load(); }
 

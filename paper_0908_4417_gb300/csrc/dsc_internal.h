@@ -116,4 +116,7 @@ struct CompactParams {
   const OutSlot* slot;
 };
 
+// sets the text dsc_last_error() returns on the calling thread
+void set_error(const char* msg);
+
 }  // namespace dsc

@@ -31,6 +31,7 @@ EXPORTS = [
     "dsc_compute_dij", "dsc_compute_dij_batch", "dsc_result_wait", "dsc_get_csr", "dsc_copy_csr_to_host",
     "dsc_release_result", "dsc_get_beamlets", "dsc_get_depth_tables", "dsc_get_row_stats", "dsc_get_stage_times",
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
+    "dsc_compute_dij_noalloc",
 ]
 
 
@@ -104,6 +105,8 @@ def lib():
             "dsc_server_stats": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(I64),
                                            C.POINTER(I64)]),
             "dsc_server_destroy": (None, [P]),
+            "dsc_compute_dij_noalloc": (C.c_int, [C.POINTER(GridDesc), P, C.POINTER(FspbModel), C.POINTER(BeamDesc),
+                                                  I32, C.POINTER(ComputeOpts), P, P, P, I64, C.POINTER(I64), P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -289,6 +292,20 @@ def dsc_server_stats(srv):
 
 def dsc_server_destroy(srv):
     lib().dsc_server_destroy(srv)
+
+
+def dsc_compute_dij_noalloc(grid, density_ptr: int, model, beams, opts: ComputeOpts, row_ptr_ptr: int, col_ptr: int,
+                            val_ptr: int, capacity: int, stream=0) -> int:
+    """D_ij into caller-allocated device buffers, no allocation by the library.
+    Returns the number of kept entries."""
+    g = grid_desc(grid)
+    mr = _ModelRef(model)
+    arr = (BeamDesc * len(beams))(*[beam_desc(b) for b in beams])
+    nnz = C.c_int64()
+    _check(lib().dsc_compute_dij_noalloc(C.byref(g), int(density_ptr), C.byref(mr.s), arr, len(beams), C.byref(opts),
+                                         int(row_ptr_ptr), int(col_ptr), int(val_ptr), int(capacity), C.byref(nnz),
+                                         stream))
+    return nnz.value
 
 
 # ---------------------------------------------------------------------------
