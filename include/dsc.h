@@ -227,7 +227,7 @@ void dsc_server_destroy(dsc_server* srv);
  * Working memory is a fixed array of 64 MiB inside the library's device
  * image, present on every GPU that loads the library until the process
  * exits.  A request whose working set (set-up, depth tables, work items and
- * 4 bytes per candidate pair) exceeds it fails with DSC_E_INVAL and says so
+ * 8 bytes per candidate pair) exceeds it fails with DSC_E_INVAL and says so
  * in dsc_last_error(); so does an output capacity below the kept count
  * (nothing is written to the outputs then).  The first call on a device
  * looks up the array's device address; make that first call before any

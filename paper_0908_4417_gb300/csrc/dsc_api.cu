@@ -196,6 +196,7 @@ struct Plan {
   int* d_item_kept = nullptr;
   long long* d_item_out = nullptr;
   float* d_vals = nullptr;
+  int* d_cols = nullptr;
   unsigned* d_row_max = nullptr;
   long long* d_row_cand = nullptr;
   long long* d_scan = nullptr;       // kScanBlocks + 1
@@ -209,9 +210,10 @@ struct Plan {
   int kernels_per_run = 0;           // kernel launches in one computation
   std::mutex mu;                     // one computation at a time per plan
   void free_scratch() {
-    void* ps[] = {d_item_cand, d_item_off, d_item_kept, d_item_out, d_vals};
-    release_after(last_done, device, ps, 5);
+    void* ps[] = {d_item_cand, d_item_off, d_item_kept, d_item_out, d_vals, d_cols};
+    release_after(last_done, device, ps, 6);
     d_item_cand = nullptr; d_item_off = nullptr; d_item_kept = nullptr; d_item_out = nullptr; d_vals = nullptr;
+    d_cols = nullptr;
     if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
   }
   ~Plan() {
@@ -441,6 +443,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
     I.n_lut = g->n_lut;
     I.dx = g->grid.dx; I.dy = g->grid.dy; I.dz = g->grid.dz;
     I.ox = g->grid.origin[0]; I.oy = g->grid.origin[1]; I.oz = g->grid.origin[2];
+    I.idx = 1.0 / I.dx; I.idy = 1.0 / I.dy; I.idz = 1.0 / I.dz;
     I.lut_scale = (float)((g->n_lut - 1) / g->d_max);
     I.c3max = g->c3max;
     for (int i = 0; i < 3; ++i) { I.c1q[i] = (float)(g->c1[i] / 4.0); I.c2h[i] = (float)(g->c2[i] / 2.0); }
@@ -519,6 +522,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   CU(cudaMemcpyAsync(&P->n_cand, P->d_item_off + P->n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   TRY(dalloc(&P->d_vals, P->n_cand, s));
+  TRY(dalloc(&P->d_cols, P->n_cand, s));
   out = P;
   return DSC_OK;
 }
@@ -588,6 +592,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   ep.item_off = P->d_item_off;
   ep.n_items = n_items;
   ep.vals = P->d_vals;
+  ep.cols = P->d_cols;
   ep.row_max = P->d_row_max;
   ep.item_counter = P->d_counter;
   k_eval<<<P->grid_eval, kEvalThreads, 0, s>>>(ep);
@@ -608,6 +613,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.item_off = P->d_item_off;
   cp.n_items = n_items;
   cp.vals = P->d_vals;
+  cp.cols = P->d_cols;
   cp.row_max = P->d_row_max;
   cp.tau = (float)P->opts.rel_threshold;
   cp.item_kept = P->d_item_kept;

@@ -11,7 +11,7 @@
 namespace dsc {
 
 constexpr int kEvalThreads = 256;     // threads per CTA of the evaluation / compaction kernels
-constexpr int kMaxLinesPerItem = 256; // x-lines handled by one work item
+constexpr int kMaxLinesPerItem = 512; // x-lines handled by one work item (multiple of kEvalThreads)
 constexpr int kWindow = 2048;         // candidates mapped to lines per pass of an item
 constexpr int kSiddonWarps = 4;       // rays (warps) per CTA of the depth-table kernel
 constexpr int kScanBlocks = 1024;     // blocks of the device-wide scan
@@ -28,6 +28,7 @@ struct DInst {
   int n_lut;
   double dx, dy, dz;
   double ox, oy, oz;       // outer corner of voxel (0,0,0)
+  double idx, idy, idz;    // 1 / voxel sides
   float lut_scale;         // (n_lut - 1) / d_max
   float c3max;             // max of c3_1 over the table (SIGMA superset)
   float c1q[3];            // c1 / 4
@@ -56,6 +57,7 @@ struct DRow {
   double e[3];             // unit beamlet axis
   double x[3], z[3];       // lateral unit axes (x', z' directions)
   double tA, tB;           // entry A and exit B along the axis
+  double inv_e[3];         // 1 / e (0 where e is 0)
   // voxel loop, compensated FP32: value at voxel (0,0,0) and per-index slopes
   ff S0, X0, Z0;           // s = t - tA, x', z' at voxel (0,0,0)
   ff Ss[3], Xs[3], Zs[3];  // change of s, x', z' per step in ix, iy, iz
@@ -82,6 +84,7 @@ struct EvalParams {
   const long long* item_off;       // n_items + 1: first candidate of each item
   const long long* n_items;        // device scalar (= row_item_base[nrows])
   float* vals;                     // candidate values (D, or -1 outside the SIGMA cutoff)
+  int* cols;                       // candidate voxel indices
   unsigned* row_max;               // float bits, atomicMax
   int* item_counter;               // persistent-kernel work queue head
 };
@@ -107,6 +110,7 @@ struct CompactParams {
   const long long* item_off;
   const long long* n_items;
   const float* vals;
+  const int* cols;
   const unsigned* row_max;
   float tau;
   int* item_kept;                 // count pass output

@@ -16,6 +16,7 @@
 // used only in the per-beamlet set-up and for Siddon's plane-crossing
 // parameters alpha.
 #include "dsc_internal.h"
+#include "dsc_erfc_coeffs.h"
 
 #include <cuda_bf16.h>
 #include <math_constants.h>
@@ -95,7 +96,10 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
   normalize3(x);
   double z[3] = {-e[2] * e[0] - x[2] * x[0], -e[2] * e[1] - x[2] * x[1], 1.0 - e[2] * e[2] - x[2] * x[2]};
   normalize3(z);
-  for (int k = 0; k < 3; ++k) { R.S[k] = S[k]; R.e[k] = e[k]; R.x[k] = x[k]; R.z[k] = z[k]; }
+  for (int k = 0; k < 3; ++k) {
+    R.S[k] = S[k]; R.e[k] = e[k]; R.x[k] = x[k]; R.z[k] = z[k];
+    R.inv_e[k] = e[k] != 0.0 ? 1.0 / e[k] : 0.0;
+  }
 
   // entry A / exit B on the grid prism (slab method)
   double blo[3] = {G.ox, G.oy, G.oz};
@@ -220,6 +224,7 @@ __global__ void __launch_bounds__(32 * kSiddonWarps) k_siddon(const DInst* __res
   const double* e = R.e;
   const double org[3] = {G.ox, G.oy, G.oz};
   const double sp[3] = {G.dx, G.dy, G.dz};
+  const double isp[3] = {G.idx, G.idy, G.idz};
   const int nv[3] = {G.nx, G.ny, G.nz};
   double total = 0.0;
   if (k0 < k1) {
@@ -228,16 +233,17 @@ __global__ void __launch_bounds__(32 * kSiddonWarps) k_siddon(const DInst* __res
     double alpha[3], dalpha[3];
     for (int a = 0; a < 3; ++a) {
       double p = fma(tcur, e[a], S[a]);
-      int i = (int)floor((p - org[a]) / sp[a]);
+      int i = (int)floor((p - org[a]) * isp[a]);
       idx[a] = min(max(i, 0), nv[a] - 1);
+      const double ie = R.inv_e[a];
       if (e[a] > 0.0) {
         step[a] = 1;
-        alpha[a] = (org[a] + (idx[a] + 1) * sp[a] - S[a]) / e[a];
-        dalpha[a] = sp[a] / e[a];
+        alpha[a] = (org[a] + (idx[a] + 1) * sp[a] - S[a]) * ie;
+        dalpha[a] = sp[a] * ie;
       } else if (e[a] < 0.0) {
         step[a] = -1;
-        alpha[a] = (org[a] + idx[a] * sp[a] - S[a]) / e[a];
-        dalpha[a] = -sp[a] / e[a];
+        alpha[a] = (org[a] + idx[a] * sp[a] - S[a]) * ie;
+        dalpha[a] = -sp[a] * ie;
       } else {
         step[a] = 0;
         alpha[a] = CUDART_INF;
@@ -281,8 +287,7 @@ __global__ void __launch_bounds__(32 * kSiddonWarps) k_siddon(const DInst* __res
 // ---------------------------------------------------------------------------
 struct LineSm {
   int lo[kMaxLinesPerItem];
-  int iy[kMaxLinesPerItem];
-  int iz[kMaxLinesPerItem];
+  int colbase[kMaxLinesPerItem];      // nx (iy + ny iz) of the line
   int off[kMaxLinesPerItem + 1];
   float sh[kMaxLinesPerItem], sl[kMaxLinesPerItem];
   float xh[kMaxLinesPerItem], xl[kMaxLinesPerItem];
@@ -363,31 +368,55 @@ __device__ __forceinline__ int block_excl_scan(int v, int& excl, int* wscan) {
   return tot;
 }
 
-// set up all lines of an item in shared memory; returns the candidate count
-__device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, long long chunk) {
+// line (iy, iz) of line index l of row R
+__device__ __forceinline__ void line_yz(const DRow& R, long long l, int& iy, int& iz) {
   int nyb = R.iy1 - R.iy0 + 1;
-  long long nlines = (long long)nyb * (R.iz1 - R.iz0 + 1);
-  long long l0 = chunk * R.lpc;
-  int nl = (int)min((long long)R.lpc, nlines - l0);
-  int len = 0;
+  iz = R.iz0 + (int)(l / nyb);
+  iy = R.iy0 + (int)(l - (long long)(iz - R.iz0) * nyb);
+}
+
+// lines of a work item: [chunk * lpc, min(+lpc, lines of the row))
+__device__ __forceinline__ int item_nlines(const DRow& R, long long chunk, long long& l0) {
+  long long nlines = (long long)(R.iy1 - R.iy0 + 1) * (R.iz1 - R.iz0 + 1);
+  l0 = chunk * R.lpc;
+  return (int)min((long long)R.lpc, nlines - l0);
+}
+
+// set up all lines of an item in shared memory (each thread takes lines t and
+// t + kEvalThreads); returns the candidate count
+__device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, long long chunk) {
+  constexpr int per = kMaxLinesPerItem / kEvalThreads;
+  long long l0;
+  int nl = item_nlines(R, chunk, l0);
   int t = threadIdx.x;
-  if (t < nl) {
-    long long l = l0 + t;
-    int iz = R.iz0 + (int)(l / nyb);
-    int iy = R.iy0 + (int)(l - (long long)(iz - R.iz0) * nyb);
-    ff s0, x0, z0;
-    int lo;
-    len = line_setup(R, mode, nx, iy, iz, s0, x0, z0, lo);
-    sm.lo[t] = lo;
-    sm.iy[t] = iy;
-    sm.iz[t] = iz;
-    sm.sh[t] = s0.hi; sm.sl[t] = s0.lo;
-    sm.xh[t] = x0.hi; sm.xl[t] = x0.lo;
-    sm.zh[t] = z0.hi; sm.zl[t] = z0.lo;
+  int len[per];
+  int mine = 0;
+#pragma unroll
+  for (int q = 0; q < per; ++q) {
+    int li = t * per + q;             // consecutive lines per thread keep the scan order
+    len[q] = 0;
+    if (li < nl) {
+      int iy, iz;
+      line_yz(R, l0 + li, iy, iz);
+      ff s0, x0, z0;
+      int lo;
+      len[q] = line_setup(R, mode, nx, iy, iz, s0, x0, z0, lo);
+      sm.lo[li] = lo;
+      sm.colbase[li] = nx * (iy + ny * iz);
+      sm.sh[li] = s0.hi; sm.sl[li] = s0.lo;
+      sm.xh[li] = x0.hi; sm.xl[li] = x0.lo;
+      sm.zh[li] = z0.hi; sm.zl[li] = z0.lo;
+    }
+    mine += len[q];
   }
   int excl;
-  int tot = block_excl_scan(len, excl, sm.wscan);
-  if (t < nl) sm.off[t] = excl;
+  int tot = block_excl_scan(mine, excl, sm.wscan);
+#pragma unroll
+  for (int q = 0; q < per; ++q) {
+    int li = t * per + q;
+    if (li < nl) sm.off[li] = excl;
+    excl += len[q];
+  }
   if (t == 0) { sm.nl = nl; sm.off[nl] = tot; }
   __syncthreads();
   return tot;
@@ -406,11 +435,11 @@ __device__ void item_map(LineSm& sm, int w0, int wl) {
   // scatter the starts into a shared buffer (the map itself as scratch)
   for (int j = t; j < kWindow; j += kEvalThreads) sm.map[j] = 0xffff;
   __syncthreads();
-  if (t < nl) {
-    int o = sm.off[t], e = sm.off[t + 1];
+  for (int li = t; li < nl; li += kEvalThreads) {
+    int o = sm.off[li], e = sm.off[li + 1];
     if (e > o) {
-      if (o >= w0 && o < w0 + wl) sm.map[o - w0] = (unsigned short)t;
-      else if (o < w0 && e > w0) sm.map[0] = (unsigned short)t;
+      if (o >= w0 && o < w0 + wl) sm.map[o - w0] = (unsigned short)li;
+      else if (o < w0 && e > w0) sm.map[0] = (unsigned short)li;
     }
   }
   __syncthreads();
@@ -445,34 +474,75 @@ __device__ void item_map(LineSm& sm, int w0, int wl) {
 }
 
 // ---------------------------------------------------------------------------
-// k_count: candidate pairs per work item (persistent over the item queue)
+// k_count: candidate pairs per work item, one warp per item
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict__ inst, const DRow* __restrict__ rows,
                                                         const long long* __restrict__ row_item_base, int nrows,
                                                         const long long* __restrict__ n_items, int* item_cand) {
-  __shared__ LineSm sm;
-  long long ni = *n_items;
-  for (long long item = blockIdx.x; item < ni; item += gridDim.x) {
+  const long long ni = *n_items;
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (kEvalThreads / 32);
+  for (long long item = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5); item < ni; item += nw) {
     int row = row_of_item(row_item_base, nrows, item);
     const DRow& R = rows[row];
     const DInst& G = inst[R.inst];
-    int tot = item_lines(sm, R, G.cutoff_mode, G.nx, item - row_item_base[row]);
-    if (threadIdx.x == 0) item_cand[item] = tot;
-    __syncthreads();
+    long long l0;
+    int nl = item_nlines(R, item - row_item_base[row], l0);
+    int cnt = 0;
+    for (int li = lane; li < nl; li += 32) {
+      int iy, iz;
+      line_yz(R, l0 + li, iy, iz);
+      ff s0, x0, z0;
+      int lo;
+      cnt += line_setup(R, G.cutoff_mode, G.nx, iy, iz, s0, x0, z0, lo);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) item_cand[item] = cnt;
   }
 }
 
 // ---------------------------------------------------------------------------
 // FSPB evaluation (Eq. 2-3)
 // ---------------------------------------------------------------------------
-// erf(u1) + erf(u2) for u1 = (h - |x'|)/s, u2 = (h + |x'|)/s with h >= 0:
-// in the tails the erfc form avoids the cancellation of 1 - erf
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// erfc(u) for u >= 0, given v = u sqrt(log2 e):  t exp(-u^2) P(t) with
+// t = 1/(1 + p u) (coefficients from fit_erfc.py) and exp(-u^2) = 2^(-v^2),
+// v^2 split exactly into vh + vl so the exponent carries no rounding
+__device__ __forceinline__ float erfc_v(float v) {
+  constexpr float kInvSqrtL = 0.83255461115769775635f;   // 1 / sqrt(log2 e)
+  constexpr float kLn2 = 0.69314718055994530942f;
+  float t = rcp_approx(fmaf(kErfcP * kInvSqrtL, v, 1.0f));
+  float p = kErfcC[kErfcN];
+#pragma unroll
+  for (int k = kErfcN - 1; k >= 0; --k) p = fmaf(p, t, kErfcC[k]);
+  float vh = __fmul_rn(v, v);
+  float vl = fmaf(v, v, -vh);
+  float e = ex2_approx(-vh);
+  e = fmaf(e, -vl * kLn2, e);
+  return (t * p) * e;
+}
+
+// erf(u1) + erf(u2) for u1 = (h - |x'|)/s, u2 = (h + |x'|)/s (h >= 0), from
+// the scaled arguments v = u sqrt(log2 e): inside the beamlet
+// 2 - erfc(u1) - erfc(u2), outside erfc(|u1|) - erfc(u2) (no cancellation of
+// 1 - erf in the tails)
 __device__ __forceinline__ float erf_pair(float h, float ax, float inv_s) {
-  float u1 = (h - ax) * inv_s;
-  float u2 = (h + ax) * inv_s;
-  if (u1 >= 0.5f) return (2.0f - erfcf(u1)) - erfcf(u2);
-  if (u1 <= -0.5f) return erfcf(-u1) - erfcf(u2);
-  return erff(u1) + erff(u2);
+  float v1 = (h - ax) * inv_s;
+  float v2 = (h + ax) * inv_s;
+  float e1 = erfc_v(fabsf(v1));
+  float e2 = erfc_v(v2);
+  return v1 >= 0.0f ? (2.0f - e1) - e2 : e1 - e2;
 }
 
 struct RowConst {
@@ -539,13 +609,14 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, const DInst& G, co
     float lim = G.cutoff_k * P.y;
     if (ax > fmaf(0.5f, a_t, lim) || az > fmaf(0.5f, b_t, lim)) return -1.0f;
   }
-  // Eq. 3: three erf-pair products
-  const float kSqrt2 = 1.41421356237309515f;
+  // Eq. 3: three erf-pair products; arguments scaled by sqrt(log2 e):
+  // 1/(sqrt(2) c3) * sqrt(log2 e) = sqrt(log2(e)/2) / c3
+  constexpr float kSqrtHalfL = 0.84932180028801904272f;
   float c3[3] = {P.y, P.z, P.w};
   float F = 0.0f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    float inv_s = __frcp_rn(kSqrt2 * c3[i]);
+    float inv_s = kSqrtHalfL * __frcp_rn(c3[i]);
     float X = erf_pair(G.c2h[i] * a_t, ax, inv_s);
     float Z = erf_pair(G.c2h[i] * b_t, az, inv_s);
     F = fmaf(G.c1q[i] * X, Z, F);
@@ -588,21 +659,23 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalParams p) {
     const DRow& R = p.rows[row];
     const DInst& G = p.inst[R.inst];
     const int mode = G.cutoff_mode;
-    const int total = item_lines(sm, R, mode, G.nx, item - p.row_item_base[row]);
+    const int total = item_lines(sm, R, mode, G.nx, G.ny, item - p.row_item_base[row]);
     RowConst C;
     load_row_const(C, R, G);
     const float* tab = p.tables + (size_t)row * p.table_stride;
     float* out = p.vals + p.item_off[item];
+    int* outc = p.cols + p.item_off[item];
     float vmax = 0.0f;
     for (int w0 = 0; w0 < total; w0 += kWindow) {
       int wl = min(kWindow, total - w0);
       item_map(sm, w0, wl);
       for (int j = threadIdx.x; j < wl; j += kEvalThreads) {
         int li = min((int)sm.map[j], sm.nl - 1);
-        int k = w0 + j - sm.off[li];
-        float fi = (float)(sm.lo[li] + k);
-        float D = eval_pair(C, G, tab, fi, sm.sh[li], sm.sl[li], sm.xh[li], sm.xl[li], sm.zh[li], sm.zl[li], mode);
+        int ix = sm.lo[li] + (w0 + j - sm.off[li]);
+        float D = eval_pair(C, G, tab, (float)ix, sm.sh[li], sm.sl[li], sm.xh[li], sm.xl[li], sm.zh[li], sm.zl[li],
+                            mode);
         out[w0 + j] = D;
+        outc[w0 + j] = sm.colbase[li] + ix;
         vmax = fmaxf(vmax, D);
       }
       __syncthreads();
@@ -635,79 +708,81 @@ __global__ void k_beam_scale(const DBeam* __restrict__ beams, int nbeams, const 
 // ---------------------------------------------------------------------------
 
 
+// kept = D > 0 and D >= tau * row max; one warp per item, 8 loads in
+// flight per lane
 __global__ void __launch_bounds__(kEvalThreads) k_compact_count(CompactParams p) {
-  __shared__ int ws[kEvalThreads / 32];
-  __shared__ int ws2[kEvalThreads / 32];
-  long long ni = *p.n_items;
-  for (long long item = blockIdx.x; item < ni; item += gridDim.x) {
+  const long long ni = *p.n_items;
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (kEvalThreads / 32);
+  for (long long item = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5); item < ni; item += nw) {
     int row = row_of_item(p.row_item_base, p.nrows, item);
     float thr = p.tau * __uint_as_float(p.row_max[row]);
     long long a = p.item_off[item], b = p.item_off[item + 1];
     int kept = 0, valid = 0;
-    for (long long i = a + threadIdx.x; i < b; i += kEvalThreads) {
-      float D = p.vals[i];
-      kept += (D > 0.0f && D >= thr);
-      valid += (D >= 0.0f);
+    for (long long i0 = a; i0 < b; i0 += 8 * 32) {
+      float D[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        long long i = i0 + u * 32 + lane;
+        D[u] = i < b ? __ldcs(p.vals + i) : -1.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        kept += (D[u] > 0.0f && D[u] >= thr);
+        valid += (D[u] >= 0.0f);
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       kept += __shfl_xor_sync(0xffffffffu, kept, o);
       valid += __shfl_xor_sync(0xffffffffu, valid, o);
     }
-    if ((threadIdx.x & 31) == 0) { ws[threadIdx.x >> 5] = kept; ws2[threadIdx.x >> 5] = valid; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int k = 0, v = 0;
-      for (int i = 0; i < kEvalThreads / 32; ++i) { k += ws[i]; v += ws2[i]; }
-      p.item_kept[item] = k;
-      if (v) atomicAdd((unsigned long long*)(p.row_cand + row), (unsigned long long)v);
+    if (lane == 0) {
+      p.item_kept[item] = kept;
+      if (valid) atomicAdd((unsigned long long*)(p.row_cand + row), (unsigned long long)valid);
     }
-    __syncthreads();
   }
 }
 
+// CSR columns and values: each warp compacts one item in candidate order
+// (ascending voxel index) with ballots; 8 x 32 candidates per round
 __global__ void __launch_bounds__(kEvalThreads) k_compact_write(CompactParams p) {
-  __shared__ LineSm sm;
-  long long ni = *p.n_items;
-  for (long long item = blockIdx.x; item < ni; item += gridDim.x) {
+  const long long ni = *p.n_items;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long nw = (long long)gridDim.x * (kEvalThreads / 32);
+  int* col = p.slot->col;
+  void* valp = p.slot->val;
+  for (long long item = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5); item < ni; item += nw) {
     int row = row_of_item(p.row_item_base, p.nrows, item);
-    const DRow& R = p.rows[row];
-    const DInst& G = p.inst[R.inst];
-    int total = item_lines(sm, R, G.cutoff_mode, G.nx, item - p.row_item_base[row]);
     float thr = p.tau * __uint_as_float(p.row_max[row]);
     float scale = 1.0f;
-    if (p.value_dtype == 1) scale = p.slot->beam_scale[R.beam];
-    int* col = p.slot->col;
-    void* valp = p.slot->val;
-    const float* v = p.vals + p.item_off[item];
-    long long outb = p.item_out[item];
-    int written = 0;
-    for (int w0 = 0; w0 < total; w0 += kWindow) {
-      int wl = min(kWindow, total - w0);
-      item_map(sm, w0, wl);
-      for (int j0 = 0; j0 < wl; j0 += kEvalThreads) {
-        int j = j0 + threadIdx.x;
-        float D = 0.0f;
-        int keep = 0;
-        if (j < wl) {
-          D = v[w0 + j];
-          keep = (D > 0.0f && D >= thr);
-        }
-        int excl;
-        int tot = block_excl_scan(keep, excl, sm.wscan);
-        if (keep) {
-          int li = min((int)sm.map[j], sm.nl - 1);
-          int ix = sm.lo[li] + (w0 + j - sm.off[li]);
-          long long o = outb + written + excl;
-          col[o] = ix + G.nx * (sm.iy[li] + G.ny * sm.iz[li]);
-          if (p.value_dtype == 1)
-            ((__nv_bfloat16*)valp)[o] = __float2bfloat16_rn(__fdiv_rn(D, scale));
-          else
-            ((float*)valp)[o] = D;
-        }
-        written += tot;
+    if (p.value_dtype == 1) scale = p.slot->beam_scale[p.rows[row].beam];
+    long long a = p.item_off[item], b = p.item_off[item + 1];
+    long long o = p.item_out[item];
+    for (long long i0 = a; i0 < b; i0 += 8 * 32) {
+      float D[8];
+      int C[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        long long i = i0 + u * 32 + lane;
+        D[u] = i < b ? __ldcs(p.vals + i) : -1.0f;
+        C[u] = i < b ? __ldcs(p.cols + i) : 0;
       }
-      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        bool keep = D[u] > 0.0f && D[u] >= thr;
+        unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          long long q = o + __popc(m & lt);
+          col[q] = C[u];
+          if (p.value_dtype == 1)
+            ((__nv_bfloat16*)valp)[q] = __float2bfloat16_rn(__fdiv_rn(D[u], scale));
+          else
+            ((float*)valp)[q] = D[u];
+        }
+        o += __popc(m);
+      }
     }
   }
 }

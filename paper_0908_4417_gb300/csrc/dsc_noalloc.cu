@@ -141,6 +141,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   I.n_lut = model->n;
   I.dx = grid->dx; I.dy = grid->dy; I.dz = grid->dz;
   I.ox = grid->origin[0]; I.oy = grid->origin[1]; I.oz = grid->origin[2];
+  I.idx = 1.0 / I.dx; I.idy = 1.0 / I.dy; I.idz = 1.0 / I.dz;
   I.lut_scale = (float)((model->n - 1) / model->d_max);
   float c3max = 0.f;
   for (int k = 0; k < model->n; ++k) {
@@ -256,7 +257,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   NA_CU(cudaMemcpyAsync(&n_cand, d_item_off + n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
   NA_CU(cudaStreamSynchronize(s));
   float* d_vals = cv.take<float>(n_cand);
-  if (!d_vals)
+  int* d_cols = cv.take<int>(n_cand);
+  if (!d_cols)
     return na_fail(DSC_E_INVAL, "needs %zu bytes of working memory for %lld candidate pairs; the fixed maximum is %zu",
                    cv.need, n_cand, kNoAllocBytes);
 
@@ -271,6 +273,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   ep.item_off = d_item_off;
   ep.n_items = n_items_dev;
   ep.vals = d_vals;
+  ep.cols = d_cols;
   ep.row_max = d_row_max;
   ep.item_counter = d_counter;
   k_eval<<<grid_eval, kEvalThreads, 0, s>>>(ep);
@@ -283,6 +286,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.item_off = d_item_off;
   cp.n_items = n_items_dev;
   cp.vals = d_vals;
+  cp.cols = d_cols;
   cp.row_max = d_row_max;
   cp.tau = (float)opts->rel_threshold;
   cp.item_kept = d_item_kept;

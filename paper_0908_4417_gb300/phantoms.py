@@ -257,13 +257,15 @@ def prostate_density(g: Grid, seed: int, scale_x: float = 1.0, scale_y: float = 
     return np.maximum(rho, 0.0).astype(np.float32)
 
 
-def prostate_256(seed: int = 20090908) -> Workload:
-    """256x256x100 at 2x2x2.5 mm, 9 fields at 0,40,...,320 deg, 16x16 beamlets of 5 mm."""
+def prostate_256(seed: int = 20090908, fields: int = 9) -> Workload:
+    """256x256x100 at 2x2x2.5 mm, 9 fields at 0,40,...,320 deg, 16x16 beamlets of 5 mm
+    (the first `fields` of them)."""
     g = centred_grid(256, 256, 100, 2.0, 2.0, 2.5)
     rho = prostate_density(g, seed)
     m = synthetic_model(cutoff_mode=CUTOFF_VOI6)
-    beams = [Beam(40.0 * k, 1000.0, (0.0, 0.0, 0.0), 5.0, 5.0, 16, 16) for k in range(9)]
-    return Workload("prostate_256", g, rho, m, beams)
+    beams = [Beam(40.0 * k, 1000.0, (0.0, 0.0, 0.0), 5.0, 5.0, 16, 16) for k in range(fields)]
+    name = "prostate_256" if fields == 9 else f"prostate_256_{fields}f"
+    return Workload(name, g, rho, m, beams)
 
 
 def batched_instance(seed: int) -> Workload:
@@ -320,6 +322,7 @@ WORKLOADS = {
     "water_32": water_32,
     "slabs_128": slabs_128,
     "prostate_256": prostate_256,
+    "prostate_256_2f": lambda: prostate_256(fields=2),
 }
 
 
