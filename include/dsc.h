@@ -187,8 +187,9 @@ dsc_status dsc_get_beamlets(dsc_result* res, double* out, int64_t cap_rows);
 dsc_status dsc_get_depth_tables(dsc_result* res, float* out, int64_t cap, int32_t* n_max_out);
 /* Per row: max D over the row's candidates and the candidate count. */
 dsc_status dsc_get_row_stats(dsc_result* res, float* row_max, int64_t* row_cand);
-/* Milliseconds per stage (needs DSC_FLAG_TIMING): [setup, siddon, count+scan,
- * eval, beam-scale, compact count+scan, compact write, total]. n >= 8. */
+/* Milliseconds per stage (needs DSC_FLAG_TIMING): [set-up + item scan, Siddon
+ * tables, candidate count + scan, evaluation, beam scale, compaction, row
+ * pointers + statistics, total]. n >= 8. */
 dsc_status dsc_get_stage_times(dsc_result* res, float* ms, int32_t n);
 
 /* --- serving: continuous batching of re-plan requests -------------------- */

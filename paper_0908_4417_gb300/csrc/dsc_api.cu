@@ -34,12 +34,15 @@ namespace dsc {
 // kernels (dsc_kernels.cu)
 __global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
-__global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*);
+__global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*, const int*);
+__global__ void k_item_rows(const long long*, int, int*);
+__global__ void k_tile_map(const long long*, const long long*, long long, long long*, long long*);
 __global__ void k_eval(EvalParams);
 __global__ void k_beam_scale(const DBeam*, int, const unsigned*, const OutSlot*);
-__global__ void k_compact_count(CompactParams);
-__global__ void k_compact_write(CompactParams);
-__global__ void k_row_ptr(const long long*, const long long*, int, int, long long, int, int, const OutSlot*);
+__global__ void k_tile_count(CompactParams, int*);
+__global__ void k_tile_write(CompactParams, const long long*);
+__global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
+                          long long, int, int, long long, int, int, const OutSlot*);
 __global__ void k_copy_stats(const unsigned*, const long long*, int, const OutSlot*);
 __global__ void k_scan_partial(const int*, const long long*, long long, long long*);
 __global__ void k_scan_blocks(long long*);
@@ -133,10 +136,11 @@ struct Plan;
 struct OutBufs {
   int device = 0;
   cudaEvent_t done = nullptr;        // end of the computation that writes these buffers
-  OutSlot slot{};                    // row_ptr, col, val, beam_scale, row_max, row_cand, inst_begin
+  OutSlot slot{};                    // row_ptr, col, val, beam_scale, row_max, row_cand, inst_begin, status
   ~OutBufs() {
-    void* ps[] = {slot.row_ptr, slot.col, slot.val, slot.beam_scale, slot.row_max, slot.row_cand, slot.inst_begin};
-    release_after(done, device, ps, 7);
+    void* ps[] = {slot.row_ptr, slot.col, slot.val, slot.beam_scale, slot.row_max, slot.row_cand, slot.inst_begin,
+                  slot.status};
+    release_after(done, device, ps, 8);
     if (done) cudaEventDestroy(done);
   }
 };
@@ -192,9 +196,14 @@ struct Plan {
   long long* d_row_item_base = nullptr;
   float* d_tables = nullptr;
   int* d_item_cand = nullptr;
+  int* d_item_row = nullptr;
   long long* d_item_off = nullptr;
-  int* d_item_kept = nullptr;
   long long* d_item_out = nullptr;
+  int* d_tile_cnt = nullptr;
+  long long* d_tile_off = nullptr;   // n_tiles + 1
+  long long* d_tile_item0 = nullptr;
+  long long* d_tile_first = nullptr;
+  long long n_tiles = 0;
   float* d_vals = nullptr;
   int* d_cols = nullptr;
   unsigned* d_row_max = nullptr;
@@ -210,10 +219,11 @@ struct Plan {
   int kernels_per_run = 0;           // kernel launches in one computation
   std::mutex mu;                     // one computation at a time per plan
   void free_scratch() {
-    void* ps[] = {d_item_cand, d_item_off, d_item_kept, d_item_out, d_vals, d_cols};
-    release_after(last_done, device, ps, 6);
-    d_item_cand = nullptr; d_item_off = nullptr; d_item_kept = nullptr; d_item_out = nullptr; d_vals = nullptr;
-    d_cols = nullptr;
+    void* ps[] = {d_item_cand, d_item_off, d_tile_cnt, d_tile_off, d_item_out, d_vals, d_cols, d_item_row,
+                  d_tile_item0, d_tile_first};
+    release_after(last_done, device, ps, 10);
+    d_item_cand = nullptr; d_item_off = nullptr; d_tile_cnt = nullptr; d_tile_off = nullptr; d_item_out = nullptr;
+    d_vals = nullptr; d_cols = nullptr; d_item_row = nullptr; d_tile_item0 = nullptr; d_tile_first = nullptr;
     if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
   }
   ~Plan() {
@@ -506,8 +516,8 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   CU(cudaMemcpyAsync(&P->n_items, P->d_row_item_base + P->nrows, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   TRY(dalloc(&P->d_item_cand, P->n_items, s));
+  TRY(dalloc(&P->d_item_row, P->n_items, s));
   TRY(dalloc(&P->d_item_off, P->n_items + 1, s));
-  TRY(dalloc(&P->d_item_kept, P->n_items, s));
   TRY(dalloc(&P->d_item_out, P->n_items + 1, s));
   int sms = 0, nb = 0;
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
@@ -515,14 +525,21 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   P->grid_eval = std::max(1, nb) * sms;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count, kEvalThreads, 0));
   P->grid_items = std::max(1, nb) * sms;
+  k_item_rows<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_row_item_base, P->nrows, P->d_item_row);
+  CHECK_LAUNCH();
   k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, P->d_row_item_base, P->nrows,
-                                                 P->d_row_item_base + P->nrows, P->d_item_cand);
+                                                 P->d_row_item_base + P->nrows, P->d_item_cand, P->d_item_row);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_item_cand, P->d_row_item_base + P->nrows, 0, P->d_scan, P->d_item_off, s));
   CU(cudaMemcpyAsync(&P->n_cand, P->d_item_off + P->n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
-  TRY(dalloc(&P->d_vals, P->n_cand, s));
-  TRY(dalloc(&P->d_cols, P->n_cand, s));
+  P->n_tiles = (P->n_cand + kTile - 1) / kTile;
+  TRY(dalloc(&P->d_vals, P->n_cand + 4, s));
+  TRY(dalloc(&P->d_cols, P->n_cand + 4, s));
+  TRY(dalloc(&P->d_tile_cnt, P->n_tiles, s));
+  TRY(dalloc(&P->d_tile_off, P->n_tiles + 1, s));
+  TRY(dalloc(&P->d_tile_item0, P->n_tiles, s));
+  TRY(dalloc(&P->d_tile_first, P->n_tiles, s));
   out = P;
   return DSC_OK;
 }
@@ -550,7 +567,7 @@ static dsc_status plan_get(dsc_geometry* const* geoms, int n, const dsc_compute_
 // ---------------------------------------------------------------------------
 // the launch sequence of one computation (stream-ordered, graph-capturable)
 // ---------------------------------------------------------------------------
-enum { ST_SETUP, ST_SIDDON, ST_COUNT, ST_EVAL, ST_SCALE, ST_CCOUNT, ST_CWRITE, ST_N };
+enum { ST_SETUP, ST_SIDDON, ST_COUNT, ST_EVAL, ST_SCALE, ST_COMPACT, ST_FINISH, ST_N };
 
 static dsc_status record(EventSet* ev, int i, cudaStream_t s) {
   if (ev) CU(cudaEventRecord(ev->ev[i], s));
@@ -571,15 +588,18 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s));
   TRY(record(ev, 1, s));
   // a2: radiological-depth tables
-  k_siddon<<<(P->nrows + kSiddonWarps - 1) / kSiddonWarps, 32 * kSiddonWarps, 0, s>>>(P->d_inst, P->d_rows, P->nrows,
-                                                                                      P->d_tables, P->stride);
+  k_siddon<<<P->nrows, kSiddonThreads, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride);
   CHECK_LAUNCH();
   TRY(record(ev, 2, s));
   // a3: candidate pairs per work item
+  k_item_rows<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_row_item_base, P->nrows, P->d_item_row);
+  CHECK_LAUNCH();
   k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, P->d_row_item_base, P->nrows, n_items,
-                                                 P->d_item_cand);
+                                                 P->d_item_cand, P->d_item_row);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_item_cand, n_items, 0, P->d_scan, P->d_item_off, s));
+  k_tile_map<<<256, 256, 0, s>>>(P->d_item_off, n_items, P->n_cand, P->d_tile_item0, P->d_tile_first);
+  CHECK_LAUNCH();
   TRY(record(ev, 3, s));
   // a4: FSPB evaluation
   EvalParams ep;
@@ -590,10 +610,12 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   ep.row_item_base = P->d_row_item_base;
   ep.nrows = P->nrows;
   ep.item_off = P->d_item_off;
+  ep.item_row = P->d_item_row;
   ep.n_items = n_items;
   ep.vals = P->d_vals;
   ep.cols = P->d_cols;
   ep.row_max = P->d_row_max;
+  ep.row_cand = P->d_row_cand;
   ep.item_counter = P->d_counter;
   k_eval<<<P->grid_eval, kEvalThreads, 0, s>>>(ep);
   CHECK_LAUNCH();
@@ -604,32 +626,33 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
     CHECK_LAUNCH();
   }
   TRY(record(ev, 5, s));
-  // a5: threshold + CSR compaction
+  // a5: threshold + CSR compaction: kept count per tile, scan, write
   CompactParams cp;
-  cp.inst = P->d_inst;
   cp.rows = P->d_rows;
-  cp.row_item_base = P->d_row_item_base;
-  cp.nrows = P->nrows;
   cp.item_off = P->d_item_off;
+  cp.item_row = P->d_item_row;
   cp.n_items = n_items;
+  cp.n_cand = P->n_cand;
   cp.vals = P->d_vals;
   cp.cols = P->d_cols;
   cp.row_max = P->d_row_max;
   cp.tau = (float)P->opts.rel_threshold;
-  cp.item_kept = P->d_item_kept;
-  cp.row_cand = P->d_row_cand;
   cp.item_out = P->d_item_out;
+  cp.tile_item0 = P->d_tile_item0;
+  cp.tile_first = P->d_tile_first;
   cp.value_dtype = P->opts.value_dtype;
   cp.slot = P->d_slot;
-  k_compact_count<<<P->grid_items, kEvalThreads, 0, s>>>(cp);
+  const unsigned tiles = (unsigned)std::max<long long>(1, P->n_tiles);
+  k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_cnt);
   CHECK_LAUNCH();
-  TRY(scan_launch(P->d_item_kept, n_items, 0, P->d_scan, P->d_item_out, s));
+  TRY(scan_launch(P->d_tile_cnt, nullptr, P->n_tiles, P->d_scan, P->d_tile_off, s));
+  k_tile_write<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_off);
+  CHECK_LAUNCH();
   TRY(record(ev, 6, s));
-  k_compact_write<<<P->grid_items, kEvalThreads, 0, s>>>(cp);
-  CHECK_LAUNCH();
   for (int k = 0; k < P->ninst; ++k) {
     const DInst& I = P->h_inst[k];
-    k_row_ptr<<<(I.nrows + 1 + 255) / 256, 256, 0, s>>>(P->d_row_item_base, P->d_item_out, I.row_base, I.nrows,
+    k_row_ptr<<<(I.nrows + 1 + 255) / 256, 256, 0, s>>>(P->d_row_item_base, P->d_item_off, P->d_item_out, n_items,
+                                                        P->d_tile_off + P->n_tiles, P->n_cand, I.row_base, I.nrows,
                                                         P->rp_off[k], k, k == P->ninst - 1, P->d_slot);
     CHECK_LAUNCH();
   }
@@ -660,6 +683,8 @@ static dsc_status alloc_outputs(Plan* P, cudaStream_t s, std::shared_ptr<OutBufs
   TRY(dalloc(&q.row_max, P->nrows, s));
   TRY(dalloc(&q.row_cand, P->nrows, s));
   TRY(dalloc(&q.inst_begin, P->ninst + 1, s));
+  TRY(dalloc(&q.status, 1, s));
+  CU(cudaMemsetAsync(q.status, 0, sizeof(int), s));
   if (P->opts.value_dtype != DSC_VALUE_BF16) {
     // FP32 values carry no scale (pageable source: staged before the call returns)
     std::vector<float> ones(P->nbeams, 1.0f);
@@ -764,15 +789,22 @@ extern "C" dsc_status dsc_compute_dij_batch(dsc_geometry* const* geoms, int32_t 
 // ---------------------------------------------------------------------------
 // results
 // ---------------------------------------------------------------------------
+static dsc_status check_status(dsc_result* r) {
+  int st = 0;
+  CU(cudaEventSynchronize(r->done));
+  CU(cudaMemcpy(&st, r->out->slot.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) return fail(DSC_E_TIMEOUT, "a bounded device wait expired (status %d); the result is invalid", st);
+  return DSC_OK;
+}
+
 extern "C" dsc_status dsc_result_wait(dsc_result* r) {
   if (!r) return fail(DSC_E_INVAL, "null result");
-  CU(cudaEventSynchronize(r->done));
-  return DSC_OK;
+  return check_status(r);
 }
 
 static dsc_status fetch_counts(dsc_result* r) {
   if (r->have_counts) return DSC_OK;
-  CU(cudaEventSynchronize(r->done));
+  TRY(check_status(r));
   long long be[2];
   CU(cudaMemcpy(&be[0], r->out->slot.inst_begin + r->inst, sizeof(long long), cudaMemcpyDeviceToHost));
   CU(cudaMemcpy(&be[1], r->out->slot.row_ptr + r->rp_off + r->nrows, sizeof(long long), cudaMemcpyDeviceToHost));

@@ -13,7 +13,7 @@ namespace dsc {
 constexpr int kEvalThreads = 256;     // threads per CTA of the evaluation / compaction kernels
 constexpr int kMaxLinesPerItem = 512; // x-lines handled by one work item (multiple of kEvalThreads)
 constexpr int kWindow = 2048;         // candidates mapped to lines per pass of an item
-constexpr int kSiddonWarps = 4;       // rays (warps) per CTA of the depth-table kernel
+constexpr int kSiddonThreads = 128;   // lanes per ray (one CTA) of the depth-table kernel
 constexpr int kScanBlocks = 1024;     // blocks of the device-wide scan
 constexpr int kScanThreads = 256;
 
@@ -82,10 +82,12 @@ struct EvalParams {
   const long long* row_item_base;  // nrows + 1
   int nrows;
   const long long* item_off;       // n_items + 1: first candidate of each item
+  const int* item_row;             // n_items: row of each item
   const long long* n_items;        // device scalar (= row_item_base[nrows])
   float* vals;                     // candidate values (D, or -1 outside the SIGMA cutoff)
   int* cols;                       // candidate voxel indices
   unsigned* row_max;               // float bits, atomicMax
+  long long* row_cand;             // candidates inside the cutoff per row (atomic add)
   int* item_counter;               // persistent-kernel work queue head
 };
 
@@ -100,22 +102,25 @@ struct OutSlot {
   unsigned* row_max;       // per row, float bits
   long long* row_cand;     // per row
   long long* inst_begin;   // per instance: first output slot; [ninst] = total
+  int* status;             // nonzero when a bounded device wait expired
 };
 
+constexpr int kTilePer = 16;                      // candidates per thread of the compaction
+constexpr int kTile = kEvalThreads * kTilePer;    // candidates per compaction tile
+
 struct CompactParams {
-  const DInst* inst;
   const DRow* rows;
-  const long long* row_item_base;
-  int nrows;
-  const long long* item_off;
+  const long long* item_off;      // n_items + 1
+  const int* item_row;
   const long long* n_items;
+  long long n_cand;
   const float* vals;
   const int* cols;
   const unsigned* row_max;
   float tau;
-  int* item_kept;                 // count pass output
-  long long* row_cand;            // candidates inside the cutoff per row (atomic)
-  const long long* item_out;      // write pass: first output slot of each item
+  long long* item_out;            // n_items: kept entries before each item's first candidate
+  const long long* tile_item0;    // per tile: item holding its first candidate
+  const long long* tile_first;    // per tile: first item starting at or after its first candidate
   int value_dtype;
   const OutSlot* slot;
 };

@@ -5,8 +5,9 @@
 //   k_count          candidate pairs per work item                        (VOI, Section 2.1)
 //   k_eval           D_ij = T(d) (SAD/t)^2 F(x', d, z')  (persistent)     (Eq. 2-3)
 //   k_beam_scale     per-beam maximum for BF16 storage
-//   k_compact_count  kept pairs per item (D >= tau * row max)
-//   k_compact_write  CSR columns/values, ascending voxel index
+//   k_tile_count     kept entries (D >= tau * row max) per tile of candidates
+//   k_tile_write     CSR columns/values of the kept entries, tile by tile
+//   k_row_ptr        CSR row pointers per instance
 //   k_scan_*         device-wide exclusive scans with device-side length
 //
 // The evaluation is FP32 with compensated (float-float) voxel coordinates:
@@ -50,6 +51,17 @@ __device__ __forceinline__ ff ff_mul_i(ff a, float n) {
   e = fmaf(a.lo, n, e);
   return quick_two_sum(p, e);
 }
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __host__ __device__ inline ff ff_from_double(double v) {
   float hi = (float)v;
   float lo = (float)(v - (double)hi);
@@ -198,26 +210,28 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// k_siddon: radiological depth table, one warp per beamlet axis.
-// Lane l walks table intervals [l Q, (l+1) Q) with Siddon's incremental
-// plane crossings (alpha in FP64), stores its lane-local cumulative depth,
-// then adds the warp-exclusive prefix of the lane totals.
+// k_siddon: radiological depth table, one CTA of kSiddonThreads lanes per
+// beamlet axis.  Lane l walks the table intervals [l Q, (l+1) Q) with
+// Siddon's incremental plane crossings (alpha in FP64), stores its
+// lane-local cumulative depth, then adds the CTA-exclusive prefix of the
+// lane totals.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kSiddonWarps) k_siddon(const DInst* __restrict__ inst,
-                                                              const DRow* __restrict__ rows, int nrows,
-                                                              float* __restrict__ tables, int stride) {
-  int warp = blockIdx.x * kSiddonWarps + (threadIdx.x >> 5);
-  int lane = threadIdx.x & 31;
-  if (warp >= nrows) return;
-  const DRow& R = rows[warp];
-  int n = R.n_table;
-  if (n <= 0) return;
+__global__ void __launch_bounds__(kSiddonThreads) k_siddon(const DInst* __restrict__ inst,
+                                                            const DRow* __restrict__ rows, int nrows,
+                                                            float* __restrict__ tables, int stride) {
+  __shared__ double wsum[kSiddonThreads / 32];
+  const int ray = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (ray >= nrows) return;
+  const DRow& R = rows[ray];
+  const int n = R.n_table;
+  if (n <= 0) return;                                // uniform over the CTA
   const DInst& G = inst[R.inst];
-  float* tab = tables + (size_t)warp * stride;
-  if (lane == 0) tab[0] = 0.0f;
-  int nint = n - 1;                                  // intervals
-  int Q = (nint + 31) >> 5;
-  int k0 = min(lane * Q, nint), k1 = min(k0 + Q, nint);
+  float* tab = tables + (size_t)ray * stride;
+  if (threadIdx.x == 0) tab[0] = 0.0f;
+  const int nint = n - 1;                            // intervals
+  const int Q = (nint + kSiddonThreads - 1) / kSiddonThreads;
+  const int k0 = min((int)threadIdx.x * Q, nint), k1 = min(k0 + Q, nint);
   const double L = R.tB - R.tA;
   const double h = G.hd;
   const double* S = R.S;
@@ -229,56 +243,77 @@ __global__ void __launch_bounds__(32 * kSiddonWarps) k_siddon(const DInst* __res
   double total = 0.0;
   if (k0 < k1) {
     double tcur = R.tA + fmin(k0 * h, L);
-    int idx[3], step[3];
-    double alpha[3], dalpha[3];
+    // per axis: voxel index, step, next crossing alpha and its increment
+    int i[3], st[3];
+    double al[3], da[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
       double p = fma(tcur, e[a], S[a]);
-      int i = (int)floor((p - org[a]) * isp[a]);
-      idx[a] = min(max(i, 0), nv[a] - 1);
+      int q = (int)floor((p - org[a]) * isp[a]);
+      i[a] = min(max(q, 0), nv[a] - 1);
       const double ie = R.inv_e[a];
       if (e[a] > 0.0) {
-        step[a] = 1;
-        alpha[a] = (org[a] + (idx[a] + 1) * sp[a] - S[a]) * ie;
-        dalpha[a] = sp[a] * ie;
+        st[a] = 1;
+        al[a] = (org[a] + (i[a] + 1) * sp[a] - S[a]) * ie;
+        da[a] = sp[a] * ie;
       } else if (e[a] < 0.0) {
-        step[a] = -1;
-        alpha[a] = (org[a] + idx[a] * sp[a] - S[a]) * ie;
-        dalpha[a] = -sp[a] * ie;
+        st[a] = -1;
+        al[a] = (org[a] + i[a] * sp[a] - S[a]) * ie;
+        da[a] = -sp[a] * ie;
       } else {
-        step[a] = 0;
-        alpha[a] = CUDART_INF;
-        dalpha[a] = 0.0;
+        st[a] = 0;
+        al[a] = CUDART_INF;
+        da[a] = 0.0;
       }
     }
+    // scalar walk state (no dynamically indexed arrays: they would live in local memory)
+    int ix = i[0], iy = i[1], iz = i[2];
+    const int sx = st[0], sy_ = st[1], sz_ = st[2];
+    double ax = al[0], ay = al[1], az = al[2];
+    const double dax = da[0], day = da[1], daz = da[2];
     const float* rho = G.rho;
-    const size_t sy = (size_t)G.nx, sz = (size_t)G.nx * G.ny;
+    const long long ny_s = G.nx, nz_s = (long long)G.nx * G.ny;
+    long long vox = ix + iy * ny_s + iz * nz_s;
+    double rv = (double)__ldg(rho + vox);
     int guard = 4 * (G.nx + G.ny + G.nz) + 8 * (k1 - k0) + 16;
     for (int k = k0; k < k1; ++k) {
       double tend = (k + 1 == nint) ? R.tB : R.tA + fmin((k + 1) * h, L);
       for (;;) {
-        double am = fmin(alpha[0], fmin(alpha[1], alpha[2]));
+        double am = fmin(ax, fmin(ay, az));
         if (am >= tend || --guard < 0) break;
-        double len = fmax(am - tcur, 0.0);
-        total = fma(len, (double)__ldg(rho + idx[0] + idx[1] * sy + idx[2] * sz), total);
+        total = fma(fmax(am - tcur, 0.0), rv, total);
         tcur = fmax(tcur, am);
-        int a = (alpha[0] == am) ? 0 : ((alpha[1] == am) ? 1 : 2);
-        idx[a] = min(max(idx[a] + step[a], 0), nv[a] - 1);
-        alpha[a] += dalpha[a];
+        if (ax == am) {
+          int n2 = ix + sx;
+          if (n2 >= 0 && n2 < G.nx) { ix = n2; vox += sx; }
+          ax += dax;
+        } else if (ay == am) {
+          int n2 = iy + sy_;
+          if (n2 >= 0 && n2 < G.ny) { iy = n2; vox += sy_ * ny_s; }
+          ay += day;
+        } else {
+          int n2 = iz + sz_;
+          if (n2 >= 0 && n2 < G.nz) { iz = n2; vox += sz_ * nz_s; }
+          az += daz;
+        }
+        rv = (double)__ldg(rho + vox);
       }
-      double len = fmax(tend - tcur, 0.0);
-      total = fma(len, (double)__ldg(rho + idx[0] + idx[1] * sy + idx[2] * sz), total);
+      total = fma(fmax(tend - tcur, 0.0), rv, total);
       tcur = fmax(tcur, tend);
       tab[k + 1] = (float)total;                     // lane-local, fixed below
     }
   }
-  // exclusive prefix of the lane totals
+  // exclusive prefix of the lane totals over the CTA
   double incl = total;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     double v = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += v;
   }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
   double prefix = incl - total;
+  for (int i = 0; i < w; ++i) prefix += wsum[i];
   for (int k = k0; k < k1; ++k) tab[k + 1] = (float)(prefix + (double)tab[k + 1]);
 }
 
@@ -286,12 +321,9 @@ __global__ void __launch_bounds__(32 * kSiddonWarps) k_siddon(const DInst* __res
 // x-lines of a work item
 // ---------------------------------------------------------------------------
 struct LineSm {
-  int lo[kMaxLinesPerItem];
-  int colbase[kMaxLinesPerItem];      // nx (iy + ny iz) of the line
+  float4 sx[kMaxLinesPerItem];        // s hi, s lo, x' hi, x' lo at ix = 0
+  float4 zc[kMaxLinesPerItem];        // z' hi, z' lo, first ix (int bits), nx (iy + ny iz) (int bits)
   int off[kMaxLinesPerItem + 1];
-  float sh[kMaxLinesPerItem], sl[kMaxLinesPerItem];
-  float xh[kMaxLinesPerItem], xl[kMaxLinesPerItem];
-  float zh[kMaxLinesPerItem], zl[kMaxLinesPerItem];
   int wscan[kEvalThreads / 32];
   unsigned short map[kWindow];
   long long item;
@@ -314,8 +346,9 @@ __device__ __forceinline__ int line_setup(const DRow& R, int mode, int nx, int i
   float lo = 0.0f, hi = (float)(nx - 1);
   bool empty = false;
   auto constrain = [&](float c, float r) {
-    if (c > 0.0f) hi = fminf(hi, __fdiv_rn(r, c));
-    else if (c < 0.0f) lo = fmaxf(lo, __fdiv_rn(r, c));
+    float q = r * rcp_approx(c);
+    if (c > 0.0f) hi = fminf(hi, q);
+    else if (c < 0.0f) lo = fmaxf(lo, q);
     else if (r < 0.0f) empty = true;
   };
   if (mode != 2) {
@@ -325,8 +358,8 @@ __device__ __forceinline__ int line_setup(const DRow& R, int mode, int nx, int i
     constrain(fmaf(-R.kz, tx, -zx), fmaf(R.kz, T0, R.bz) + Z0);
   } else {
     // t > 0 (voxels in front of the source)
-    if (tx > 0.0f) lo = fmaxf(lo, floorf(__fdiv_rn(-T0, tx)) + 1.0f);
-    else if (tx < 0.0f) hi = fminf(hi, ceilf(__fdiv_rn(-T0, tx)) - 1.0f);
+    if (tx > 0.0f) lo = fmaxf(lo, floorf(-T0 * rcp_approx(tx)) + 1.0f);
+    else if (tx < 0.0f) hi = fminf(hi, ceilf(-T0 * rcp_approx(tx)) - 1.0f);
     else if (T0 <= 0.0f) empty = true;
   }
   int ilo = (int)ceilf(lo), ihi = (int)floorf(hi);
@@ -335,15 +368,6 @@ __device__ __forceinline__ int line_setup(const DRow& R, int mode, int nx, int i
   return ihi - ilo + 1;
 }
 
-// row of an item: last r with row_item_base[r] <= item
-__device__ __forceinline__ int row_of_item(const long long* __restrict__ base, int nrows, long long item) {
-  int lo = 0, hi = nrows - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (__ldg(base + mid) <= item) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 // block-wide exclusive scan of one int per thread (kEvalThreads threads); returns the total
 __device__ __forceinline__ int block_excl_scan(int v, int& excl, int* wscan) {
@@ -401,11 +425,8 @@ __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, l
       ff s0, x0, z0;
       int lo;
       len[q] = line_setup(R, mode, nx, iy, iz, s0, x0, z0, lo);
-      sm.lo[li] = lo;
-      sm.colbase[li] = nx * (iy + ny * iz);
-      sm.sh[li] = s0.hi; sm.sl[li] = s0.lo;
-      sm.xh[li] = x0.hi; sm.xl[li] = x0.lo;
-      sm.zh[li] = z0.hi; sm.zl[li] = z0.lo;
+      sm.sx[li] = make_float4(s0.hi, s0.lo, x0.hi, x0.lo);
+      sm.zc[li] = make_float4(z0.hi, z0.lo, __int_as_float(lo), __int_as_float(nx * (iy + ny * iz)));
     }
     mine += len[q];
   }
@@ -474,16 +495,27 @@ __device__ void item_map(LineSm& sm, int w0, int wl) {
 }
 
 // ---------------------------------------------------------------------------
+// k_item_rows: the row of every work item (rows own items
+// [row_item_base[r], row_item_base[r+1]))
+// ---------------------------------------------------------------------------
+__global__ void k_item_rows(const long long* __restrict__ row_item_base, int nrows, int* item_row) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  for (long long i = row_item_base[r]; i < row_item_base[r + 1]; ++i) item_row[i] = r;
+}
+
+// ---------------------------------------------------------------------------
 // k_count: candidate pairs per work item, one warp per item
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict__ inst, const DRow* __restrict__ rows,
                                                         const long long* __restrict__ row_item_base, int nrows,
-                                                        const long long* __restrict__ n_items, int* item_cand) {
+                                                        const long long* __restrict__ n_items, int* item_cand,
+                                                        const int* __restrict__ item_row) {
   const long long ni = *n_items;
   const int lane = threadIdx.x & 31;
   const long long nw = (long long)gridDim.x * (kEvalThreads / 32);
   for (long long item = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5); item < ni; item += nw) {
-    int row = row_of_item(row_item_base, nrows, item);
+    int row = item_row[item];
     const DRow& R = rows[row];
     const DInst& G = inst[R.inst];
     long long l0;
@@ -505,17 +537,6 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
 // ---------------------------------------------------------------------------
 // FSPB evaluation (Eq. 2-3)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ float ex2_approx(float x) {
-  float r;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
 // erfc(u) for u >= 0, given v = u sqrt(log2 e):  t exp(-u^2) P(t) with
 // t = 1/(1 + p u) (coefficients from fit_erfc.py) and exp(-u^2) = 2^(-v^2),
 // v^2 split exactly into vh + vl so the exponent carries no rounding
@@ -545,68 +566,65 @@ __device__ __forceinline__ float erf_pair(float h, float ax, float inv_s) {
   return v1 >= 0.0f ? (2.0f - e1) - e2 : e1 - e2;
 }
 
+// everything the per-pair evaluation reads, loaded once per work item
 struct RowConst {
-  ff Sx;            // slope of s per ix
+  ff Sx;                 // slope of s per ix
   float Xxh, Xxl, Zxh, Zxl;
   float tA, h, inv_h, sad, a_sad, b_sad;
-  float kx, kz, bx, bz;
   int n_table;
+  const float* tab;      // the row's depth table
+  const float4* lut;     // beam-model table
+  float lut_scale, lut_last;
+  float c1q[3], c2h[3];
+  float cutoff_k;
 };
 
 // D for candidate ix of a line; returns -1 outside the SIGMA cutoff
-__device__ __forceinline__ float eval_pair(const RowConst& C, const DInst& G, const float* __restrict__ tab,
-                                           float fi, float sh, float sl, float xh, float xl, float zh, float zl,
-                                           int mode) {
+__device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 sx, float2 zz, int mode) {
   // s = t - tA in float-float
   float ph = __fmul_rn(fi, C.Sx.hi);
   float pl = fmaf(fi, C.Sx.hi, -ph);
-  ff a = two_sum(sh, ph);
-  float s_lo = __fadd_rn(a.lo, __fadd_rn(pl, fmaf(fi, C.Sx.lo, sl)));
+  ff a = two_sum(sx.x, ph);
+  float s_lo = __fadd_rn(a.lo, __fadd_rn(pl, fmaf(fi, C.Sx.lo, sx.y)));
   float s_hi = a.hi;
-  float xp = fmaf(fi, C.Xxh, xh) + fmaf(fi, C.Xxl, xl);
-  float zp = fmaf(fi, C.Zxh, zh) + fmaf(fi, C.Zxl, zl);
+  float xp = fmaf(fi, C.Xxh, sx.z) + fmaf(fi, C.Xxl, sx.w);
+  float zp = fmaf(fi, C.Zxh, zz.x) + fmaf(fi, C.Zxl, zz.y);
   float t = s_hi + C.tA;
 
-  // radiological depth at O' (Section 2.2): linear interpolation of the table
-  float d;
-  if (s_hi + s_lo <= 0.0f) {
-    d = 0.0f;
-  } else {
-    float kf = floorf(s_hi * C.inv_h);
-    float khh = __fmul_rn(kf, C.h);
-    float khl = fmaf(kf, C.h, -khh);
-    float r = __fadd_rn(__fsub_rn(__fsub_rn(s_hi, khh), khl), s_lo);
-    if (r < 0.0f) { kf -= 1.0f; r += C.h; }
-    else if (r >= C.h) { kf += 1.0f; r -= C.h; }
-    int k = (int)kf;
-    if (k >= C.n_table - 1) {
-      d = __ldg(tab + C.n_table - 1);
-    } else {
-      k = max(k, 0);
-      float f = r * C.inv_h;
-      float d0 = __ldg(tab + k), d1 = __ldg(tab + k + 1);
-      d = fmaf(f, d1 - d0, d0);
-    }
-  }
-  // beam-model table: T(d), c3_1..3(d)
-  float g = fmaxf(d * G.lut_scale, 0.0f);   // also maps a NaN depth to 0
+  // radiological depth at O' (Section 2.2): linear interpolation of the
+  // table; the cell and fraction come from the float-float s.  s <= 0 gives
+  // depth 0 (cell 0, fraction 0), past the last entry the last value.
+  float kf = floorf(s_hi * C.inv_h);
+  float khh = __fmul_rn(kf, C.h);
+  float khl = fmaf(kf, C.h, -khh);
+  float r = __fadd_rn(__fsub_rn(__fsub_rn(s_hi, khh), khl), s_lo);
+  kf = r < 0.0f ? kf - 1.0f : kf;
+  r = r < 0.0f ? r + C.h : r;
+  kf = r >= C.h ? kf + 1.0f : kf;
+  r = r >= C.h ? r - C.h : r;
+  const bool neg = (s_hi + s_lo) <= 0.0f;
+  const bool past = kf >= (float)(C.n_table - 1);
+  int k = neg ? 0 : (past ? C.n_table - 2 : (int)kf);
+  float f = neg ? 0.0f : r * C.inv_h;
+  float d0 = __ldg(C.tab + k), d1 = __ldg(C.tab + k + 1);
+  float d = past ? d1 : fmaf(f, d1 - d0, d0);
+
+  // beam-model table: T(d), c3_1..3(d); past the end, the last row
+  float g = fmaxf(d * C.lut_scale, 0.0f);   // also maps a NaN depth to 0
+  float kl = fminf(floorf(g), C.lut_last - 1.0f);
+  float w = fminf(g - kl, 1.0f);
+  int kk = (int)kl;
+  float4 A = __ldg(C.lut + kk), B = __ldg(C.lut + kk + 1);
   float4 P;
-  if (g >= (float)(G.n_lut - 1)) {
-    P = __ldg(G.lut + G.n_lut - 1);
-  } else {
-    float kl = floorf(g);
-    float w = g - kl;
-    int k = (int)kl;
-    float4 A = __ldg(G.lut + k), B = __ldg(G.lut + k + 1);
-    P.x = fmaf(w, B.x - A.x, A.x);
-    P.y = fmaf(w, B.y - A.y, A.y);
-    P.z = fmaf(w, B.z - A.z, A.z);
-    P.w = fmaf(w, B.w - A.w, A.w);
-  }
+  P.x = fmaf(w, B.x - A.x, A.x);
+  P.y = fmaf(w, B.y - A.y, A.y);
+  P.z = fmaf(w, B.z - A.z, A.z);
+  P.w = fmaf(w, B.w - A.w, A.w);
+
   float a_t = C.a_sad * t, b_t = C.b_sad * t;
   float ax = fabsf(xp), az = fabsf(zp);
   if (mode == 1) {
-    float lim = G.cutoff_k * P.y;
+    float lim = C.cutoff_k * P.y;
     if (ax > fmaf(0.5f, a_t, lim) || az > fmaf(0.5f, b_t, lim)) return -1.0f;
   }
   // Eq. 3: three erf-pair products; arguments scaled by sqrt(log2 e):
@@ -616,17 +634,19 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, const DInst& G, co
   float F = 0.0f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    float inv_s = kSqrtHalfL * __frcp_rn(c3[i]);
-    float X = erf_pair(G.c2h[i] * a_t, ax, inv_s);
-    float Z = erf_pair(G.c2h[i] * b_t, az, inv_s);
-    F = fmaf(G.c1q[i] * X, Z, F);
+    float inv_s = kSqrtHalfL * rcp_approx(c3[i]);
+    float X = erf_pair(C.c2h[i] * a_t, ax, inv_s);
+    float Z = erf_pair(C.c2h[i] * b_t, az, inv_s);
+    F = fmaf(C.c1q[i] * X, Z, F);
   }
-  // Eq. 2 with A = T(d) (SAD/t)^2
-  float q = __fdiv_rn(C.sad, t);
+  // Eq. 2 with A = T(d) (SAD/t)^2; 1/t with one Newton step
+  float it = rcp_approx(t);
+  it = fmaf(it, fmaf(-t, it, 1.0f), it);
+  float q = C.sad * it;
   return P.x * (q * q) * F;
 }
 
-__device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const DInst& G) {
+__device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const DInst& G, const float* tab) {
   C.Sx = R.Ss[0];
   C.Xxh = R.Xs[0].hi; C.Xxl = R.Xs[0].lo;
   C.Zxh = R.Zs[0].hi; C.Zxl = R.Zs[0].lo;
@@ -636,8 +656,13 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
   C.sad = R.sad;
   C.a_sad = R.a_sad;
   C.b_sad = R.b_sad;
-  C.kx = R.kx; C.kz = R.kz; C.bx = R.bx; C.bz = R.bz;
   C.n_table = R.n_table;
+  C.tab = tab;
+  C.lut = G.lut;
+  C.lut_scale = G.lut_scale;
+  C.lut_last = (float)(G.n_lut - 1);
+  for (int i = 0; i < 3; ++i) { C.c1q[i] = G.c1q[i]; C.c2h[i] = G.c2h[i]; }
+  C.cutoff_k = G.cutoff_k;
 }
 
 // persistent: CTAs take work items from a queue; every candidate's D goes to
@@ -650,7 +675,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalParams p) {
     if (threadIdx.x == 0) {
       long long it = atomicAdd(p.item_counter, 1);
       sm.item = it;
-      if (it < ni) sm.row = row_of_item(p.row_item_base, p.nrows, it);
+      if (it < ni) sm.row = p.item_row[it];
     }
     __syncthreads();
     const long long item = sm.item;
@@ -661,29 +686,37 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalParams p) {
     const int mode = G.cutoff_mode;
     const int total = item_lines(sm, R, mode, G.nx, G.ny, item - p.row_item_base[row]);
     RowConst C;
-    load_row_const(C, R, G);
-    const float* tab = p.tables + (size_t)row * p.table_stride;
+    load_row_const(C, R, G, p.tables + (size_t)row * p.table_stride);
     float* out = p.vals + p.item_off[item];
     int* outc = p.cols + p.item_off[item];
     float vmax = 0.0f;
+    int valid = 0;
     for (int w0 = 0; w0 < total; w0 += kWindow) {
       int wl = min(kWindow, total - w0);
       item_map(sm, w0, wl);
       for (int j = threadIdx.x; j < wl; j += kEvalThreads) {
         int li = min((int)sm.map[j], sm.nl - 1);
-        int ix = sm.lo[li] + (w0 + j - sm.off[li]);
-        float D = eval_pair(C, G, tab, (float)ix, sm.sh[li], sm.sl[li], sm.xh[li], sm.xl[li], sm.zh[li], sm.zl[li],
-                            mode);
+        float4 sx = sm.sx[li];
+        float4 zc = sm.zc[li];
+        int ix = __float_as_int(zc.z) + (w0 + j - sm.off[li]);
+        float D = eval_pair(C, (float)ix, sx, make_float2(zc.x, zc.y), mode);
         out[w0 + j] = D;
-        outc[w0 + j] = sm.colbase[li] + ix;
+        outc[w0 + j] = __float_as_int(zc.w) + ix;
         vmax = fmaxf(vmax, D);
+        valid += D >= 0.0f;
       }
       __syncthreads();
     }
-    // block max -> row max
+    // row max and candidates inside the cutoff (one atomic per warp)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if ((threadIdx.x & 31) == 0 && vmax > 0.0f) atomicMax(p.row_max + row, __float_as_uint(vmax));
+    for (int o = 16; o > 0; o >>= 1) {
+      vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      valid += __shfl_xor_sync(0xffffffffu, valid, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (vmax > 0.0f) atomicMax(p.row_max + row, __float_as_uint(vmax));
+      if (valid) atomicAdd((unsigned long long*)(p.row_cand + row), (unsigned long long)valid);
+    }
     __syncthreads();
   }
 }
@@ -704,100 +737,273 @@ __global__ void k_beam_scale(const DBeam* __restrict__ beams, int nbeams, const 
 }
 
 // ---------------------------------------------------------------------------
-// compaction: kept = D > 0 and D >= tau * row max
+// compaction: kept = D > 0 and D >= tau * row max, over tiles of kTile
+// candidates (kTilePer consecutive ones per thread, vector loads):
+//   k_tile_count  kept entries per tile
+//   (scan)        tile output offsets
+//   k_tile_write  block scan within the tile, kept entries staged in shared
+//                 memory and written coalesced; item_out receives the kept
+//                 count before each item's start
 // ---------------------------------------------------------------------------
+struct TileKeep {
+  float D[kTilePer];
+  int C[kTilePer];
+  unsigned keep;
+};
 
+// The items that start before the tile's end, from the one holding its first
+// candidate: their starts relative to the tile (the first may be negative)
+// and thresholds.  Built by all threads; overflow (more starts than entries,
+// e.g. runs of empty items) sends the tile down the global-memory walk.
+constexpr int kTileItems = kEvalThreads;
+struct TileTable {
+  long long start[kTileItems + 1];
+  float thr[kTileItems];
+  float scale[kTileItems];
+  int n;                              // entries in use
+  int overflow;
+};
 
-// kept = D > 0 and D >= tau * row max; one warp per item, 8 loads in
-// flight per lane
-__global__ void __launch_bounds__(kEvalThreads) k_compact_count(CompactParams p) {
+__device__ void tile_table(const CompactParams& p, long long base, long long item0, TileTable& T, bool bf16) {
   const long long ni = *p.n_items;
-  const int lane = threadIdx.x & 31;
-  const long long nw = (long long)gridDim.x * (kEvalThreads / 32);
-  for (long long item = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5); item < ni; item += nw) {
-    int row = row_of_item(p.row_item_base, p.nrows, item);
-    float thr = p.tau * __uint_as_float(p.row_max[row]);
-    long long a = p.item_off[item], b = p.item_off[item + 1];
-    int kept = 0, valid = 0;
-    for (long long i0 = a; i0 < b; i0 += 8 * 32) {
-      float D[8];
+  const long long* __restrict__ off = p.item_off;
+  const int t = threadIdx.x;
+  const long long i = item0 + t;
+  const long long end = base + kTile;
+  bool in = i < ni && (t == 0 || off[i] < end);
+  if (in) {
+    int r = p.item_row[i];
+    T.start[t] = off[i] - base;
+    T.thr[t] = p.tau * __uint_as_float(p.row_max[r]);
+    if (bf16) T.scale[t] = p.slot->beam_scale[p.rows[r].beam];
+  }
+  unsigned b = __ballot_sync(0xffffffffu, in);
+  __shared__ int wcnt[kEvalThreads / 32];
+  if ((t & 31) == 0) wcnt[t >> 5] = __popc(b);
+  __syncthreads();
+  if (t == 0) {
+    int n = 0;
+    for (int k = 0; k < kEvalThreads / 32; ++k) n += wcnt[k];
+    T.n = n;
+    const long long nx = item0 + n;                  // first item after the table
+    T.start[n] = nx < ni ? off[nx] - base : p.n_cand - base;
+    T.overflow = nx < ni && off[nx] < end;
+  }
+  __syncthreads();
+}
+
+// candidates [p0, p0 + kTilePer) and their keep flags
+template <bool kCols>
+__device__ __forceinline__ void tile_keep(const CompactParams& p, long long base, long long p0, long long item0,
+                                          const TileTable& T, TileKeep& K) {
+  const long long n = p.n_cand;
+  if (p0 + kTilePer <= n) {
+    const float4* v4 = reinterpret_cast<const float4*>(p.vals + p0);
+    const int4* c4 = reinterpret_cast<const int4*>(p.cols + p0);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        long long i = i0 + u * 32 + lane;
-        D[u] = i < b ? __ldcs(p.vals + i) : -1.0f;
+    for (int q = 0; q < kTilePer / 4; ++q) {
+      float4 v = __ldcs(v4 + q);
+      K.D[4 * q] = v.x; K.D[4 * q + 1] = v.y; K.D[4 * q + 2] = v.z; K.D[4 * q + 3] = v.w;
+      if (kCols) {
+        int4 c = __ldcs(c4 + q);
+        K.C[4 * q] = c.x; K.C[4 * q + 1] = c.y; K.C[4 * q + 2] = c.z; K.C[4 * q + 3] = c.w;
       }
+    }
+  } else {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        kept += (D[u] > 0.0f && D[u] >= thr);
-        valid += (D[u] >= 0.0f);
+    for (int i = 0; i < kTilePer; ++i) {
+      bool in = p0 + i < n;
+      K.D[i] = in ? __ldcs(p.vals + p0 + i) : -1.0f;
+      if (kCols) K.C[i] = in ? __ldcs(p.cols + p0 + i) : 0;
+    }
+  }
+  unsigned keep = 0;
+  const bool bf16 = kCols && p.value_dtype == 1;
+  if (!T.overflow) {
+    // last table entry starting at or before p0
+    const long long rel0 = p0 - base;
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (T.start[mid] <= rel0) lo = mid; else hi = mid - 1;
+    }
+    int k = lo;
+    long long next = T.start[k + 1];
+    float thr = T.thr[k], scale = bf16 ? T.scale[k] : 1.0f;
+#pragma unroll
+    for (int i = 0; i < kTilePer; ++i) {
+      const long long rel = rel0 + i;
+      while (rel >= next && k + 1 < T.n) {
+        ++k;
+        next = T.start[k + 1];
+        thr = T.thr[k];
+        if (bf16) scale = T.scale[k];
+      }
+      if (p0 + i < n && K.D[i] > 0.0f && K.D[i] >= thr) {
+        keep |= 1u << i;
+        if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      kept += __shfl_xor_sync(0xffffffffu, kept, o);
-      valid += __shfl_xor_sync(0xffffffffu, valid, o);
+  } else {
+    const long long ni = *p.n_items;
+    const long long* __restrict__ off = p.item_off;
+    long long it = item0;
+    long long next = it + 1 < ni ? off[it + 1] : n;
+    int row = -1;
+    float thr = 0.0f, scale = 1.0f;
+    for (int i = 0; i < kTilePer; ++i) {
+      const long long pos = p0 + i;
+      if (pos >= n) break;
+      while (next <= pos) {
+        ++it;
+        next = it + 1 < ni ? off[it + 1] : n;
+      }
+      int r = p.item_row[it];
+      if (r != row) {
+        row = r;
+        thr = p.tau * __uint_as_float(p.row_max[r]);
+        if (bf16) scale = p.slot->beam_scale[p.rows[r].beam];
+      }
+      if (K.D[i] > 0.0f && K.D[i] >= thr) {
+        keep |= 1u << i;
+        if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
+      }
     }
-    if (lane == 0) {
-      p.item_kept[item] = kept;
-      if (valid) atomicAdd((unsigned long long*)(p.row_cand + row), (unsigned long long)valid);
-    }
+  }
+  K.keep = keep;
+}
+
+// per tile: the item holding its first candidate (tile_item0) and the first
+// item starting at or after it (tile_first), from one thread per item
+__global__ void k_tile_map(const long long* __restrict__ item_off, const long long* __restrict__ n_items_p,
+                           long long n_cand, long long* tile_item0, long long* tile_first) {
+  const long long ni = *n_items_p;
+  const long long n_tiles = (n_cand + kTile - 1) / kTile;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ni; i += (long long)gridDim.x * blockDim.x) {
+    const long long a = item_off[i], b = item_off[i + 1];
+    // tiles whose first candidate lies in item i
+    for (long long t = (a + kTile - 1) / kTile; t * kTile < b && t < n_tiles; ++t) tile_item0[t] = i;
+    // tiles whose first candidate is in (off[i-1], off[i]]: item i is the first one starting at or after it
+    const long long prev = i > 0 ? item_off[i - 1] : -1;
+    for (long long t = prev < 0 ? 0 : prev / kTile + 1; t * kTile <= a && t < n_tiles; ++t) tile_first[t] = i;
+    // tiles starting after the last item's start: no item starts at or after them
+    if (i == ni - 1)
+      for (long long t = a / kTile + 1; t < n_tiles; ++t) tile_first[t] = ni;
   }
 }
 
-// CSR columns and values: each warp compacts one item in candidate order
-// (ascending voxel index) with ballots; 8 x 32 candidates per round
-__global__ void __launch_bounds__(kEvalThreads) k_compact_write(CompactParams p) {
+__global__ void __launch_bounds__(kEvalThreads) k_tile_count(CompactParams p, int* tile_cnt) {
+  __shared__ TileTable T;
+  __shared__ int wsum[kEvalThreads / 32];
+  const int t = threadIdx.x;
+  const long long base = (long long)blockIdx.x * kTile;
+  if (base >= p.n_cand) return;                        // uniform
+  const long long item0 = p.tile_item0[blockIdx.x];
+  tile_table(p, base, item0, T, false);
+  TileKeep K;
+  tile_keep<false>(p, base, base + (long long)t * kTilePer, item0, T, K);
+  int c = __popc(K.keep);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((t & 31) == 0) wsum[t >> 5] = c;
+  __syncthreads();
+  if (t == 0) {
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kEvalThreads / 32; ++k) s += wsum[k];
+    tile_cnt[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kEvalThreads) k_tile_write(CompactParams p, const long long* __restrict__ tile_off) {
+  __shared__ int s_col[kTile];
+  __shared__ float s_val[kTile];
+  __shared__ TileTable T;
+  __shared__ int wscan[kEvalThreads / 32];
+  const int t = threadIdx.x;
+  const long long n = p.n_cand;
+  const long long base = (long long)blockIdx.x * kTile;
+  if (base >= n) return;                               // uniform
   const long long ni = *p.n_items;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const long long nw = (long long)gridDim.x * (kEvalThreads / 32);
+  const long long* __restrict__ off = p.item_off;
+  const long long item0 = p.tile_item0[blockIdx.x];
+  tile_table(p, base, item0, T, p.value_dtype == 1);
+  const long long p0 = base + (long long)t * kTilePer;
+  TileKeep K;
+  tile_keep<true>(p, base, p0, item0, T, K);
+  const int cnt = __popc(K.keep);
+  const int lane = t & 31, w = t >> 5;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int x = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) wscan[w] = incl;
+  __syncthreads();
+  int wpre = 0, tot = 0;
+#pragma unroll
+  for (int k = 0; k < kEvalThreads / 32; ++k) {
+    int x = wscan[k];
+    if (k < w) wpre += x;
+    tot += x;
+  }
+  const int excl = wpre + incl - cnt;
+  const long long prefix = tile_off[blockIdx.x];
+  // kept count before each item start in this thread's range (items starting
+  // exactly at the tile's first candidate go to thread 0)
+  {
+    long long j = t == 0 ? p.tile_first[blockIdx.x] : item0;
+    while (j < ni && off[j] < p0) ++j;
+    for (; j < ni && off[j] < p0 + kTilePer && off[j] < n; ++j) {
+      int r = (int)(off[j] - p0);
+      p.item_out[j] = prefix + excl + __popc(K.keep & ((1u << r) - 1u));
+    }
+  }
+  int q = excl;
+#pragma unroll
+  for (int i = 0; i < kTilePer; ++i) {
+    if (K.keep & (1u << i)) {
+      s_col[q] = K.C[i];
+      s_val[q] = K.D[i];
+      ++q;
+    }
+  }
+  __syncthreads();
   int* col = p.slot->col;
-  void* valp = p.slot->val;
-  for (long long item = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5); item < ni; item += nw) {
-    int row = row_of_item(p.row_item_base, p.nrows, item);
-    float thr = p.tau * __uint_as_float(p.row_max[row]);
-    float scale = 1.0f;
-    if (p.value_dtype == 1) scale = p.slot->beam_scale[p.rows[row].beam];
-    long long a = p.item_off[item], b = p.item_off[item + 1];
-    long long o = p.item_out[item];
-    for (long long i0 = a; i0 < b; i0 += 8 * 32) {
-      float D[8];
-      int C[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        long long i = i0 + u * 32 + lane;
-        D[u] = i < b ? __ldcs(p.vals + i) : -1.0f;
-        C[u] = i < b ? __ldcs(p.cols + i) : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        bool keep = D[u] > 0.0f && D[u] >= thr;
-        unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          long long q = o + __popc(m & lt);
-          col[q] = C[u];
-          if (p.value_dtype == 1)
-            ((__nv_bfloat16*)valp)[q] = __float2bfloat16_rn(__fdiv_rn(D[u], scale));
-          else
-            ((float*)valp)[q] = D[u];
-        }
-        o += __popc(m);
-      }
+  if (p.value_dtype == 1) {
+    __nv_bfloat16* val = (__nv_bfloat16*)p.slot->val;
+    for (int k = t; k < tot; k += kEvalThreads) {
+      col[prefix + k] = s_col[k];
+      val[prefix + k] = __float2bfloat16_rn(s_val[k]);
+    }
+  } else {
+    float* val = (float*)p.slot->val;
+    for (int k = t; k < tot; k += kEvalThreads) {
+      col[prefix + k] = s_col[k];
+      val[prefix + k] = s_val[k];
     }
   }
 }
 
 // CSR row pointers of one instance (rows [row_base, row_base + nrows)),
-// relative to the instance's first output slot, which goes to inst_begin
-__global__ void k_row_ptr(const long long* __restrict__ row_item_base, const long long* __restrict__ item_out,
-                          int row_base, int nrows, long long rp_off, int inst, int last,
-                          const OutSlot* __restrict__ slot) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  long long b = item_out[row_item_base[row_base]];
-  if (r <= nrows) slot->row_ptr[rp_off + r] = item_out[row_item_base[row_base + r]] - b;
+// relative to the instance's first output slot, which goes to inst_begin.
+// Row r starts at item row_item_base[r]; the kept count before it is
+// item_out of that item, or the total when the item starts past the end.
+__global__ void k_row_ptr(const long long* __restrict__ row_item_base, const long long* __restrict__ item_off,
+                          const long long* __restrict__ item_out, const long long* __restrict__ n_items_p,
+                          const long long* __restrict__ total_p, long long n_cand, int row_base, int nrows,
+                          long long rp_off, int inst, int last, const OutSlot* __restrict__ slot) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ni = *n_items_p, total = *total_p;
+  auto kept_before = [&](long long i) -> long long {
+    return (i >= ni || item_off[i] >= n_cand) ? total : item_out[i];
+  };
+  const long long b = kept_before(row_item_base[row_base]);
+  if (r <= nrows) slot->row_ptr[rp_off + r] = kept_before(row_item_base[row_base + r]) - b;
   if (r == 0) {
     slot->inst_begin[inst] = b;
-    if (last) slot->inst_begin[inst + 1] = item_out[row_item_base[row_base + nrows]];
+    if (last) slot->inst_begin[inst + 1] = total;
   }
 }
 

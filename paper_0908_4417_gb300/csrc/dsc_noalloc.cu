@@ -25,11 +25,14 @@
 namespace dsc {
 __global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
-__global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*);
+__global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*, const int*);
+__global__ void k_item_rows(const long long*, int, int*);
+__global__ void k_tile_map(const long long*, const long long*, long long, long long*, long long*);
 __global__ void k_eval(EvalParams);
-__global__ void k_compact_count(CompactParams);
-__global__ void k_compact_write(CompactParams);
-__global__ void k_row_ptr(const long long*, const long long*, int, int, long long, int, int, const OutSlot*);
+__global__ void k_tile_count(CompactParams, int*);
+__global__ void k_tile_write(CompactParams, const long long*);
+__global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
+                          long long, int, int, long long, int, int, const OutSlot*);
 __global__ void k_scan_partial(const int*, const long long*, long long, long long*);
 __global__ void k_scan_blocks(long long*);
 __global__ void k_scan_final(const int*, const long long*, long long, const long long*, long long*);
@@ -198,6 +201,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   unsigned* d_row_max = cv.take<unsigned>(nrows);
   long long* d_row_cand = cv.take<long long>(nrows);
   float* d_scale = cv.take<float>(1);
+  int* d_status = cv.take<int>(1);
   long long* d_inst_begin = cv.take<long long>(2);
   if (!d_inst_begin)
     return na_fail(DSC_E_INVAL, "needs more than %zu bytes of working memory (the fixed maximum) for %d beamlets",
@@ -221,6 +225,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   NA_CU(cudaMemsetAsync(d_row_max, 0, sizeof(unsigned) * nrows, s));
   NA_CU(cudaMemsetAsync(d_row_cand, 0, sizeof(long long) * nrows, s));
   NA_CU(cudaMemsetAsync(d_counter, 0, sizeof(int) * 4, s));
+  NA_CU(cudaMemsetAsync(d_status, 0, sizeof(int), s));
 
   int sms = 0, nb = 0;
   NA_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -239,26 +244,32 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   NA_CU(cudaMemcpyAsync(&n_items, d_rib + nrows, sizeof(long long), cudaMemcpyDeviceToHost, s));
   NA_CU(cudaStreamSynchronize(s));
   int* d_item_cand = cv.take<int>(n_items);
+  int* d_item_row = cv.take<int>(n_items);
   long long* d_item_off = cv.take<long long>(n_items + 1);
-  int* d_item_kept = cv.take<int>(n_items);
   long long* d_item_out = cv.take<long long>(n_items + 1);
   if (!d_item_out)
     return na_fail(DSC_E_INVAL, "needs more than %zu bytes of working memory (the fixed maximum): %lld work items",
                    kNoAllocBytes, n_items);
   const long long* n_items_dev = d_rib + nrows;
-  k_siddon<<<(nrows + kSiddonWarps - 1) / kSiddonWarps, 32 * kSiddonWarps, 0, s>>>(d_inst, d_rows, nrows, d_tables,
-                                                                                  stride);
+  k_siddon<<<nrows, kSiddonThreads, 0, s>>>(d_inst, d_rows, nrows, d_tables, stride);
   NA_LAUNCH();
-  k_count<<<grid_items, kEvalThreads, 0, s>>>(d_inst, d_rows, d_rib, nrows, n_items_dev, d_item_cand);
+  k_item_rows<<<(nrows + 127) / 128, 128, 0, s>>>(d_rib, nrows, d_item_row);
+  NA_LAUNCH();
+  k_count<<<grid_items, kEvalThreads, 0, s>>>(d_inst, d_rows, d_rib, nrows, n_items_dev, d_item_cand, d_item_row);
   NA_LAUNCH();
   st = na_scan(d_item_cand, n_items_dev, 0, d_scan, d_item_off, s);
   if (st != DSC_OK) return st;
   long long n_cand = 0;
   NA_CU(cudaMemcpyAsync(&n_cand, d_item_off + n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
   NA_CU(cudaStreamSynchronize(s));
-  float* d_vals = cv.take<float>(n_cand);
-  int* d_cols = cv.take<int>(n_cand);
-  if (!d_cols)
+  const long long n_tiles = (n_cand + kTile - 1) / kTile;
+  float* d_vals = cv.take<float>(n_cand + 4);
+  int* d_cols = cv.take<int>(n_cand + 4);
+  int* d_tile_cnt = cv.take<int>(n_tiles);
+  long long* d_tile_off = cv.take<long long>(n_tiles + 1);
+  long long* d_tile_item0 = cv.take<long long>(n_tiles);
+  long long* d_tile_first = cv.take<long long>(n_tiles);
+  if (!d_tile_first)
     return na_fail(DSC_E_INVAL, "needs %zu bytes of working memory for %lld candidate pairs; the fixed maximum is %zu",
                    cv.need, n_cand, kNoAllocBytes);
 
@@ -271,38 +282,15 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   ep.row_item_base = d_rib;
   ep.nrows = nrows;
   ep.item_off = d_item_off;
+  ep.item_row = d_item_row;
   ep.n_items = n_items_dev;
   ep.vals = d_vals;
   ep.cols = d_cols;
   ep.row_max = d_row_max;
+  ep.row_cand = d_row_cand;
   ep.item_counter = d_counter;
   k_eval<<<grid_eval, kEvalThreads, 0, s>>>(ep);
   NA_LAUNCH();
-  CompactParams cp;
-  cp.inst = d_inst;
-  cp.rows = d_rows;
-  cp.row_item_base = d_rib;
-  cp.nrows = nrows;
-  cp.item_off = d_item_off;
-  cp.n_items = n_items_dev;
-  cp.vals = d_vals;
-  cp.cols = d_cols;
-  cp.row_max = d_row_max;
-  cp.tau = (float)opts->rel_threshold;
-  cp.item_kept = d_item_kept;
-  cp.row_cand = d_row_cand;
-  cp.item_out = d_item_out;
-  cp.value_dtype = DSC_VALUE_F32;
-  cp.slot = d_slot;
-  k_compact_count<<<grid_items, kEvalThreads, 0, s>>>(cp);
-  NA_LAUNCH();
-  st = na_scan(d_item_kept, n_items_dev, 0, d_scan, d_item_out, s);
-  if (st != DSC_OK) return st;
-  long long nnz = 0;
-  NA_CU(cudaMemcpyAsync(&nnz, d_item_out + n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
-  NA_CU(cudaStreamSynchronize(s));
-  if (nnz > capacity)
-    return na_fail(DSC_E_INVAL, "output capacity %lld < %lld kept entries", (long long)capacity, nnz);
   OutSlot q{};
   q.row_ptr = (long long*)row_ptr_dev;
   q.col = col_dev;
@@ -311,12 +299,45 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   q.row_max = d_row_max;
   q.row_cand = d_row_cand;
   q.inst_begin = d_inst_begin;
+  q.status = d_status;
   NA_CU(cudaMemcpyAsync(d_slot, &q, sizeof(OutSlot), cudaMemcpyHostToDevice, s));
-  k_compact_write<<<grid_items, kEvalThreads, 0, s>>>(cp);
+  CompactParams cp;
+  cp.rows = d_rows;
+  cp.item_off = d_item_off;
+  cp.item_row = d_item_row;
+  cp.n_items = n_items_dev;
+  cp.n_cand = n_cand;
+  cp.vals = d_vals;
+  cp.cols = d_cols;
+  cp.row_max = d_row_max;
+  cp.tau = (float)opts->rel_threshold;
+  cp.item_out = d_item_out;
+  cp.tile_item0 = d_tile_item0;
+  cp.tile_first = d_tile_first;
+  cp.value_dtype = DSC_VALUE_F32;
+  k_tile_map<<<256, 256, 0, s>>>(d_item_off, n_items_dev, n_cand, d_tile_item0, d_tile_first);
   NA_LAUNCH();
-  k_row_ptr<<<(nrows + 1 + 255) / 256, 256, 0, s>>>(d_rib, d_item_out, 0, nrows, 0, 0, 1, d_slot);
+  cp.slot = d_slot;
+  // kept count first, so the capacity is checked before any output is touched
+  const unsigned tiles = (unsigned)(n_tiles > 0 ? n_tiles : 1);
+  k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, d_tile_cnt);
   NA_LAUNCH();
+  st = na_scan(d_tile_cnt, nullptr, n_tiles, d_scan, d_tile_off, s);
+  if (st != DSC_OK) return st;
+  long long nnz = 0;
+  int status = 0;
+  NA_CU(cudaMemcpyAsync(&nnz, d_tile_off + n_tiles, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  NA_CU(cudaStreamSynchronize(s));
+  if (nnz > capacity)
+    return na_fail(DSC_E_INVAL, "output capacity %lld < %lld kept entries", (long long)capacity, nnz);
+  k_tile_write<<<tiles, kEvalThreads, 0, s>>>(cp, d_tile_off);
+  NA_LAUNCH();
+  k_row_ptr<<<(nrows + 1 + 255) / 256, 256, 0, s>>>(d_rib, d_item_off, d_item_out, n_items_dev, d_tile_off + n_tiles,
+                                                    n_cand, 0, nrows, 0, 0, 1, d_slot);
+  NA_LAUNCH();
+  NA_CU(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   NA_CU(cudaStreamSynchronize(s));   // the array is free for the next call once this returns
+  if (status) return na_fail(DSC_E_TIMEOUT, "a bounded device wait expired (status %d)", status);
   *nnz_out = nnz;
   return DSC_OK;
 }

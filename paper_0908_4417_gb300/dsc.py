@@ -23,7 +23,7 @@ DSC_E_BUSY = 8
 DSC_CUTOFF_VOI6, DSC_CUTOFF_SIGMA, DSC_CUTOFF_NONE = 0, 1, 2
 DSC_VALUE_F32, DSC_VALUE_BF16 = 0, 1
 DSC_FLAG_TIMING = 1
-STAGES = ("setup", "siddon", "count", "eval", "beam_scale", "compact_count", "compact_write", "total")
+STAGES = ("setup", "siddon", "count", "eval", "beam_scale", "compact", "finish", "total")
 
 EXPORTS = [
     "dsc_status_str", "dsc_last_error", "dsc_abi_version", "dsc_launch_count",
