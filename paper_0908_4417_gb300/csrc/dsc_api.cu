@@ -110,7 +110,7 @@ static void release_after(cudaEvent_t ev, int dev, void* const* ps, int n) {
     if (ps[i]) cudaFreeAsync(ps[i], fs);
 }
 
-static int g_target_cand = 4096;     // candidates per work item (tile shape)
+static int g_target_cand = 8192;     // candidates per work item (tile shape)
 
 // ---------------------------------------------------------------------------
 // handles

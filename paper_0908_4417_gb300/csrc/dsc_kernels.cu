@@ -334,12 +334,16 @@ struct LineSm {
 
 // the candidate interval [lo, hi] of one x-line (iy, iz) of row R and its
 // float-float s, x', z' at ix = 0
-__device__ __forceinline__ int line_setup(const DRow& R, int mode, int nx, int iy, int iz, ff& s0, ff& x0, ff& z0,
-                                          int& lo_out) {
+__device__ __forceinline__ void line_base(const DRow& R, int iy, int iz, ff& s0, ff& x0, ff& z0) {
   float fy = (float)iy, fz = (float)iz;
   s0 = ff_add(ff_add(R.S0, ff_mul_i(R.Ss[1], fy)), ff_mul_i(R.Ss[2], fz));
   x0 = ff_add(ff_add(R.X0, ff_mul_i(R.Xs[1], fy)), ff_mul_i(R.Xs[2], fz));
   z0 = ff_add(ff_add(R.Z0, ff_mul_i(R.Zs[1], fy)), ff_mul_i(R.Zs[2], fz));
+}
+
+// candidate interval [lo, lo + len) of the x-line whose s, x', z' at ix = 0 are given
+__device__ __forceinline__ int line_interval(const DRow& R, int mode, int nx, const ff& s0, const ff& x0, const ff& z0,
+                                             int& lo_out) {
   // t(i) = T0 + i tx, x'(i) = X0 + i xx, z'(i) = Z0 + i zx; constraints c i <= r
   float T0 = R.tA_f + s0.hi, tx = R.Ss[0].hi;
   float X0 = x0.hi, xx = R.Xs[0].hi, Z0 = z0.hi, zx = R.Zs[0].hi;
@@ -366,6 +370,14 @@ __device__ __forceinline__ int line_setup(const DRow& R, int mode, int nx, int i
   lo_out = ilo;
   if (empty || ihi < ilo) return 0;
   return ihi - ilo + 1;
+}
+
+// the candidate interval of x-line (iy, iz) and its s, x', z' at ix = 0; the
+// enumeration count and the evaluation both call this, so they agree exactly
+__device__ __forceinline__ int line_setup(const DRow& R, int mode, int nx, int iy, int iz, ff& s0, ff& x0, ff& z0,
+                                          int& lo_out) {
+  line_base(R, iy, iz, s0, x0, z0);
+  return line_interval(R, mode, nx, s0, x0, z0, lo_out);
 }
 
 
@@ -563,7 +575,7 @@ __device__ __forceinline__ float erf_pair(float h, float ax, float inv_s) {
   float v2 = (h + ax) * inv_s;
   float e1 = erfc_v(fabsf(v1));
   float e2 = erfc_v(v2);
-  return v1 >= 0.0f ? (2.0f - e1) - e2 : e1 - e2;
+  return (v1 >= 0.0f ? 2.0f - e1 : e1) - e2;
 }
 
 // everything the per-pair evaluation reads, loaded once per work item
@@ -684,13 +696,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalParams p) {
     const DRow& R = p.rows[row];
     const DInst& G = p.inst[R.inst];
     const int mode = G.cutoff_mode;
-    const int total = item_lines(sm, R, mode, G.nx, G.ny, item - p.row_item_base[row]);
+    const long long a_off = p.item_off[item];
+    const int total = min(item_lines(sm, R, mode, G.nx, G.ny, item - p.row_item_base[row]),
+                          (int)(p.item_off[item + 1] - a_off));   // never past the counted range
     RowConst C;
     load_row_const(C, R, G, p.tables + (size_t)row * p.table_stride);
-    float* out = p.vals + p.item_off[item];
-    int* outc = p.cols + p.item_off[item];
+    float* out = p.vals + a_off;
+    int* outc = p.cols + a_off;
     float vmax = 0.0f;
-    int valid = 0;
+    int valid = (mode != 1 && threadIdx.x == 0) ? total : 0;   // outside the sigma cutoff every candidate counts
     for (int w0 = 0; w0 < total; w0 += kWindow) {
       int wl = min(kWindow, total - w0);
       item_map(sm, w0, wl);
@@ -703,7 +717,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalParams p) {
         out[w0 + j] = D;
         outc[w0 + j] = __float_as_int(zc.w) + ix;
         vmax = fmaxf(vmax, D);
-        valid += D >= 0.0f;
+        if (mode == 1) valid += D >= 0.0f;
       }
       __syncthreads();
     }

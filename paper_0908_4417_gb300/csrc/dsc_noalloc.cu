@@ -233,7 +233,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   const int grid_eval = (nb > 0 ? nb : 1) * sms;
   NA_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count, kEvalThreads, 0));
   const int grid_items = (nb > 0 ? nb : 1) * sms;
-  const int kTargetCand = 4096;
+  const int kTargetCand = 8192;
 
   // set-up and work items
   k_setup<<<(nrows + 127) / 128, 128, 0, s>>>(d_inst, d_beams, nbeams, d_rows, nrows, d_row_items, kTargetCand);
