@@ -58,6 +58,9 @@ struct DRow {
   double x[3], z[3];       // lateral unit axes (x', z' directions)
   double tA, tB;           // entry A and exit B along the axis
   double inv_e[3];         // 1 / e (0 where e is 0)
+  // Siddon walk in fixed point (units of 2^-fix_q mm, set up in FP64)
+  long long fx_tA, fx_h, fx_tB;
+  int fix_q;
   // voxel loop, compensated FP32: value at voxel (0,0,0) and per-index slopes
   ff S0, X0, Z0;           // s = t - tA, x', z' at voxel (0,0,0)
   ff Ss[3], Xs[3], Zs[3];  // change of s, x', z' per step in ix, iy, iz

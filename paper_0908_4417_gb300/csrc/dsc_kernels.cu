@@ -135,6 +135,17 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
   R.tB = hit ? t1 : 0.0;
   R.tA_f = (float)R.tA;
   R.n_table = hit ? (int)ceil((R.tB - R.tA) / G.hd) + 1 : 0;
+  {
+    // fixed-point constants of the Siddon walk: the unit 2^-q mm keeps t_B
+    // (plus one plane step) below 2^60 units; q <= 48 (3.6e-15 mm)
+    double tmax = R.tB + fmax(G.dx, fmax(G.dy, G.dz)) * 2.0 + 1.0;
+    int q = min(max(60 - (int)ceil(log2(tmax)), 0), 48);
+    double fx = ldexp(1.0, q);
+    R.fix_q = q;
+    R.fx_tA = __double2ll_rn(R.tA * fx);
+    R.fx_tB = __double2ll_rn(R.tB * fx);
+    R.fx_h = __double2ll_rn(G.hd * fx);
+  }
 
   // voxel-loop constants: w0 = centre of voxel (0,0,0) - S
   double w0[3] = {G.ox + 0.5 * G.dx - S[0], G.oy + 0.5 * G.dy - S[1], G.oz + 0.5 * G.dz - S[2]};
@@ -240,68 +251,94 @@ __global__ void __launch_bounds__(kSiddonThreads) k_siddon(const DInst* __restri
   const double sp[3] = {G.dx, G.dy, G.dz};
   const double isp[3] = {G.idx, G.idy, G.idz};
   const int nv[3] = {G.nx, G.ny, G.nz};
+  // The walk runs in fixed point (crossing parameters alpha as 64-bit
+  // integers from the FP64 set-up in k_setup, in units finer than an FP64 ulp
+  // at these distances) on the integer pipes; the density integral is a
+  // compensated FP32 sum, as fine as the FP32 table that stores it.
   double total = 0.0;
   if (k0 < k1) {
-    double tcur = R.tA + fmin(k0 * h, L);
-    // per axis: voxel index, step, next crossing alpha and its increment
+    const long long kNever = 0x3fffffffffffffffll;
+    const float unfix = ldexpf(1.0f, -R.fix_q);
+    const long long tcur0 = R.fx_tA + min((long long)k0 * R.fx_h, R.fx_tB - R.fx_tA);
+    long long tcur = tcur0;
+    // starting voxel and next crossing per axis (FP64 once per lane), then
+    // fixed point; a crossing past t_B never happens, and steps are capped so
+    // that no sum overflows
+    const double tcur_d = R.tA + fmin(k0 * h, L);
+    const double fx = ldexp(1.0, R.fix_q);
+    const double tlim = R.tB + 1.0;
+    long long al[3], da[3];
     int i[3], st[3];
-    double al[3], da[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double p = fma(tcur, e[a], S[a]);
+      double p = fma(tcur_d, e[a], S[a]);
       int q = (int)floor((p - org[a]) * isp[a]);
       i[a] = min(max(q, 0), nv[a] - 1);
       const double ie = R.inv_e[a];
+      double an = CUDART_INF, dn = 0.0;
       if (e[a] > 0.0) {
         st[a] = 1;
-        al[a] = (org[a] + (i[a] + 1) * sp[a] - S[a]) * ie;
-        da[a] = sp[a] * ie;
+        an = (org[a] + (i[a] + 1) * sp[a] - S[a]) * ie;
+        dn = sp[a] * ie;
       } else if (e[a] < 0.0) {
         st[a] = -1;
-        al[a] = (org[a] + i[a] * sp[a] - S[a]) * ie;
-        da[a] = -sp[a] * ie;
+        an = (org[a] + i[a] * sp[a] - S[a]) * ie;
+        dn = -sp[a] * ie;
       } else {
         st[a] = 0;
-        al[a] = CUDART_INF;
-        da[a] = 0.0;
       }
+      al[a] = an <= tlim ? __double2ll_rn(an * fx) : kNever;
+      da[a] = dn <= tlim ? __double2ll_rn(dn * fx) : kNever;
     }
     // scalar walk state (no dynamically indexed arrays: they would live in local memory)
     int ix = i[0], iy = i[1], iz = i[2];
     const int sx = st[0], sy_ = st[1], sz_ = st[2];
-    double ax = al[0], ay = al[1], az = al[2];
-    const double dax = da[0], day = da[1], daz = da[2];
+    long long ax = al[0], ay = al[1], az = al[2];
+    const long long dax = da[0], day = da[1], daz = da[2];
     const float* rho = G.rho;
     const long long ny_s = G.nx, nz_s = (long long)G.nx * G.ny;
     long long vox = ix + iy * ny_s + iz * nz_s;
-    double rv = (double)__ldg(rho + vox);
+    float rv = __ldg(rho + vox) * unfix;              // density per fixed-point unit
+    float sum = 0.0f, comp = 0.0f;                     // Kahan sum of the lane
+    long long tend = tcur0;
     int guard = 4 * (G.nx + G.ny + G.nz) + 8 * (k1 - k0) + 16;
     for (int k = k0; k < k1; ++k) {
-      double tend = (k + 1 == nint) ? R.tB : R.tA + fmin((k + 1) * h, L);
+      tend = (k + 1 == nint) ? R.fx_tB : min(tend + R.fx_h, R.fx_tB);
       for (;;) {
-        double am = fmin(ax, fmin(ay, az));
+        const long long am = min(ax, min(ay, az));
         if (am >= tend || --guard < 0) break;
-        total = fma(fmax(am - tcur, 0.0), rv, total);
-        tcur = fmax(tcur, am);
+        {
+          float y = fmaf((float)max(am - tcur, 0ll), rv, -comp);
+          float tt = sum + y;
+          comp = (tt - sum) - y;
+          sum = tt;
+        }
+        tcur = max(tcur, am);
         if (ax == am) {
           int n2 = ix + sx;
           if (n2 >= 0 && n2 < G.nx) { ix = n2; vox += sx; }
-          ax += dax;
+          ax = ax + dax > ax ? min(ax + dax, kNever) : kNever;
         } else if (ay == am) {
           int n2 = iy + sy_;
           if (n2 >= 0 && n2 < G.ny) { iy = n2; vox += sy_ * ny_s; }
-          ay += day;
+          ay = ay + day > ay ? min(ay + day, kNever) : kNever;
         } else {
           int n2 = iz + sz_;
           if (n2 >= 0 && n2 < G.nz) { iz = n2; vox += sz_ * nz_s; }
-          az += daz;
+          az = az + daz > az ? min(az + daz, kNever) : kNever;
         }
-        rv = (double)__ldg(rho + vox);
+        rv = __ldg(rho + vox) * unfix;
       }
-      total = fma(fmax(tend - tcur, 0.0), rv, total);
-      tcur = fmax(tcur, tend);
-      tab[k + 1] = (float)total;                     // lane-local, fixed below
+      {
+        float y = fmaf((float)max(tend - tcur, 0ll), rv, -comp);
+        float tt = sum + y;
+        comp = (tt - sum) - y;
+        sum = tt;
+      }
+      tcur = max(tcur, tend);
+      tab[k + 1] = sum - comp;                         // lane-local, fixed below
     }
+    total = (double)sum - (double)comp;
   }
   // exclusive prefix of the lane totals over the CTA
   double incl = total;
