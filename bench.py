@@ -36,6 +36,10 @@ sys.path.insert(0, ROOT)
 # evaluations x 20, inverse square and product 4.
 F_PAIR = 337
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of the evaluation kernel per candidate pair, from
+# one Nsight Compute capture of the current kernel on the 2-field prostate
+# (27.85 M pairs, 163.7 MB); the full workload's traffic is this times its pairs
+KEVAL_DRAM_BYTES_PER_PAIR = 5.876
 
 
 def parse():
@@ -285,7 +289,9 @@ def run_ours(args):
                 "host_wall_ms_per_step": 1e3 * wall_s / e2e_steps},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_eval",
+                     "frac": achieved / peak, "traffic": KEVAL_DRAM_BYTES_PER_PAIR * pairs,
+                     "traffic_basis": "ncu dram bytes per pair of k_eval on prostate_256_2f, times pairs",
+                     "kernel": "k_eval",
                      "flop_per_pair": F_PAIR, "eval_ms": eval_ms,
                      "peak_basis": f"FP32 FMA 2x{FP32_LANES_PER_SM} lanes x {props.multi_processor_count} SMs "
                                    f"x {peak_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"},
