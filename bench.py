@@ -2,7 +2,7 @@
 """Benchmark of the FSPB D_ij path: voxel-beamlet pairs/s and 9-field latency.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload prostate_256|slabs_128|water_32]
+                    [--workload prostate_256|slabs_128|water_32|batched|serving]
 
 One step = the whole path (beamlet set-up, Siddon depth tables, VOI
 enumeration, FSPB evaluation, threshold + CSR compaction) for the 9-field
@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="prostate_256")
     p.add_argument("--cpu-sample-stride", type=int, default=4)
+    p.add_argument("--instances", type=int, default=32, help="batched: re-plan instances")
+    p.add_argument("--requests", type=int, default=64, help="serving: requests")
+    p.add_argument("--rate", type=float, default=4.0, help="serving: mean Poisson arrival rate (1/s)")
     return p.parse_args()
 
 
@@ -304,10 +307,178 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _timed(fn, stream, steps):
+    """Device time (s) of `steps` calls of fn on `stream`, events on that stream."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def run_batched(args):
+    """Many uneven re-plan instances in one batched launch sequence (one
+    persistent evaluation over a shared work queue, replayed as a CUDA graph)
+    against the same instances as sequential per-plan launches."""
+    import torch
+    from paper_0908_4417_gb300 import build as B
+    B.build()
+    from paper_0908_4417_gb300 import dsc, phantoms as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    sp = stream.cuda_stream
+    ws = P.batched(args.instances)
+    gs = []
+    for w in ws:
+        g = dsc.dsc_create_geometry(w.grid, w.density, False, w.model, sp)
+        for b in w.beams:
+            dsc.dsc_add_beam(g, b)
+        gs.append(g)
+    opts = dsc.compute_opts(1e-3, dsc.DSC_VALUE_F32, 0.5, 0)
+    held = []
+
+    def batch():
+        held.extend(dsc.dsc_compute_dij_batch(gs, opts, sp))
+
+    def sequential():
+        for g in gs:
+            held.append(dsc.dsc_compute_dij(g, opts, sp))
+
+    def drain():
+        stream.synchronize()
+        for r in held:
+            dsc.dsc_release_result(r)
+        held.clear()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            batch(); drain(); sequential(); drain()
+        batch()
+        stream.synchronize()
+        pairs = sum(int(dsc.dsc_get_csr(r, False).pairs) for r in held)
+        nnz = sum(int(dsc.dsc_get_csr(r, False).nnz) for r in held)
+        drain()
+        n0 = dsc.dsc_launch_count()
+        t_batch = 0.0
+        for _ in range(args.steps):
+            t_batch += _timed(batch, stream, 1)
+            drain()
+        launches = dsc.dsc_launch_count() - n0
+        t_seq = 0.0
+        for _ in range(args.steps):
+            t_seq += _timed(sequential, stream, 1)
+            drain()
+    for g in gs:
+        dsc.dsc_destroy_geometry(g)
+    out = {"metric": "voxel-beamlet pairs/s (batched re-plan instances)", "value": pairs * args.steps / t_batch,
+           "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batched_{args.instances}", "instances": args.instances,
+                      "rows": sum(w.nrows for w in ws), "pairs_per_step": pairs, "nnz_per_step": nnz,
+                      "l2": "working set far above L2 (no flush needed)",
+                      "sequential_pairs_per_s": pairs * args.steps / t_seq,
+                      "sequential_ms_per_step": 1e3 * t_seq / args.steps,
+                      "batched_over_sequential": t_seq / t_batch},
+           "gpu_launches": int(launches)}
+    print(json.dumps(out), flush=True)
+
+
+def run_serving(args):
+    """Continuous-batching server on a seeded Poisson stream of re-plan
+    requests (resident geometries, fresh beam sets), then the same requests
+    submitted at once (server throughput) and as sequential per-plan launches."""
+    import numpy as np
+    import torch
+    from paper_0908_4417_gb300 import build as B
+    B.build()
+    from paper_0908_4417_gb300 import dsc, phantoms as P
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    base = [P.batched_instance(7000 + k) for k in range(8)]
+    gs = [dsc.dsc_create_geometry(w.grid, w.density, False, w.model, sp) for w in base]
+    stream.synchronize()
+    draw = P._Draw(8080)
+    reqs = []
+    for _ in range(args.requests):
+        k = draw.randint(0, len(base) - 1)
+        b0 = base[k].beams[0]
+        nf = draw.randint(5, 9)
+        beams = [P.Beam(360.0 * draw.u(), b0.sad, b0.iso, b0.a, b0.b, b0.n_u, b0.n_v) for _ in range(nf)]
+        reqs.append((k, beams))
+    gaps = -np.log(P.uniform01(8081, np.arange(args.requests, dtype=np.uint64))) / args.rate
+    arrive = np.cumsum(gaps) - gaps[0]
+    opts = dsc.compute_opts(1e-3, dsc.DSC_VALUE_F32, 0.5, 0)
+
+    def serve(times):
+        srv = dsc.dsc_server_create(96 << 30, max_inflight=2, max_batch=8)
+        t0 = time.perf_counter()
+        ids = []
+        for (k, beams), ta in zip(reqs, times):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(dsc.dsc_server_submit(srv, gs[k], beams, opts))
+        for rid in ids:
+            dsc.dsc_release_result(dsc.dsc_server_poll(srv, rid, -1))
+        span = time.perf_counter() - t0
+        st = dsc.dsc_server_stats(srv)
+        dsc.dsc_server_destroy(srv)
+        return st, span
+
+    def sequential():
+        t0 = time.perf_counter()
+        lat, pairs = [], 0
+        for k, beams in reqs:
+            ts = time.perf_counter()
+            g = gs[k]
+            dsc.dsc_clear_beams(g)
+            for b in beams:
+                dsc.dsc_add_beam(g, b)
+            r = dsc.dsc_compute_dij(g, opts, sp)
+            dsc.dsc_result_wait(r)
+            pairs += int(dsc.dsc_get_csr(r, False).pairs)
+            dsc.dsc_release_result(r)
+            lat.append(1e3 * (time.perf_counter() - ts))
+        return pairs, time.perf_counter() - t0, lat
+
+    serve(np.zeros(min(8, args.requests)))            # warm-up (module load, pools)
+    st_p, span_p = serve(arrive)                        # Poisson arrivals
+    st_s, span_s = serve(np.zeros(args.requests))       # all at once: server throughput
+    pairs_q, span_q, lat_q = sequential()
+    for g in gs:
+        dsc.dsc_destroy_geometry(g)
+    lat_q = sorted(lat_q)
+    out = {"metric": "voxel-beamlet pairs/s (served re-plan requests)", "value": st_s["pairs_done"] / span_s,
+           "unit": "pairs/s", "n_gpus": 1, "steps": args.requests, "warmup": min(8, args.requests),
+           "ms_per_step": 1e3 * span_s / args.requests, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"serving_{args.requests}", "requests": args.requests,
+                      "resident_geometries": len(gs), "poisson_rate_per_s": args.rate,
+                      "poisson_p50_ms": st_p["p50_ms"], "poisson_p99_ms": st_p["p99_ms"],
+                      "poisson_pairs_per_s": st_p["pairs_done"] / span_p,
+                      "saturated_p50_ms": st_s["p50_ms"], "saturated_p99_ms": st_s["p99_ms"],
+                      "sequential_pairs_per_s": pairs_q / span_q,
+                      "sequential_p50_ms": lat_q[len(lat_q) // 2],
+                      "sequential_p99_ms": lat_q[min(len(lat_q) - 1, int(0.99 * len(lat_q)))],
+                      "served_over_sequential": (st_s["pairs_done"] / span_s) / (pairs_q / span_q)}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -1010,6 +1010,8 @@ static size_t estimate_footprint(const dsc_geometry& g, const dsc_compute_opts& 
   return (size_t)bytes;
 }
 
+static dsc_status fetch_counts(dsc_result* r);
+
 static void srv_finish_slot(dsc_server* S, SrvSlot& sl) {
   double t = now_s();
   for (auto& q : sl.reqs) {
@@ -1017,6 +1019,7 @@ static void srv_finish_slot(dsc_server* S, SrvSlot& sl) {
     q->state = 2;
     S->lat_ms.push_back(1e3 * (t - q->t_submit));
     S->n_done++;
+    if (q->result && fetch_counts(q->result) == DSC_OK) S->pairs_done += q->result->pairs;
   }
   S->used -= sl.footprint;
   if (sl.plan) {

@@ -284,6 +284,7 @@ def test_server_results_same_alone_and_in_mix(dsc):
         dsc.dsc_release_result(res)
     st = dsc.dsc_server_stats(srv)
     assert st["n_done"] == 9 and st["p99_ms"] >= st["p50_ms"] > 0
+    assert st["pairs_done"] == 3 * sum(a.pairs for a in alone)
     dsc.dsc_server_destroy(srv)
     for g in gs:
         dsc.dsc_destroy_geometry(g)
