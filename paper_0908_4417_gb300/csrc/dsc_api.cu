@@ -40,6 +40,7 @@ __global__ void k_tile_map(const long long*, const long long*, long long, long l
 __global__ void k_eval(EvalParams);
 __global__ void k_beam_scale(const DBeam*, int, const unsigned*, const OutSlot*);
 __global__ void k_tile_count(CompactParams, int*);
+__global__ void k_tile_prep(CompactParams);
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
@@ -203,6 +204,10 @@ struct Plan {
   long long* d_tile_off = nullptr;   // n_tiles + 1
   long long* d_tile_item0 = nullptr;
   long long* d_tile_first = nullptr;
+  float* d_tile_thr = nullptr;
+  float* d_tile_scale = nullptr;
+  long long* d_tile_next = nullptr;
+  int* d_tile_starts = nullptr;
   long long n_tiles = 0;
   float* d_vals = nullptr;
   int* d_cols = nullptr;
@@ -220,10 +225,11 @@ struct Plan {
   std::mutex mu;                     // one computation at a time per plan
   void free_scratch() {
     void* ps[] = {d_item_cand, d_item_off, d_tile_cnt, d_tile_off, d_item_out, d_vals, d_cols, d_item_row,
-                  d_tile_item0, d_tile_first};
-    release_after(last_done, device, ps, 10);
+                  d_tile_item0, d_tile_first, d_tile_thr, d_tile_scale, d_tile_next, d_tile_starts};
+    release_after(last_done, device, ps, 14);
     d_item_cand = nullptr; d_item_off = nullptr; d_tile_cnt = nullptr; d_tile_off = nullptr; d_item_out = nullptr;
     d_vals = nullptr; d_cols = nullptr; d_item_row = nullptr; d_tile_item0 = nullptr; d_tile_first = nullptr;
+    d_tile_thr = nullptr; d_tile_scale = nullptr; d_tile_next = nullptr; d_tile_starts = nullptr;
     if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
   }
   ~Plan() {
@@ -540,6 +546,10 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_tile_off, P->n_tiles + 1, s));
   TRY(dalloc(&P->d_tile_item0, P->n_tiles, s));
   TRY(dalloc(&P->d_tile_first, P->n_tiles, s));
+  TRY(dalloc(&P->d_tile_thr, P->n_tiles, s));
+  TRY(dalloc(&P->d_tile_scale, P->n_tiles, s));
+  TRY(dalloc(&P->d_tile_next, P->n_tiles, s));
+  TRY(dalloc(&P->d_tile_starts, P->n_tiles, s));
   out = P;
   return DSC_OK;
 }
@@ -602,7 +612,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   CHECK_LAUNCH();
   TRY(record(ev, 3, s));
   // a4: FSPB evaluation
-  EvalParams ep;
+  EvalParams ep{};
   ep.inst = P->d_inst;
   ep.rows = P->d_rows;
   ep.tables = P->d_tables;
@@ -627,7 +637,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   }
   TRY(record(ev, 5, s));
   // a5: threshold + CSR compaction: kept count per tile, scan, write
-  CompactParams cp;
+  CompactParams cp{};
   cp.rows = P->d_rows;
   cp.item_off = P->d_item_off;
   cp.item_row = P->d_item_row;
@@ -640,9 +650,15 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.item_out = P->d_item_out;
   cp.tile_item0 = P->d_tile_item0;
   cp.tile_first = P->d_tile_first;
+  cp.tile_thr = P->d_tile_thr;
+  cp.tile_scale = P->d_tile_scale;
+  cp.tile_next = P->d_tile_next;
+  cp.tile_starts = P->d_tile_starts;
   cp.value_dtype = P->opts.value_dtype;
   cp.slot = P->d_slot;
-  const unsigned tiles = (unsigned)std::max<long long>(1, P->n_tiles);
+  k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((P->n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
+  CHECK_LAUNCH();
+  const unsigned tiles = (unsigned)std::max<long long>(1, (P->n_tiles + kEvalThreads / 32 - 1) / (kEvalThreads / 32));
   k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_cnt);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_tile_cnt, nullptr, P->n_tiles, P->d_scan, P->d_tile_off, s));

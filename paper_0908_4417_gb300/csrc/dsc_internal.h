@@ -109,7 +109,7 @@ struct OutSlot {
 };
 
 constexpr int kTilePer = 16;                      // candidates per thread of the compaction
-constexpr int kTile = kEvalThreads * kTilePer;    // candidates per compaction tile
+constexpr int kTile = 32 * kTilePer;              // candidates per compaction tile (one warp)
 
 struct CompactParams {
   const DRow* rows;
@@ -124,6 +124,10 @@ struct CompactParams {
   long long* item_out;            // n_items: kept entries before each item's first candidate
   const long long* tile_item0;    // per tile: item holding its first candidate
   const long long* tile_first;    // per tile: first item starting at or after its first candidate
+  float* tile_thr;                // per tile: threshold of tile_item0's row (k_tile_prep)
+  float* tile_scale;              // per tile: BF16 scale of that row's beam
+  long long* tile_next;           // per tile: start of the item after tile_item0
+  int* tile_starts;               // per tile: an item starts inside the tile
   int value_dtype;
   const OutSlot* slot;
 };

@@ -786,64 +786,27 @@ __global__ void k_beam_scale(const DBeam* __restrict__ beams, int nbeams, const 
 
 // ---------------------------------------------------------------------------
 // compaction: kept = D > 0 and D >= tau * row max, over tiles of kTile
-// candidates (kTilePer consecutive ones per thread, vector loads):
+// candidates, one warp per tile (kTilePer consecutive candidates per lane,
+// vector loads, no block barriers):
 //   k_tile_count  kept entries per tile
 //   (scan)        tile output offsets
-//   k_tile_write  block scan within the tile, kept entries staged in shared
+//   k_tile_write  warp scan within the tile, kept entries staged in shared
 //                 memory and written coalesced; item_out receives the kept
 //                 count before each item's start
 // ---------------------------------------------------------------------------
+constexpr int kTileWarps = kEvalThreads / 32;
+
 struct TileKeep {
   float D[kTilePer];
   int C[kTilePer];
   unsigned keep;
 };
 
-// The items that start before the tile's end, from the one holding its first
-// candidate: their starts relative to the tile (the first may be negative)
-// and thresholds.  Built by all threads; overflow (more starts than entries,
-// e.g. runs of empty items) sends the tile down the global-memory walk.
-constexpr int kTileItems = kEvalThreads;
-struct TileTable {
-  long long start[kTileItems + 1];
-  float thr[kTileItems];
-  float scale[kTileItems];
-  int n;                              // entries in use
-  int overflow;
-};
-
-__device__ void tile_table(const CompactParams& p, long long base, long long item0, TileTable& T, bool bf16) {
-  const long long ni = *p.n_items;
-  const long long* __restrict__ off = p.item_off;
-  const int t = threadIdx.x;
-  const long long i = item0 + t;
-  const long long end = base + kTile;
-  bool in = i < ni && (t == 0 || off[i] < end);
-  if (in) {
-    int r = p.item_row[i];
-    T.start[t] = off[i] - base;
-    T.thr[t] = p.tau * __uint_as_float(p.row_max[r]);
-    if (bf16) T.scale[t] = p.slot->beam_scale[p.rows[r].beam];
-  }
-  unsigned b = __ballot_sync(0xffffffffu, in);
-  __shared__ int wcnt[kEvalThreads / 32];
-  if ((t & 31) == 0) wcnt[t >> 5] = __popc(b);
-  __syncthreads();
-  if (t == 0) {
-    int n = 0;
-    for (int k = 0; k < kEvalThreads / 32; ++k) n += wcnt[k];
-    T.n = n;
-    const long long nx = item0 + n;                  // first item after the table
-    T.start[n] = nx < ni ? off[nx] - base : p.n_cand - base;
-    T.overflow = nx < ni && off[nx] < end;
-  }
-  __syncthreads();
-}
-
-// candidates [p0, p0 + kTilePer) and their keep flags
+// candidates [p0, p0 + kTilePer) and their keep flags; item0 holds the
+// tile's first candidate, and each lane walks the (rare) item boundaries
 template <bool kCols>
-__device__ __forceinline__ void tile_keep(const CompactParams& p, long long base, long long p0, long long item0,
-                                          const TileTable& T, TileKeep& K) {
+__device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, long long tile, TileKeep& K) {
+  const long long item0 = p.tile_item0[tile];
   const long long n = p.n_cand;
   if (p0 + kTilePer <= n) {
     const float4* v4 = reinterpret_cast<const float4*>(p.vals + p0);
@@ -865,57 +828,38 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long base
       if (kCols) K.C[i] = in ? __ldcs(p.cols + p0 + i) : 0;
     }
   }
-  unsigned keep = 0;
+  const long long ni = *p.n_items;
+  const long long* __restrict__ off = p.item_off;
   const bool bf16 = kCols && p.value_dtype == 1;
-  if (!T.overflow) {
-    // last table entry starting at or before p0
-    const long long rel0 = p0 - base;
-    int lo = 0, hi = T.n - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (T.start[mid] <= rel0) lo = mid; else hi = mid - 1;
+  long long it = item0;
+  long long next = p.tile_next[tile];
+  float thr = p.tile_thr[tile];
+  float scale = bf16 ? p.tile_scale[tile] : 1.0f;
+  if (next <= p0) {                                    // this lane starts past the first boundary
+    while (next <= p0 && it + 1 < ni) {
+      ++it;
+      next = it + 1 < ni ? off[it + 1] : n;
     }
-    int k = lo;
-    long long next = T.start[k + 1];
-    float thr = T.thr[k], scale = bf16 ? T.scale[k] : 1.0f;
+    int r = p.item_row[it];
+    thr = p.tau * __uint_as_float(p.row_max[r]);
+    if (bf16) scale = p.slot->beam_scale[p.rows[r].beam];
+  }
+  unsigned keep = 0;
 #pragma unroll
-    for (int i = 0; i < kTilePer; ++i) {
-      const long long rel = rel0 + i;
-      while (rel >= next && k + 1 < T.n) {
-        ++k;
-        next = T.start[k + 1];
-        thr = T.thr[k];
-        if (bf16) scale = T.scale[k];
-      }
-      if (p0 + i < n && K.D[i] > 0.0f && K.D[i] >= thr) {
-        keep |= 1u << i;
-        if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
-      }
-    }
-  } else {
-    const long long ni = *p.n_items;
-    const long long* __restrict__ off = p.item_off;
-    long long it = item0;
-    long long next = it + 1 < ni ? off[it + 1] : n;
-    int row = -1;
-    float thr = 0.0f, scale = 1.0f;
-    for (int i = 0; i < kTilePer; ++i) {
-      const long long pos = p0 + i;
-      if (pos >= n) break;
-      while (next <= pos) {
+  for (int i = 0; i < kTilePer; ++i) {
+    const long long pos = p0 + i;
+    if (pos >= next && pos < n) {
+      while (next <= pos && it + 1 < ni) {
         ++it;
         next = it + 1 < ni ? off[it + 1] : n;
       }
-      int r = p.item_row[it];
-      if (r != row) {
-        row = r;
-        thr = p.tau * __uint_as_float(p.row_max[r]);
-        if (bf16) scale = p.slot->beam_scale[p.rows[r].beam];
-      }
-      if (K.D[i] > 0.0f && K.D[i] >= thr) {
-        keep |= 1u << i;
-        if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
-      }
+      const int r = p.item_row[it];
+      thr = p.tau * __uint_as_float(p.row_max[r]);
+      if (bf16) scale = p.slot->beam_scale[p.rows[r].beam];
+    }
+    if (pos < n && K.D[i] > 0.0f && K.D[i] >= thr) {
+      keep |= 1u << i;
+      if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
     }
   }
   K.keep = keep;
@@ -940,68 +884,66 @@ __global__ void k_tile_map(const long long* __restrict__ item_off, const long lo
   }
 }
 
-__global__ void __launch_bounds__(kEvalThreads) k_tile_count(CompactParams p, int* tile_cnt) {
-  __shared__ TileTable T;
-  __shared__ int wsum[kEvalThreads / 32];
-  const int t = threadIdx.x;
-  const long long base = (long long)blockIdx.x * kTile;
-  if (base >= p.n_cand) return;                        // uniform
-  const long long item0 = p.tile_item0[blockIdx.x];
-  tile_table(p, base, item0, T, false);
-  TileKeep K;
-  tile_keep<false>(p, base, base + (long long)t * kTilePer, item0, T, K);
-  int c = __popc(K.keep);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((t & 31) == 0) wsum[t >> 5] = c;
-  __syncthreads();
-  if (t == 0) {
-    int s = 0;
-#pragma unroll
-    for (int k = 0; k < kEvalThreads / 32; ++k) s += wsum[k];
-    tile_cnt[blockIdx.x] = s;
+// per tile, once the row maxima are final: the threshold and BF16 scale of
+// the item holding the tile's first candidate, the next item boundary, and
+// whether any item starts inside the tile (so the compaction starts from
+// independent loads instead of a chain of dependent ones)
+__global__ void k_tile_prep(CompactParams p) {
+  const long long n = p.n_cand;
+  const long long n_tiles = (n + kTile - 1) / kTile;
+  const long long ni = *p.n_items;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_tiles;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long it = p.tile_item0[t];
+    const int r = p.item_row[it];
+    p.tile_thr[t] = p.tau * __uint_as_float(p.row_max[r]);
+    p.tile_scale[t] = p.value_dtype == 1 ? p.slot->beam_scale[p.rows[r].beam] : 1.0f;
+    p.tile_next[t] = it + 1 < ni ? p.item_off[it + 1] : n;
+    const long long f = p.tile_first[t];
+    p.tile_starts[t] = f < ni && p.item_off[f] < min(n, (t + 1) * kTile);
   }
 }
 
+__global__ void __launch_bounds__(kEvalThreads) k_tile_count(CompactParams p, int* tile_cnt) {
+  const int lane = threadIdx.x & 31;
+  const long long tile = (long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5);
+  const long long base = tile * kTile;
+  if (base >= p.n_cand) return;                        // warp-uniform
+  TileKeep K;
+  tile_keep<false>(p, base + (long long)lane * kTilePer, tile, K);
+  int c = __popc(K.keep);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) tile_cnt[tile] = c;
+}
+
 __global__ void __launch_bounds__(kEvalThreads) k_tile_write(CompactParams p, const long long* __restrict__ tile_off) {
-  __shared__ int s_col[kTile];
-  __shared__ float s_val[kTile];
-  __shared__ TileTable T;
-  __shared__ int wscan[kEvalThreads / 32];
-  const int t = threadIdx.x;
+  __shared__ int s_col[kTileWarps][kTile];
+  __shared__ float s_val[kTileWarps][kTile];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long tile = (long long)blockIdx.x * kTileWarps + w;
   const long long n = p.n_cand;
-  const long long base = (long long)blockIdx.x * kTile;
-  if (base >= n) return;                               // uniform
+  const long long base = tile * kTile;
+  if (base >= n) return;                               // warp-uniform
   const long long ni = *p.n_items;
   const long long* __restrict__ off = p.item_off;
-  const long long item0 = p.tile_item0[blockIdx.x];
-  tile_table(p, base, item0, T, p.value_dtype == 1);
-  const long long p0 = base + (long long)t * kTilePer;
+  const long long p0 = base + (long long)lane * kTilePer;
   TileKeep K;
-  tile_keep<true>(p, base, p0, item0, T, K);
+  tile_keep<true>(p, p0, tile, K);
   const int cnt = __popc(K.keep);
-  const int lane = t & 31, w = t >> 5;
   int incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     int x = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += x;
   }
-  if (lane == 31) wscan[w] = incl;
-  __syncthreads();
-  int wpre = 0, tot = 0;
-#pragma unroll
-  for (int k = 0; k < kEvalThreads / 32; ++k) {
-    int x = wscan[k];
-    if (k < w) wpre += x;
-    tot += x;
-  }
-  const int excl = wpre + incl - cnt;
-  const long long prefix = tile_off[blockIdx.x];
-  // kept count before each item start in this thread's range (items starting
-  // exactly at the tile's first candidate go to thread 0)
-  {
-    long long j = t == 0 ? p.tile_first[blockIdx.x] : item0;
+  const int tot = __shfl_sync(0xffffffffu, incl, 31);
+  const int excl = incl - cnt;
+  const long long prefix = tile_off[tile];
+  // kept count before each item start in this lane's range (items starting
+  // exactly at the tile's first candidate go to lane 0)
+  if (p.tile_starts[tile]) {                           // warp-uniform
+    long long j = p.tile_first[tile];
     while (j < ni && off[j] < p0) ++j;
     for (; j < ni && off[j] < p0 + kTilePer && off[j] < n; ++j) {
       int r = (int)(off[j] - p0);
@@ -1012,24 +954,24 @@ __global__ void __launch_bounds__(kEvalThreads) k_tile_write(CompactParams p, co
 #pragma unroll
   for (int i = 0; i < kTilePer; ++i) {
     if (K.keep & (1u << i)) {
-      s_col[q] = K.C[i];
-      s_val[q] = K.D[i];
+      s_col[w][q] = K.C[i];
+      s_val[w][q] = K.D[i];
       ++q;
     }
   }
-  __syncthreads();
+  __syncwarp();
   int* col = p.slot->col;
   if (p.value_dtype == 1) {
     __nv_bfloat16* val = (__nv_bfloat16*)p.slot->val;
-    for (int k = t; k < tot; k += kEvalThreads) {
-      col[prefix + k] = s_col[k];
-      val[prefix + k] = __float2bfloat16_rn(s_val[k]);
+    for (int k = lane; k < tot; k += 32) {
+      col[prefix + k] = s_col[w][k];
+      val[prefix + k] = __float2bfloat16_rn(s_val[w][k]);
     }
   } else {
     float* val = (float*)p.slot->val;
-    for (int k = t; k < tot; k += kEvalThreads) {
-      col[prefix + k] = s_col[k];
-      val[prefix + k] = s_val[k];
+    for (int k = lane; k < tot; k += 32) {
+      col[prefix + k] = s_col[w][k];
+      val[prefix + k] = s_val[w][k];
     }
   }
 }

@@ -20,6 +20,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 
 namespace dsc {
@@ -30,6 +31,7 @@ __global__ void k_item_rows(const long long*, int, int*);
 __global__ void k_tile_map(const long long*, const long long*, long long, long long*, long long*);
 __global__ void k_eval(EvalParams);
 __global__ void k_tile_count(CompactParams, int*);
+__global__ void k_tile_prep(CompactParams);
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
@@ -269,12 +271,16 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   long long* d_tile_off = cv.take<long long>(n_tiles + 1);
   long long* d_tile_item0 = cv.take<long long>(n_tiles);
   long long* d_tile_first = cv.take<long long>(n_tiles);
-  if (!d_tile_first)
+  float* d_tile_thr = cv.take<float>(n_tiles);
+  float* d_tile_scale = cv.take<float>(n_tiles);
+  long long* d_tile_next = cv.take<long long>(n_tiles);
+  int* d_tile_starts = cv.take<int>(n_tiles);
+  if (!d_tile_starts)
     return na_fail(DSC_E_INVAL, "needs %zu bytes of working memory for %lld candidate pairs; the fixed maximum is %zu",
                    cv.need, n_cand, kNoAllocBytes);
 
   // evaluation and compaction
-  EvalParams ep;
+  EvalParams ep{};
   ep.inst = d_inst;
   ep.rows = d_rows;
   ep.tables = d_tables;
@@ -301,7 +307,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   q.inst_begin = d_inst_begin;
   q.status = d_status;
   NA_CU(cudaMemcpyAsync(d_slot, &q, sizeof(OutSlot), cudaMemcpyHostToDevice, s));
-  CompactParams cp;
+  CompactParams cp{};
   cp.rows = d_rows;
   cp.item_off = d_item_off;
   cp.item_row = d_item_row;
@@ -314,12 +320,18 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.item_out = d_item_out;
   cp.tile_item0 = d_tile_item0;
   cp.tile_first = d_tile_first;
+  cp.tile_thr = d_tile_thr;
+  cp.tile_scale = d_tile_scale;
+  cp.tile_next = d_tile_next;
+  cp.tile_starts = d_tile_starts;
   cp.value_dtype = DSC_VALUE_F32;
+  cp.slot = d_slot;
   k_tile_map<<<256, 256, 0, s>>>(d_item_off, n_items_dev, n_cand, d_tile_item0, d_tile_first);
   NA_LAUNCH();
-  cp.slot = d_slot;
+  k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
+  NA_LAUNCH();
   // kept count first, so the capacity is checked before any output is touched
-  const unsigned tiles = (unsigned)(n_tiles > 0 ? n_tiles : 1);
+  const unsigned tiles = (unsigned)(n_tiles > 0 ? (n_tiles + kEvalThreads / 32 - 1) / (kEvalThreads / 32) : 1);
   k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, d_tile_cnt);
   NA_LAUNCH();
   st = na_scan(d_tile_cnt, nullptr, n_tiles, d_scan, d_tile_off, s);
