@@ -590,26 +590,40 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
 // t = 1/(1 + p u) (coefficients from fit_erfc.py) and exp(-u^2) = 2^(-v^2).
 // Rounding v^2 to FP32 costs a relative error of about 4e-8 v^2 in the
 // exponential, below the fit's own 3.3e-7 where the terms matter.
-__device__ __forceinline__ float erfc_v(float v) {
+// Two arguments at once in packed FP32x2 arithmetic: one instruction per
+// pair of operations, each half rounded as the scalar fmaf / mul.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// erfc = tp * e with tp = t P(t), e = 2^(-v^2), kept apart so that callers
+// fold the last product into their own FMA
+__device__ __forceinline__ void erfc_v2(float2 v, float2& tp, float2& e) {
   constexpr float kInvSqrtL = 0.83255461115769775635f;   // 1 / sqrt(log2 e)
-  float t = rcp_approx(fmaf(kErfcP * kInvSqrtL, v, 1.0f));
-  float p = kErfcC[kErfcN];
+  const float2 den = __ffma2_rn(f2(kErfcP * kInvSqrtL), v, f2(1.0f));
+  const float2 t = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+  float2 p = kErfcC2[kErfcN];
 #pragma unroll
-  for (int k = kErfcN - 1; k >= 0; --k) p = fmaf(p, t, kErfcC[k]);
-  float e = ex2_approx(-(v * v));
-  return (t * p) * e;
+  for (int k = kErfcN - 1; k >= 0; --k) p = __ffma2_rn(p, t, kErfcC2[k]);
+  const float2 vv = __fmul2_rn(v, v);
+  e = make_float2(ex2_approx(-vv.x), ex2_approx(-vv.y));
+  tp = __fmul2_rn(t, p);
 }
 
-// erf(u1) + erf(u2) for u1 = (h - |x'|)/s, u2 = (h + |x'|)/s (h >= 0), from
-// the scaled arguments v = u sqrt(log2 e): inside the beamlet
-// 2 - erfc(u1) - erfc(u2), outside erfc(|u1|) - erfc(u2) (no cancellation of
-// 1 - erf in the tails)
-__device__ __forceinline__ float erf_pair(float h, float ax, float inv_s) {
-  float v1 = (h - ax) * inv_s;
-  float v2 = (h + ax) * inv_s;
-  float e1 = erfc_v(fabsf(v1));
-  float e2 = erfc_v(v2);
-  return (v1 >= 0.0f ? 2.0f - e1 : e1) - e2;
+// The X and Z factors of one Eq. 3 component together:
+//   erf(u1) + erf(u2), u1 = (h - |x'|)/s, u2 = (h + |x'|)/s, h = c2/2 a_t
+// (b_t for Z), from the scaled arguments v = u sqrt(log2 e); inside the
+// beamlet 2 - erfc(u1) - erfc(u2), outside erfc(|u1|) - erfc(u2) (no
+// cancellation of 1 - erf in the tails).  abt = (a_t, b_t),
+// axz = (|x'|, |z'|); h -/+ |x'| and the final sums round once (FMA).
+__device__ __forceinline__ float2 erf_pair2(float c2h, float2 abt, float2 axz, float inv_s) {
+  const float2 v1 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, make_float2(-axz.x, -axz.y)), f2(inv_s));
+  const float2 v2 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, axz), f2(inv_s));
+  float2 tp1, e1, tp2, e2;
+  erfc_v2(make_float2(fabsf(v1.x), fabsf(v1.y)), tp1, e1);
+  erfc_v2(v2, tp2, e2);
+  const float2 in = __ffma2_rn(make_float2(-tp1.x, -tp1.y), e1, f2(2.0f));   // 2 - erfc(u1)
+  const float2 out = __fmul2_rn(tp1, e1);                                     // erfc(|u1|)
+  const float2 sel = make_float2(v1.x >= 0.0f ? in.x : out.x, v1.y >= 0.0f ? in.y : out.y);
+  return __ffma2_rn(make_float2(-tp2.x, -tp2.y), e2, sel);
 }
 
 // everything the per-pair evaluation reads, loaded once per work item
@@ -661,35 +675,32 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 s
   float w = fminf(g - kl, 1.0f);
   int kk = (int)kl;
   float4 A = __ldg(C.lut + kk), B = __ldg(C.lut + kk + 1);
-  float4 P;
-  P.x = fmaf(w, B.x - A.x, A.x);
-  P.y = fmaf(w, B.y - A.y, A.y);
-  P.z = fmaf(w, B.z - A.z, A.z);
-  P.w = fmaf(w, B.w - A.w, A.w);
+  const float2 Axy = make_float2(A.x, A.y), Azw = make_float2(A.z, A.w);
+  const float2 Pxy = __ffma2_rn(f2(w), __ffma2_rn(Axy, f2(-1.0f), make_float2(B.x, B.y)), Axy);
+  const float2 Pzw = __ffma2_rn(f2(w), __ffma2_rn(Azw, f2(-1.0f), make_float2(B.z, B.w)), Azw);
 
-  float a_t = C.a_sad * t, b_t = C.b_sad * t;
-  float ax = fabsf(xp), az = fabsf(zp);
+  const float2 abt = __fmul2_rn(make_float2(C.a_sad, C.b_sad), f2(t));   // (a_t, b_t)
+  const float2 axz = make_float2(fabsf(xp), fabsf(zp));
   if (mode == 1) {
-    float lim = C.cutoff_k * P.y;
-    if (ax > fmaf(0.5f, a_t, lim) || az > fmaf(0.5f, b_t, lim)) return -1.0f;
+    float lim = C.cutoff_k * Pxy.y;
+    if (axz.x > fmaf(0.5f, abt.x, lim) || axz.y > fmaf(0.5f, abt.y, lim)) return -1.0f;
   }
   // Eq. 3: three erf-pair products; arguments scaled by sqrt(log2 e):
   // 1/(sqrt(2) c3) * sqrt(log2 e) = sqrt(log2(e)/2) / c3
   constexpr float kSqrtHalfL = 0.84932180028801904272f;
-  float c3[3] = {P.y, P.z, P.w};
+  const float c3[3] = {Pxy.y, Pzw.x, Pzw.y};
   float F = 0.0f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    float inv_s = kSqrtHalfL * rcp_approx(c3[i]);
-    float X = erf_pair(C.c2h[i] * a_t, ax, inv_s);
-    float Z = erf_pair(C.c2h[i] * b_t, az, inv_s);
-    F = fmaf(C.c1q[i] * X, Z, F);
+    const float inv_s = kSqrtHalfL * rcp_approx(c3[i]);
+    const float2 XZ = erf_pair2(C.c2h[i], abt, axz, inv_s);
+    F = fmaf(C.c1q[i] * XZ.x, XZ.y, F);
   }
   // Eq. 2 with A = T(d) (SAD/t)^2; 1/t with one Newton step
   float it = rcp_approx(t);
   it = fmaf(it, fmaf(-t, it, 1.0f), it);
   float q = C.sad * it;
-  return P.x * (q * q) * F;
+  return Pxy.x * (q * q) * F;
 }
 
 __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const DInst& G, const float* tab) {
