@@ -594,36 +594,40 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
 // pair of operations, each half rounded as the scalar fmaf / mul.
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// erfc = tp * e with tp = t P(t), e = 2^(-v^2), kept apart so that callers
-// fold the last product into their own FMA
-__device__ __forceinline__ void erfc_v2(float2 v, float2& tp, float2& e) {
-  constexpr float kInvSqrtL = 0.83255461115769775635f;   // 1 / sqrt(log2 e)
-  const float2 den = __ffma2_rn(f2(kErfcP * kInvSqrtL), v, f2(1.0f));
+// t = 1/(1 + p |v|) from the denominators, tp = t P(t) (P from `c`: the
+// fitted coefficients, or their negatives for -t P(t)), e = 2^(-v^2);
+// erfc(|u|) = tp e, kept apart so that callers fold the product into an FMA
+__device__ __forceinline__ void erfc_parts(float2 den, float2 v, const float2* __restrict__ c, float2& tp,
+                                           float2& e) {
   const float2 t = make_float2(rcp_approx(den.x), rcp_approx(den.y));
-  float2 p = kErfcC2[kErfcN];
+  float2 p = c[kErfcN];
 #pragma unroll
-  for (int k = kErfcN - 1; k >= 0; --k) p = __ffma2_rn(p, t, kErfcC2[k]);
+  for (int k = kErfcN - 1; k >= 0; --k) p = __ffma2_rn(p, t, c[k]);
   const float2 vv = __fmul2_rn(v, v);
   e = make_float2(ex2_approx(-vv.x), ex2_approx(-vv.y));
   tp = __fmul2_rn(t, p);
 }
 
 // The X and Z factors of one Eq. 3 component together:
-//   erf(u1) + erf(u2), u1 = (h - |x'|)/s, u2 = (h + |x'|)/s, h = c2/2 a_t
-// (b_t for Z), from the scaled arguments v = u sqrt(log2 e); inside the
-// beamlet 2 - erfc(u1) - erfc(u2), outside erfc(|u1|) - erfc(u2) (no
-// cancellation of 1 - erf in the tails).  abt = (a_t, b_t),
-// axz = (|x'|, |z'|); h -/+ |x'| and the final sums round once (FMA).
-__device__ __forceinline__ float2 erf_pair2(float c2h, float2 abt, float2 axz, float inv_s) {
-  const float2 v1 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, make_float2(-axz.x, -axz.y)), f2(inv_s));
-  const float2 v2 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, axz), f2(inv_s));
-  float2 tp1, e1, tp2, e2;
-  erfc_v2(make_float2(fabsf(v1.x), fabsf(v1.y)), tp1, e1);
-  erfc_v2(v2, tp2, e2);
-  const float2 in = __ffma2_rn(make_float2(-tp1.x, -tp1.y), e1, f2(2.0f));   // 2 - erfc(u1)
-  const float2 out = __fmul2_rn(tp1, e1);                                     // erfc(|u1|)
-  const float2 sel = make_float2(v1.x >= 0.0f ? in.x : out.x, v1.y >= 0.0f ? in.y : out.y);
-  return __ffma2_rn(make_float2(-tp2.x, -tp2.y), e2, sel);
+//   erf(u1) + erf(u2) = erfc(-u1) - erfc(u2),
+//   u1 = (h - |x'|)/s, u2 = (h + |x'|)/s, h = c2/2 a_t (b_t for Z),
+// from the scaled arguments v = u sqrt(log2 e).  erfc(-u1) is erfc(|u1|)
+// outside the beamlet and 2 - erfc(|u1|) inside (no cancellation of 1 - erf
+// in the tails); the sign bit of -u1 picks the form.  abt = (a_t, b_t),
+// axz = (|x'|, |z'|), c2hn = -c2/2; h -/+ |x'| and the final sums round once.
+__device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, float2 axz, float inv_s) {
+  constexpr float kPs = kErfcP * 0.83255461115769775635f;   // p / sqrt(log2 e)
+  const float2 x = __fmul2_rn(__ffma2_rn(f2(c2hn), abt, axz), f2(inv_s));   // -u1 sqrt(log2 e)
+  const float2 v2 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, axz), f2(inv_s));  //  u2 sqrt(log2 e) >= 0
+  float2 tp1, e1, tp2n, e2;
+  erfc_parts(make_float2(fmaf(kPs, fabsf(x.x), 1.0f), fmaf(kPs, fabsf(x.y), 1.0f)), x, kErfcC2, tp1, e1);
+  erfc_parts(__ffma2_rn(f2(kPs), v2, f2(1.0f)), v2, kErfcC2n, tp2n, e2);
+  // erfc(x) = s tp e + (1 - s), s = sign of x: the sign bit flips tp, and
+  // shifted right by one it is the bit pattern of 2.0f
+  const unsigned sx = __float_as_uint(x.x) & 0x80000000u, sy = __float_as_uint(x.y) & 0x80000000u;
+  const float2 tps = make_float2(__uint_as_float(__float_as_uint(tp1.x) ^ sx), __uint_as_float(__float_as_uint(tp1.y) ^ sy));
+  const float2 erfc_x = __ffma2_rn(tps, e1, make_float2(__uint_as_float(sx >> 1), __uint_as_float(sy >> 1)));
+  return __ffma2_rn(tp2n, e2, erfc_x);
 }
 
 // everything the per-pair evaluation reads, loaded once per work item
@@ -635,7 +639,7 @@ struct RowConst {
   const float* tab;      // the row's depth table
   const float4* lut;     // beam-model table
   float lut_scale, lut_last;
-  float c1q[3], c2h[3];
+  float c1q[3], c2h[3], c2hn[3];   // c1/4, c2/2, -c2/2
   float cutoff_k;
 };
 
@@ -693,7 +697,7 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 s
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const float inv_s = kSqrtHalfL * rcp_approx(c3[i]);
-    const float2 XZ = erf_pair2(C.c2h[i], abt, axz, inv_s);
+    const float2 XZ = erf_pair2(C.c2h[i], C.c2hn[i], abt, axz, inv_s);
     F = fmaf(C.c1q[i] * XZ.x, XZ.y, F);
   }
   // Eq. 2 with A = T(d) (SAD/t)^2; 1/t with one Newton step
@@ -718,7 +722,7 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
   C.lut = G.lut;
   C.lut_scale = G.lut_scale;
   C.lut_last = (float)(G.n_lut - 1);
-  for (int i = 0; i < 3; ++i) { C.c1q[i] = G.c1q[i]; C.c2h[i] = G.c2h[i]; }
+  for (int i = 0; i < 3; ++i) { C.c1q[i] = G.c1q[i]; C.c2h[i] = G.c2h[i]; C.c2hn[i] = -G.c2h[i]; }
   C.cutoff_k = G.cutoff_k;
 }
 
