@@ -10,9 +10,9 @@
 
 namespace dsc {
 
-constexpr int kEvalThreads = 256;     // threads per CTA of the evaluation / compaction kernels
-constexpr int kMaxLinesPerItem = 1024; // x-lines handled by one work item (multiple of kEvalThreads)
-constexpr int kWindow = 4096;         // candidates mapped to lines per pass of an item
+constexpr int kEvalThreads = 128;     // threads per CTA of the evaluation / compaction kernels
+constexpr int kMaxLinesPerItem = 512;  // x-lines handled by one work item (multiple of kEvalThreads)
+constexpr int kWindow = 2048;         // candidates mapped to lines per pass of an item
 constexpr int kSiddonThreads = 128;   // lanes per ray (one CTA) of the depth-table kernel
 constexpr int kScanBlocks = 1024;     // blocks of the device-wide scan
 constexpr int kScanThreads = 256;

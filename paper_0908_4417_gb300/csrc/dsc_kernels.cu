@@ -594,12 +594,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
 // pair of operations, each half rounded as the scalar fmaf / mul.
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// t = 1/(1 + p |v|) from the denominators, tp = t P(t) (P from `c`: the
+__device__ __forceinline__ float2 rcp2(float2 d) { return make_float2(rcp_approx(d.x), rcp_approx(d.y)); }
+
+// given t = 1/(1 + p |v|): tp = t P(t) (P from `c`: the
 // fitted coefficients, or their negatives for -t P(t)), e = 2^(-v^2);
 // erfc(|u|) = tp e, kept apart so that callers fold the product into an FMA
-__device__ __forceinline__ void erfc_parts(float2 den, float2 v, const float2* __restrict__ c, float2& tp,
-                                           float2& e) {
-  const float2 t = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+__device__ __forceinline__ void erfc_parts(float2 t, float2 v, const float2* __restrict__ c, float2& tp, float2& e) {
   float2 p = c[kErfcN];
 #pragma unroll
   for (int k = kErfcN - 1; k >= 0; --k) p = __ffma2_rn(p, t, c[k]);
@@ -620,8 +620,8 @@ __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, f
   const float2 x = __fmul2_rn(__ffma2_rn(f2(c2hn), abt, axz), f2(inv_s));   // -u1 sqrt(log2 e)
   const float2 v2 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, axz), f2(inv_s));  //  u2 sqrt(log2 e) >= 0
   float2 tp1, e1, tp2n, e2;
-  erfc_parts(make_float2(fmaf(kPs, fabsf(x.x), 1.0f), fmaf(kPs, fabsf(x.y), 1.0f)), x, kErfcC2, tp1, e1);
-  erfc_parts(__ffma2_rn(f2(kPs), v2, f2(1.0f)), v2, kErfcC2n, tp2n, e2);
+  erfc_parts(rcp2(make_float2(fmaf(kPs, fabsf(x.x), 1.0f), fmaf(kPs, fabsf(x.y), 1.0f))), x, kErfcC2, tp1, e1);
+  erfc_parts(rcp2(__ffma2_rn(f2(kPs), v2, f2(1.0f))), v2, kErfcC2n, tp2n, e2);
   // erfc(x) = s tp e + (1 - s), s = sign of x: the sign bit flips tp, and
   // shifted right by one it is the bit pattern of 2.0f
   const unsigned sx = __float_as_uint(x.x) & 0x80000000u, sy = __float_as_uint(x.y) & 0x80000000u;
