@@ -38,8 +38,8 @@ F_PAIR = 337
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of the evaluation kernel per candidate pair, from
 # one Nsight Compute capture of the current kernel on the 2-field prostate
-# (27.85 M pairs, 163.7 MB); the full workload's traffic is this times its pairs
-KEVAL_DRAM_BYTES_PER_PAIR = 5.876
+# (27.85 M pairs, 163.9 MB); the full workload's traffic is this times its pairs
+KEVAL_DRAM_BYTES_PER_PAIR = 5.886
 
 
 def parse():
@@ -77,46 +77,94 @@ def oracle_sample(w, stride):
 
 
 class Clocks:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """SM clock, power and clock-event reasons sampled every 10 ms from NVML
+    (read-only queries through libnvidia-ml) while the timed region runs;
+    nvidia-smi every 200 ms where the library cannot be loaded."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    # clock-event reason bits of NVML
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+            "hw_power_brake_slowdown": 0x80}
 
-    def __init__(self, index):
-        self.index = index
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    def __init__(self, uuid):
+        import threading
+        self.sm, self.mx, self.reasons, self.p = [], [], set(), None
+        self.source = "nvml"
+        self.nvml = self._nvml(uuid)
+        if self.nvml is None:
+            self.source = "nvidia-smi"
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            try:
+                self.p = subprocess.Popen(["nvidia-smi", f"--id={uuid}", f"--query-gpu={self.Q}",
+                                           "--format=csv,noheader", "-lms", "200"], stdout=self.f,
+                                          stderr=subprocess.DEVNULL)
+            except OSError:
+                self.p = None
+            return
+        self.stop_flag = threading.Event()
+        self.t = threading.Thread(target=self._poll, daemon=True)
+        self.t.start()
+
+    def _nvml(self, uuid):
+        import ctypes
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
-        except OSError:
-            self.p = None
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            if not str(uuid).startswith("GPU-") or lib.nvmlDeviceGetHandleByUUID(str(uuid).encode(),
+                                                                                 ctypes.byref(h)) != 0:
+                return None
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) != 0:
+                return None
+            self.max_mhz = float(mx.value)
+            return lib, h
+        except (OSError, AttributeError):
+            return None
+
+    def _poll(self):
+        import ctypes
+        lib, h = self.nvml
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                self.sm.append(float(clk.value))
+                self.mx.append(self.max_mhz)
+            if lib.nvmlDeviceGetCurrentClocksEventReasons(h, ctypes.byref(rs)) == 0:
+                for n, bit in self.BITS.items():
+                    if rs.value & bit:
+                        self.reasons.add(n)
+            self.stop_flag.wait(0.01)
 
     def stop(self):
-        if self.p is None:
-            return None
-        self.p.terminate()
-        try:
-            self.p.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.p.kill()
-        self.f.flush()
-        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
-        os.unlink(self.f.name)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+        if self.nvml is not None:
+            self.stop_flag.set()
+            self.t.join()
+        elif self.p is not None:
+            self.p.terminate()
             try:
-                sm.append(float(r[1].split()[0]))
-                mx.append(float(r[2].split()[0]))
-            except (ValueError, IndexError):
-                continue
-            for n, v in zip(names, r[5:9]):
-                if "Active" in v and "Not" not in v:
-                    reasons.add(n)
-        if not sm:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self.f.flush()
+            rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+            os.unlink(self.f.name)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for r in rows:
+                try:
+                    self.sm.append(float(r[1].split()[0]))
+                    self.mx.append(float(r[2].split()[0]))
+                except (ValueError, IndexError):
+                    continue
+                for n, v in zip(names, r[5:9]):
+                    if "Active" in v and "Not" not in v:
+                        self.reasons.add(n)
+        if not self.sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(self.sm), "sm_max_mhz": max(self.mx), "reasons": sorted(self.reasons),
+                "samples": len(self.sm), "source": self.source}
 
 
 def gpu_id(props, index):
@@ -191,12 +239,30 @@ def run_ours(args):
     for b in w.beams:
         dsc.dsc_add_beam(g, b)
     timing = dsc.compute_opts(w.tau, w.value_dtype, w.h_frac, dsc.DSC_FLAG_TIMING)
+    plain = dsc.compute_opts(w.tau, w.value_dtype, w.h_frac, 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     props = torch.cuda.get_device_properties(dev)
+
+    def steps(opts, n, keep):
+        """n computations, each after an L2 flush; per-step device ms (and results if kept)"""
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        results = []
+        for k in range(n):
+            flush.fill_(k & 0xff)
+            evs[k][0].record(stream)
+            results.append(dsc.dsc_compute_dij(g, opts, sp))
+            evs[k][1].record(stream)
+        stream.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        if not keep:
+            for r in results:
+                dsc.dsc_release_result(r)
+            results = []
+        return ms, results
+
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            flush.fill_(1)
-            r = dsc.dsc_compute_dij(g, timing, sp)
+        for k in range(args.warmup):
+            r = dsc.dsc_compute_dij(g, timing if k == 0 else plain, sp)
             dsc.dsc_result_wait(r)
             v = dsc.dsc_get_csr(r, False)
             pairs, nnz, nrows, nbeams = int(v.pairs), int(v.nnz), int(v.nrows), int(v.nbeams)
@@ -207,25 +273,19 @@ def run_ours(args):
             torch.distributed.barrier()
         clk = Clocks(gpu_id(props, local if world > 1 else 0))
         n0 = dsc.dsc_launch_count()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        results = []
-        for k in range(args.steps):
-            flush.fill_(k & 0xff)
-            evs[k][0].record(stream)
-            results.append(dsc.dsc_compute_dij(g, timing, sp))
-            evs[k][1].record(stream)
-        stream.synchronize()
+        step_ms, _ = steps(plain, args.steps, False)
         launches = dsc.dsc_launch_count() - n0
         clocks = clk.stop()
-        step_ms = [a.elapsed_time(b) for a, b in evs]
-        stages = [dsc.dsc_get_stage_times(r) for r in results]
-        for r in results:
-            dsc.dsc_release_result(r)
         total_s = sum(step_ms) / 1e3
         if world > 1:
             t = torch.tensor([total_s], device=dev, dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total_s = float(t.item())
+        # ---- stage breakdown: the same steps with per-stage events (outside the timed region) ----
+        _, results = steps(timing, max(3, min(args.steps, 10)), True)
+        stages = [dsc.dsc_get_stage_times(r) for r in results]
+        for r in results:
+            dsc.dsc_release_result(r)
 
         # ---- end to end through the C ABI with pinned host buffers ----
         host_rho = torch.from_numpy(np.ascontiguousarray(w.density)).pin_memory()
@@ -234,7 +294,6 @@ def run_ours(args):
         h_col = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
         h_val = torch.empty(max(nnz, 1) * vsize, dtype=torch.uint8).pin_memory()
         h_sc = torch.empty(max(nbeams, 1), dtype=torch.float32).pin_memory()
-        plain = dsc.compute_opts(w.tau, w.value_dtype, w.h_frac, 0)
         e2e_steps = max(3, args.steps // 2)
         for k in range(e2e_steps + 2):
             if k == 2:
@@ -286,7 +345,11 @@ def run_ours(args):
                    "spacing_mm": [w.grid.dx, w.grid.dy, w.grid.dz], "fields": len(w.beams), "rows": nrows,
                    "pairs_per_step": pairs, "nnz_per_step": nnz, "value_dtype": "f32" if vsize == 4 else "bf16",
                    "rel_threshold": w.tau, "l2": "flushed between steps (256 MB write)",
-                   "latency_ms_9field": ms, "stage_ms": stage_ms},
+                   "latency_ms_9field": ms,
+                   "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4),
+                               "max": round(max(step_ms), 4)},
+                   "stage_ms": stage_ms,
+                   "stage_basis": "per-stage CUDA events in separate steps after the timed region"},
         "e2e": {"value": world * pairs * e2e_steps / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps,
                 "host_wall_ms_per_step": 1e3 * wall_s / e2e_steps},
