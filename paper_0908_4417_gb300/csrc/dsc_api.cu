@@ -41,6 +41,7 @@ __global__ void k_eval(EvalParams);
 __global__ void k_beam_scale(const DBeam*, int, const unsigned*, const OutSlot*);
 __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_tile_prep(CompactParams);
+__global__ void k_lut_pairs(const float4*, int, float4*);
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
@@ -364,9 +365,17 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
   g->c3max = c3max;
   size_t nvox = (size_t)grid->nx * grid->ny * grid->nz;
   dsc_status st = dalloc(&g->d_rho, nvox, s);
-  if (st == DSC_OK) st = dalloc(&g->d_lut, (size_t)model->n, s);
+  float4* rows = nullptr;
+  if (st == DSC_OK) st = dalloc(&g->d_lut, 2 * (size_t)model->n, s);
+  if (st == DSC_OK) st = dalloc(&rows, (size_t)model->n, s);
   if (st != DSC_OK) { dsc_destroy_geometry(g); return st; }
-  cudaError_t e = cudaMemcpyAsync(g->d_lut, model->table4, sizeof(float4) * model->n, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(rows, model->table4, sizeof(float4) * model->n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(rows, model->n, g->d_lut);
+    e = cudaGetLastError();
+  }
+  cudaError_t ef = cudaFreeAsync(rows, s);
+  if (e == cudaSuccess) e = ef;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->d_rho, density, nvox * sizeof(float),
                         density_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);

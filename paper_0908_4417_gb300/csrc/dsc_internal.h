@@ -23,7 +23,7 @@ struct ff { float hi, lo; };
 // One geometry of a launch.
 struct DInst {
   const float* rho;        // density [nz][ny][nx]
-  const float4* lut;       // n_lut rows {T, c3_1, c3_2, c3_3}
+  const float4* lut;       // n_lut entries {row k, row k+1 - row k}, rows {T, c3_1, c3_2, c3_3}
   int nx, ny, nz;
   int n_lut;
   double dx, dy, dz;

@@ -622,11 +622,10 @@ __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, f
   float2 tp1, e1, tp2n, e2;
   erfc_parts(rcp2(make_float2(fmaf(kPs, fabsf(x.x), 1.0f), fmaf(kPs, fabsf(x.y), 1.0f))), x, kErfcC2, tp1, e1);
   erfc_parts(rcp2(__ffma2_rn(f2(kPs), v2, f2(1.0f))), v2, kErfcC2n, tp2n, e2);
-  // erfc(x) = s tp e + (1 - s), s = sign of x: the sign bit flips tp, and
-  // shifted right by one it is the bit pattern of 2.0f
-  const unsigned sx = __float_as_uint(x.x) & 0x80000000u, sy = __float_as_uint(x.y) & 0x80000000u;
-  const float2 tps = make_float2(__uint_as_float(__float_as_uint(tp1.x) ^ sx), __uint_as_float(__float_as_uint(tp1.y) ^ sy));
-  const float2 erfc_x = __ffma2_rn(tps, e1, make_float2(__uint_as_float(sx >> 1), __uint_as_float(sy >> 1)));
+  // erfc(x) = (1 - s) + s tp e, s = +-1 the sign of x (its sign bit on 1.0f)
+  const float2 sg = make_float2(__uint_as_float((__float_as_uint(x.x) & 0x80000000u) | 0x3f800000u),
+                                __uint_as_float((__float_as_uint(x.y) & 0x80000000u) | 0x3f800000u));
+  const float2 erfc_x = __ffma2_rn(__fmul2_rn(sg, tp1), e1, __ffma2_rn(sg, f2(-1.0f), f2(1.0f)));
   return __ffma2_rn(tp2n, e2, erfc_x);
 }
 
@@ -678,10 +677,9 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 s
   float kl = fminf(floorf(g), C.lut_last - 1.0f);
   float w = fminf(g - kl, 1.0f);
   int kk = (int)kl;
-  float4 A = __ldg(C.lut + kk), B = __ldg(C.lut + kk + 1);
-  const float2 Axy = make_float2(A.x, A.y), Azw = make_float2(A.z, A.w);
-  const float2 Pxy = __ffma2_rn(f2(w), __ffma2_rn(Axy, f2(-1.0f), make_float2(B.x, B.y)), Axy);
-  const float2 Pzw = __ffma2_rn(f2(w), __ffma2_rn(Azw, f2(-1.0f), make_float2(B.z, B.w)), Azw);
+  const float4 A = __ldg(C.lut + 2 * kk), dA = __ldg(C.lut + 2 * kk + 1);   // row kk, row kk+1 - row kk
+  const float2 Pxy = __ffma2_rn(f2(w), make_float2(dA.x, dA.y), make_float2(A.x, A.y));
+  const float2 Pzw = __ffma2_rn(f2(w), make_float2(dA.z, dA.w), make_float2(A.z, A.w));
 
   const float2 abt = __fmul2_rn(make_float2(C.a_sad, C.b_sad), f2(t));   // (a_t, b_t)
   const float2 axz = make_float2(fabsf(xp), fabsf(zp));
@@ -782,6 +780,20 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalParams p) {
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// beam-model table as the evaluation reads it: entry k = {row k, row k+1 -
+// row k} (the FP32 difference the linear interpolation forms; zero for the
+// last row), so one interpolation is one FMA per column
+// ---------------------------------------------------------------------------
+__global__ void k_lut_pairs(const float4* __restrict__ rows, int n, float4* __restrict__ pairs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float4 a = rows[k];
+  const float4 b = k + 1 < n ? rows[k + 1] : a;
+  pairs[2 * k] = a;
+  pairs[2 * k + 1] = make_float4(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y), __fsub_rn(b.z, a.z), __fsub_rn(b.w, a.w));
 }
 
 // ---------------------------------------------------------------------------

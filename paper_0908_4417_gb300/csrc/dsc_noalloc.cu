@@ -32,6 +32,7 @@ __global__ void k_tile_map(const long long*, const long long*, long long, long l
 __global__ void k_eval(EvalParams);
 __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_tile_prep(CompactParams);
+__global__ void k_lut_pairs(const float4*, int, float4*);
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
@@ -190,7 +191,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   std::lock_guard<std::mutex> lk(g_na_mu);   // one host thread at a time carves and launches
 
   Carve cv{base};
-  float4* d_lut = cv.take<float4>(model->n);
+  float4* d_lut_rows = cv.take<float4>(model->n);
+  float4* d_lut = cv.take<float4>(2 * (size_t)model->n);
   DInst* d_inst = cv.take<DInst>(1);
   DBeam* d_beams = cv.take<DBeam>(nbeams);
   DRow* d_rows = cv.take<DRow>(nrows);
@@ -209,7 +211,9 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
     return na_fail(DSC_E_INVAL, "needs more than %zu bytes of working memory (the fixed maximum) for %d beamlets",
                    kNoAllocBytes, nrows);
 
-  NA_CU(cudaMemcpyAsync(d_lut, model->table4, sizeof(float4) * model->n, cudaMemcpyHostToDevice, s));
+  NA_CU(cudaMemcpyAsync(d_lut_rows, model->table4, sizeof(float4) * model->n, cudaMemcpyHostToDevice, s));
+  k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(d_lut_rows, model->n, d_lut);
+  NA_LAUNCH();
   I.lut = d_lut;
   NA_CU(cudaMemcpyAsync(d_inst, &I, sizeof(DInst), cudaMemcpyHostToDevice, s));
   for (int b = 0, row = 0; b < nbeams; ++b) {
