@@ -419,6 +419,8 @@ def run_batched(args):
         held.clear()
 
     with torch.cuda.stream(stream):
+        # tile shape from the autotuner, on these instances, before any timing
+        (tc, bps), tune_ms = dsc.dsc_autotune(gs, opts, sp, reps=3)
         for _ in range(args.warmup):
             batch(); drain(); sequential(); drain()
         batch()
@@ -443,6 +445,7 @@ def run_batched(args):
            "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"batched_{args.instances}", "instances": args.instances,
+                      "tuning": {"target_cand": tc, "eval_blocks_per_sm": bps, "autotune_median_ms": tune_ms},
                       "rows": sum(w.nrows for w in ws), "pairs_per_step": pairs, "nnz_per_step": nnz,
                       "l2": "working set far above L2 (no flush needed)",
                       "sequential_pairs_per_s": pairs * args.steps / t_seq,

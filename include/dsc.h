@@ -167,6 +167,30 @@ dsc_status dsc_compute_dij(dsc_geometry* geom, const dsc_compute_opts* opts, voi
  * and the options stay the same.  outs[k] receives instance k's result. */
 dsc_status dsc_compute_dij_batch(dsc_geometry* const* geoms, int32_t n, const dsc_compute_opts* opts,
                                  void* stream, dsc_result** outs);
+/* --- work decomposition ("tile shape") and its autotuner ---------------- */
+/* The evaluation walks work items of about target_cand candidate pairs (a
+ * chunk of one beamlet's x-lines, at most 512 lines) taken from a queue by a
+ * persistent kernel of eval_blocks_per_sm CTAs per SM.  The result does not
+ * depend on either value, only the time does.  Process-wide; a plan reads the
+ * setting when it is built (plans already cached keep theirs). */
+typedef struct {
+    int32_t target_cand;         /* 512 .. 65536; default 8192 */
+    int32_t eval_blocks_per_sm;  /* 0 = the occupancy limit (default), else 1 .. that limit */
+} dsc_tuning;
+/* DSC_E_INVAL outside the ranges above. */
+dsc_status dsc_set_tuning(const dsc_tuning* t);
+dsc_status dsc_get_tuning(dsc_tuning* t);
+/* Times every tile shape of a fixed set (target_cand 2048 .. 32768 by powers
+ * of two x eval_blocks_per_sm {limit, 3/4 limit, 1/2 limit}) on the caller's
+ * geometries: per shape a fresh plan, one warm-up, then `reps` (1 .. 100)
+ * replays of the batched computation, each timed with CUDA events on
+ * `stream`.  Installs the shape with the lowest median time (dsc_set_tuning),
+ * and returns it and that median in milliseconds (best_ms may be NULL).
+ * Blocks until done; the plans it builds are not cached and the results are
+ * released.  geoms as for dsc_compute_dij_batch. */
+dsc_status dsc_autotune(dsc_geometry* const* geoms, int32_t n, const dsc_compute_opts* opts, void* stream,
+                        int32_t reps, dsc_tuning* best, float* best_ms);
+
 /* Blocks until the result's device work has finished; returns DSC_E_TIMEOUT
  * if a bounded device wait expired, DSC_E_CUDA on a device error. */
 dsc_status dsc_result_wait(dsc_result* res);

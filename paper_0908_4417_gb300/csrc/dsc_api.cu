@@ -112,7 +112,17 @@ static void release_after(cudaEvent_t ev, int dev, void* const* ps, int n) {
     if (ps[i]) cudaFreeAsync(ps[i], fs);
 }
 
-static int g_target_cand = 8192;     // candidates per work item (tile shape)
+// work decomposition of new plans (dsc_set_tuning / dsc_autotune)
+static std::mutex g_tuning_mu;
+static dsc_tuning g_tuning = {8192, 0};
+
+namespace dsc {
+void current_tuning(int* target_cand, int* eval_blocks_per_sm) {
+  std::lock_guard<std::mutex> lk(g_tuning_mu);
+  *target_cand = g_tuning.target_cand;
+  *eval_blocks_per_sm = g_tuning.eval_blocks_per_sm;
+}
+}  // namespace dsc
 
 // ---------------------------------------------------------------------------
 // handles
@@ -222,6 +232,8 @@ struct Plan {
   cudaEvent_t last_done = nullptr;   // end of the latest computation
   cudaStream_t last_stream = nullptr;
   int grid_eval = 0, grid_items = 0;
+  int target_cand = 8192;            // candidates per work item
+  int eval_bps = 0;                  // evaluation CTAs per SM (0 = occupancy limit)
   int kernels_per_run = 0;           // kernel launches in one computation
   std::mutex mu;                     // one computation at a time per plan
   void free_scratch() {
@@ -251,10 +263,17 @@ static std::map<std::string, std::shared_ptr<Plan>> g_cache;
 static std::vector<std::string> g_cache_order;
 static const size_t kCacheMax = 16;
 
-static std::string plan_key(dsc_geometry* const* geoms, int n, const dsc_compute_opts* o) {
+static dsc_tuning tuning_now() {
+  dsc_tuning t;
+  current_tuning(&t.target_cand, &t.eval_blocks_per_sm);
+  return t;
+}
+
+static std::string plan_key(dsc_geometry* const* geoms, int n, const dsc_compute_opts* o, const dsc_tuning& tu) {
   std::string k;
   char buf[128];
-  snprintf(buf, sizeof buf, "%.17g/%d/%.17g/%d|", o->rel_threshold, o->value_dtype, o->h_frac, o->flags);
+  snprintf(buf, sizeof buf, "%.17g/%d/%.17g/%d/%d/%d|", o->rel_threshold, o->value_dtype, o->h_frac, o->flags,
+           tu.target_cand, tu.eval_blocks_per_sm);
   k += buf;
   for (int i = 0; i < n; ++i) {
     snprintf(buf, sizeof buf, "%llu:", geoms[i]->id);
@@ -449,9 +468,11 @@ static dsc_status scan_launch(const int* in, const long long* n_dev, long long n
 }
 
 static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_compute_opts* o, cudaStream_t s,
-                             std::shared_ptr<Plan>& out) {
+                             std::shared_ptr<Plan>& out, const dsc_tuning& tu) {
   auto P = std::make_shared<Plan>();
   P->opts = *o;
+  P->target_cand = tu.target_cand;
+  P->eval_bps = tu.eval_blocks_per_sm;
   P->last_stream = s;
   TRY(ensure_device(&P->device));
   P->ninst = n;
@@ -525,7 +546,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
 
   // sizes: items (from the set-up) and candidates (from the count)
   k_setup<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
-                                                 P->d_row_items, g_target_cand);
+                                                 P->d_row_items, P->target_cand);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s));
   CU(cudaMemcpyAsync(&P->n_items, P->d_row_item_base + P->nrows, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -537,7 +558,8 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   int sms = 0, nb = 0;
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval, kEvalThreads, 0));
-  P->grid_eval = std::max(1, nb) * sms;
+  nb = std::max(1, nb);
+  P->grid_eval = (P->eval_bps > 0 ? std::min(P->eval_bps, nb) : nb) * sms;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count, kEvalThreads, 0));
   P->grid_items = std::max(1, nb) * sms;
   k_item_rows<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_row_item_base, P->nrows, P->d_item_row);
@@ -565,13 +587,14 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
 
 static dsc_status plan_get(dsc_geometry* const* geoms, int n, const dsc_compute_opts* o, cudaStream_t s,
                            std::shared_ptr<Plan>& out) {
-  std::string key = plan_key(geoms, n, o);
+  const dsc_tuning tu = tuning_now();
+  std::string key = plan_key(geoms, n, o, tu);
   {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     auto it = g_cache.find(key);
     if (it != g_cache.end()) { out = it->second; return DSC_OK; }
   }
-  TRY(plan_build(geoms, n, o, s, out));
+  TRY(plan_build(geoms, n, o, s, out, tu));
   std::lock_guard<std::mutex> lk(g_cache_mu);
   g_cache[key] = out;
   g_cache_order.push_back(key);
@@ -602,7 +625,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   CU(cudaMemsetAsync(P->d_counter, 0, sizeof(int) * 4, s));
   // a1: beamlet frames, entry/exit, VOI box, work items
   k_setup<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
-                                                 P->d_row_items, g_target_cand);
+                                                 P->d_row_items, P->target_cand);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s));
   TRY(record(ev, 1, s));
@@ -793,7 +816,7 @@ static dsc_status compute_common(dsc_geometry* const* geoms, int n, const dsc_co
   if (cache) {
     TRY(plan_get(geoms, n, opts, s, P));
   } else {
-    TRY(plan_build(geoms, n, opts, s, P));
+    TRY(plan_build(geoms, n, opts, s, P, tuning_now()));
   }
   std::lock_guard<std::mutex> lk(P->mu);
   dsc_status st = run_plan(P, s, (opts->flags & DSC_FLAG_TIMING) != 0, outs);
@@ -809,6 +832,100 @@ extern "C" dsc_status dsc_compute_dij(dsc_geometry* geom, const dsc_compute_opts
 extern "C" dsc_status dsc_compute_dij_batch(dsc_geometry* const* geoms, int32_t n, const dsc_compute_opts* opts,
                                             void* stream, dsc_result** outs) {
   return compute_common(geoms, n, opts, stream, outs, true);
+}
+
+// ---------------------------------------------------------------------------
+// work decomposition and its autotuner
+// ---------------------------------------------------------------------------
+static dsc_status check_tuning(const dsc_tuning* t) {
+  if (!t) return fail(DSC_E_INVAL, "null tuning");
+  if (t->target_cand < 512 || t->target_cand > 65536 || t->eval_blocks_per_sm < 0 || t->eval_blocks_per_sm > 64)
+    return fail(DSC_E_INVAL, "tuning: need 512 <= target_cand <= 65536 and 0 <= eval_blocks_per_sm <= 64");
+  return DSC_OK;
+}
+
+extern "C" dsc_status dsc_set_tuning(const dsc_tuning* t) {
+  TRY(check_tuning(t));
+  std::lock_guard<std::mutex> lk(g_tuning_mu);
+  g_tuning = *t;
+  return DSC_OK;
+}
+
+extern "C" dsc_status dsc_get_tuning(dsc_tuning* t) {
+  if (!t) return fail(DSC_E_INVAL, "null tuning");
+  std::lock_guard<std::mutex> lk(g_tuning_mu);
+  *t = g_tuning;
+  return DSC_OK;
+}
+
+extern "C" dsc_status dsc_autotune(dsc_geometry* const* geoms, int32_t n, const dsc_compute_opts* opts, void* stream,
+                                   int32_t reps, dsc_tuning* best, float* best_ms) {
+  if (!geoms || n < 1 || !best || reps < 1 || reps > 100) return fail(DSC_E_INVAL, "autotune: bad arguments");
+  TRY(check_opts(opts));
+  for (int k = 0; k < n; ++k) {
+    if (!geoms[k]) return fail(DSC_E_INVAL, "null geometry");
+    if (geoms[k]->beams.empty()) return fail(DSC_E_STATE, "geometry %d has no beams", k);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  dsc_compute_opts o = *opts;
+  o.flags &= ~DSC_FLAG_TIMING;   // graph replays, as production calls run
+  int dev, sms = 0, nb = 0;
+  TRY(ensure_device(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval, kEvalThreads, 0));
+  nb = std::max(1, nb);
+  std::vector<int> bps_set = {0};
+  for (int b : {(3 * nb) / 4, nb / 2})
+    if (b >= 1 && b < nb && std::find(bps_set.begin(), bps_set.end(), b) == bps_set.end()) bps_set.push_back(b);
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  std::vector<dsc_result*> outs(n, nullptr);
+  auto release = [&]() {
+    for (auto& r : outs) {
+      dsc_release_result(r);
+      r = nullptr;
+    }
+  };
+  dsc_status st = DSC_OK;
+  float best_t = 1e30f;
+  dsc_tuning bt = tuning_now();
+  for (int tc = 2048; tc <= 32768 && st == DSC_OK; tc *= 2) {
+    for (int bps : bps_set) {
+      const dsc_tuning tu = {tc, bps};
+      std::shared_ptr<Plan> P;
+      st = plan_build(geoms, n, &o, s, P, tu);
+      if (st != DSC_OK) break;
+      std::lock_guard<std::mutex> lk(P->mu);
+      st = run_plan(P, s, false, outs.data());   // warm-up: captures the graph
+      release();
+      std::vector<float> t;
+      for (int r = 0; r < reps && st == DSC_OK; ++r) {
+        cudaEventRecord(e0, s);
+        st = run_plan(P, s, false, outs.data());
+        cudaEventRecord(e1, s);
+        if (st == DSC_OK) {
+          cudaError_t e = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e != cudaSuccess) st = fail(DSC_E_CUDA, "autotune timing: %s", cudaGetErrorString(e));
+          t.push_back(ms);
+        }
+        release();
+      }
+      if (st != DSC_OK) break;
+      std::sort(t.begin(), t.end());
+      const float med = t[t.size() / 2];
+      if (med < best_t) { best_t = med; bt = tu; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DSC_OK) return st;
+  TRY(dsc_set_tuning(&bt));
+  *best = bt;
+  if (best_ms) *best_ms = best_t;
+  return DSC_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -133,6 +133,9 @@ struct CompactParams {
 };
 
 // sets the text dsc_last_error() returns on the calling thread
+// process-wide work decomposition (dsc_set_tuning): candidates per work item
+// and evaluation CTAs per SM (0 = occupancy limit)
+void current_tuning(int* target_cand, int* eval_blocks_per_sm);
 void set_error(const char* msg);
 
 }  // namespace dsc

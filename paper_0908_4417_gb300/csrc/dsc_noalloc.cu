@@ -236,13 +236,15 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   int sms = 0, nb = 0;
   NA_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   NA_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval, kEvalThreads, 0));
-  const int grid_eval = (nb > 0 ? nb : 1) * sms;
+  int target_cand = 8192, eval_bps = 0;
+  current_tuning(&target_cand, &eval_bps);
+  nb = nb > 0 ? nb : 1;
+  const int grid_eval = (eval_bps > 0 && eval_bps < nb ? eval_bps : nb) * sms;
   NA_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count, kEvalThreads, 0));
   const int grid_items = (nb > 0 ? nb : 1) * sms;
-  const int kTargetCand = 8192;
 
   // set-up and work items
-  k_setup<<<(nrows + 127) / 128, 128, 0, s>>>(d_inst, d_beams, nbeams, d_rows, nrows, d_row_items, kTargetCand);
+  k_setup<<<(nrows + 127) / 128, 128, 0, s>>>(d_inst, d_beams, nbeams, d_rows, nrows, d_row_items, target_cand);
   NA_LAUNCH();
   st = na_scan(d_row_items, nullptr, nrows, d_scan, d_rib, s);
   if (st != DSC_OK) return st;

@@ -31,7 +31,7 @@ EXPORTS = [
     "dsc_compute_dij", "dsc_compute_dij_batch", "dsc_result_wait", "dsc_get_csr", "dsc_copy_csr_to_host",
     "dsc_release_result", "dsc_get_beamlets", "dsc_get_depth_tables", "dsc_get_row_stats", "dsc_get_stage_times",
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
-    "dsc_compute_dij_noalloc",
+    "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune",
 ]
 
 
@@ -53,6 +53,10 @@ class BeamDesc(C.Structure):
 class ComputeOpts(C.Structure):
     _fields_ = [("rel_threshold", C.c_double), ("value_dtype", C.c_int32), ("h_frac", C.c_double),
                 ("flags", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("target_cand", C.c_int32), ("eval_blocks_per_sm", C.c_int32)]
 
 
 class CsrView(C.Structure):
@@ -107,6 +111,10 @@ def lib():
             "dsc_server_destroy": (None, [P]),
             "dsc_compute_dij_noalloc": (C.c_int, [C.POINTER(GridDesc), P, C.POINTER(FspbModel), C.POINTER(BeamDesc),
                                                   I32, C.POINTER(ComputeOpts), P, P, P, I64, C.POINTER(I64), P]),
+            "dsc_set_tuning": (C.c_int, [C.POINTER(Tuning)]),
+            "dsc_get_tuning": (C.c_int, [C.POINTER(Tuning)]),
+            "dsc_autotune": (C.c_int, [C.POINTER(P), I32, C.POINTER(ComputeOpts), P, I32, C.POINTER(Tuning),
+                                       C.POINTER(C.c_float)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -208,6 +216,26 @@ def dsc_compute_dij_batch(geoms, opts: ComputeOpts, stream=0):
     outs = (C.c_void_p * n)()
     _check(lib().dsc_compute_dij_batch(arr, n, C.byref(opts), stream, outs))
     return [outs[i] for i in range(n)]
+
+
+def dsc_set_tuning(target_cand: int, eval_blocks_per_sm: int = 0):
+    _check(lib().dsc_set_tuning(C.byref(Tuning(int(target_cand), int(eval_blocks_per_sm)))))
+
+
+def dsc_get_tuning() -> tuple:
+    t = Tuning()
+    _check(lib().dsc_get_tuning(C.byref(t)))
+    return int(t.target_cand), int(t.eval_blocks_per_sm)
+
+
+def dsc_autotune(geoms, opts: ComputeOpts, stream=0, reps: int = 3) -> tuple:
+    """Times the tile shapes on `geoms`, installs the fastest; returns
+    ((target_cand, eval_blocks_per_sm), median ms)."""
+    n = len(geoms)
+    arr = (C.c_void_p * n)(*geoms)
+    t, ms = Tuning(), C.c_float()
+    _check(lib().dsc_autotune(arr, n, C.byref(opts), stream, int(reps), C.byref(t), C.byref(ms)))
+    return (int(t.target_cand), int(t.eval_blocks_per_sm)), float(ms.value)
 
 
 def dsc_result_wait(res):

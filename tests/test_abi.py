@@ -52,3 +52,19 @@ def test_struct_layouts_match_header():
     assert C.sizeof(dsc.BeamDesc) == 8 * 7 + 8
     assert C.sizeof(dsc.ComputeOpts) == 32
     assert C.sizeof(dsc.CsrView) == 3 * 8 + 3 * 8 + 8 + 8 + 8 + 8
+    assert C.sizeof(dsc.Tuning) == 8
+
+
+def test_tuning_is_validated_and_round_trips(lib):
+    """Host-only entry points: the work decomposition setting."""
+    before = dsc.dsc_get_tuning()
+    assert before == (8192, 0)
+    for bad in ((100, 0), (1 << 20, 0), (8192, -1), (8192, 1000)):
+        with pytest.raises(dsc.DscError):
+            dsc.dsc_set_tuning(*bad)
+    assert dsc.dsc_get_tuning() == before
+    dsc.dsc_set_tuning(4096, 3)
+    assert dsc.dsc_get_tuning() == (4096, 3)
+    dsc.dsc_set_tuning(*before)
+    assert lib.dsc_set_tuning(None) == 1 and lib.dsc_get_tuning(None) == 1
+    assert lib.dsc_autotune(None, 0, None, None, 1, None, None) == 1

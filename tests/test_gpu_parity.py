@@ -262,6 +262,42 @@ def test_batch_equals_single_and_oracle(dsc):
         dsc.dsc_destroy_geometry(g)
 
 
+def test_tile_shapes_are_bit_identical_and_autotune(dsc):
+    """The work decomposition (candidates per item, evaluation CTAs per SM)
+    changes only the time: every shape gives the same CSR bit for bit; the
+    autotuner's choice is one of its shapes and matches the oracle."""
+    ws = small_instances(3)
+    gs = [dsc.geometry_from_workload(w) for w in ws]
+    opts = dsc.compute_opts(1e-3, 0, 0.5)
+    default = dsc.dsc_get_tuning()
+    ref_res = dsc.dsc_compute_dij_batch(gs, opts)
+    ref = [dsc.HostCSR(r) for r in ref_res]
+    for r in ref_res:
+        dsc.dsc_release_result(r)
+    try:
+        for tc, bps in ((512, 0), (2048, 2), (65536, 0), (16384, 1)):
+            dsc.dsc_set_tuning(tc, bps)
+            rs = dsc.dsc_compute_dij_batch(gs, opts)
+            for k, r in enumerate(rs):
+                c = dsc.HostCSR(r)
+                assert np.array_equal(c.row_ptr, ref[k].row_ptr) and np.array_equal(c.col, ref[k].col), (tc, bps)
+                assert np.array_equal(c.val, ref[k].val), (tc, bps)
+                dsc.dsc_release_result(r)
+        (tc, bps), ms = dsc.dsc_autotune(gs, opts, reps=2)
+        assert tc in (2048, 4096, 8192, 16384, 32768) and bps >= 0 and ms > 0
+        assert dsc.dsc_get_tuning() == (tc, bps)
+        rs = dsc.dsc_compute_dij_batch(gs, opts)
+        for k, (w, r) in enumerate(zip(ws, rs)):
+            c = dsc.HostCSR(r)
+            assert np.array_equal(c.col, ref[k].col) and np.array_equal(c.val, ref[k].val)
+            compare(gpu_rows(c, range(w.nrows)), O.compute_workload(w), TOL)
+            dsc.dsc_release_result(r)
+    finally:
+        dsc.dsc_set_tuning(*default)
+        for g in gs:
+            dsc.dsc_destroy_geometry(g)
+
+
 def test_server_results_same_alone_and_in_mix(dsc):
     ws = small_instances(3)
     gs = [dsc.geometry_from_workload(w) for w in ws]
