@@ -867,24 +867,31 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
       ++it;
       next = it + 1 < ni ? off[it + 1] : n;
     }
-    int r = p.item_row[it];
+    const int r = p.item_row[it];
     thr = p.tau * __uint_as_float(p.row_max[r]);
     if (bf16) scale = p.slot->beam_scale[p.rows[r].beam];
   }
+  // kept = D > 0 and D >= thr, i.e. D >= max(thr, smallest denormal); slots
+  // past the end hold -1.  Positions relative to p0; nx = the next item
+  // boundary inside this lane's range (kTilePer: none)
+  constexpr float kTiny = 1.40129846e-45f;
+  float thr1 = fmaxf(thr, kTiny);
+  int nx = next >= n ? kTilePer : (int)min(next - p0, (long long)kTilePer);
   unsigned keep = 0;
 #pragma unroll
   for (int i = 0; i < kTilePer; ++i) {
-    const long long pos = p0 + i;
-    if (pos >= next && pos < n) {
+    if (i >= nx) {                                     // crossing into the next item(s)
+      const long long pos = p0 + i;
       while (next <= pos && it + 1 < ni) {
         ++it;
         next = it + 1 < ni ? off[it + 1] : n;
       }
       const int r = p.item_row[it];
-      thr = p.tau * __uint_as_float(p.row_max[r]);
+      thr1 = fmaxf(p.tau * __uint_as_float(p.row_max[r]), kTiny);
       if (bf16) scale = p.slot->beam_scale[p.rows[r].beam];
+      nx = next >= n ? kTilePer : (int)min(next - p0, (long long)kTilePer);
     }
-    if (pos < n && K.D[i] > 0.0f && K.D[i] >= thr) {
+    if (K.D[i] >= thr1) {
       keep |= 1u << i;
       if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
     }
