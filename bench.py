@@ -63,6 +63,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of every rank's x (the job ends when its slowest rank
+    does); the identity with one process."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, world: int, seconds: float) -> float:
+    """Units per second of the whole job: every rank processes its own
+    replica's units each step, and the job takes the slowest rank's time."""
+    return world * units_per_rank_step * steps / seconds
+
+
 def oracle_sample(w, stride):
     """Oracle pairs/s on every `stride`-th row of the workload (all host cores)."""
     import numpy as np
@@ -278,11 +296,7 @@ def run_ours(args):
         step_ms, _ = steps(plain, args.steps, False)
         launches = dsc.dsc_launch_count() - n0
         clocks = clk.stop()
-        total_s = sum(step_ms) / 1e3
-        if world > 1:
-            t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_s = float(t.item())
+        total_s = max_over_ranks(sum(step_ms) / 1e3, dev)
         # ---- stage breakdown: the same steps with per-stage events (outside the timed region) ----
         _, results = steps(timing, max(3, min(args.steps, 10)), True)
         stages = [dsc.dsc_get_stage_times(r) for r in results]
@@ -310,14 +324,14 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e1.record(stream)
         stream.synchronize()
-        e2e_s = e0.elapsed_time(e1) / 1e3
-        wall_s = time.perf_counter() - t0
+        e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
+        wall_s = max_over_ranks(time.perf_counter() - t0, dev)
 
     dsc.dsc_destroy_geometry(g)
     if rank != 0:
         return
     ms = 1e3 * total_s / args.steps
-    value = world * pairs * args.steps / total_s
+    value = whole_job_rate(pairs, args.steps, world, total_s)
     eval_ms = statistics.mean(s["eval"] for s in stages)
     achieved = F_PAIR * pairs / (eval_ms / 1e3) / 1e12
     peak_mhz = 2070.0
@@ -353,7 +367,7 @@ def run_ours(args):
                                "max": round(max(step_ms), 4)},
                    "stage_ms": stage_ms,
                    "stage_basis": "per-stage CUDA events in separate steps after the timed region"},
-        "e2e": {"value": world * pairs * e2e_steps / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(pairs, e2e_steps, world, e2e_s), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps,
                 "host_wall_ms_per_step": 1e3 * wall_s / e2e_steps},
         "gpu_launches": int(launches),

@@ -593,6 +593,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
 // Two arguments at once in packed FP32x2 arithmetic: one instruction per
 // pair of operations, each half rounded as the scalar fmaf / mul.
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+constexpr float kInvSqrtL = 0.83255461115769775635f;   // 1 / sqrt(log2 e)
 
 __device__ __forceinline__ float2 rcp2(float2 d) { return make_float2(rcp_approx(d.x), rcp_approx(d.y)); }
 
@@ -616,7 +617,7 @@ __device__ __forceinline__ void erfc_parts(float2 t, float2 v, const float2* __r
 // in the tails); the sign bit of -u1 picks the form.  abt = (a_t, b_t),
 // axz = (|x'|, |z'|), c2hn = -c2/2; h -/+ |x'| and the final sums round once.
 __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, float2 axz, float inv_s) {
-  constexpr float kPs = kErfcP * 0.83255461115769775635f;   // p / sqrt(log2 e)
+  constexpr float kPs = kErfcP * kInvSqrtL;   // p / sqrt(log2 e)
   const float2 x = __fmul2_rn(__ffma2_rn(f2(c2hn), abt, axz), f2(inv_s));   // -u1 sqrt(log2 e)
   const float2 v2 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, axz), f2(inv_s));  //  u2 sqrt(log2 e) >= 0
   float2 tp1, e1, tp2n, e2;
