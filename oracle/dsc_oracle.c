@@ -216,6 +216,59 @@ int or_depth_table(const or_grid* g, const float* rho, const or_beamlet* bl, dou
     return n;
 }
 
+/* ---------------------------------------------------------------------------
+ * Density at a point by trilinear interpolation of the voxel-centred values
+ * (Section 2.2 samples the CT this way, in software).  Along each axis the
+ * two voxel centres around the point are blended linearly; before the first
+ * centre or past the last one the edge value is used (clamp to edge).
+ * ------------------------------------------------------------------------- */
+double or_trilinear(const or_grid* g, const float* rho, const double* p) {
+    const int n[3] = {g->nx, g->ny, g->nz};
+    const double f[3] = {(p[0] - g->ox) / g->dx - 0.5, (p[1] - g->oy) / g->dy - 0.5, (p[2] - g->oz) / g->dz - 0.5};
+    int i0[3], i1[3];
+    double w[3];
+    for (int k = 0; k < 3; ++k) {
+        if (f[k] <= 0.0) { i0[k] = i1[k] = 0; w[k] = 0.0; }
+        else if (f[k] >= n[k] - 1) { i0[k] = i1[k] = n[k] - 1; w[k] = 0.0; }
+        else { i0[k] = (int)floor(f[k]); i1[k] = i0[k] + 1; w[k] = f[k] - i0[k]; }
+    }
+    double v = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int ix = (c & 1) ? i1[0] : i0[0], iy = (c & 2) ? i1[1] : i0[1], iz = (c & 4) ? i1[2] : i0[2];
+        double wt = ((c & 1) ? w[0] : 1.0 - w[0]) * ((c & 2) ? w[1] : 1.0 - w[1]) * ((c & 4) ? w[2] : 1.0 - w[2]);
+        v += wt * (double)rho[((size_t)iz * g->ny + iy) * g->nx + ix];
+    }
+    return v;
+}
+
+/* ---------------------------------------------------------------------------
+ * The paper's own table construction (Section 2.2): the density is sampled
+ * by trilinear interpolation at the n equally spaced points of AB (the same
+ * points as or_depth_table, the last one at B), and entry k is the
+ * radiological depth from A to point k, accumulated over the sample
+ * intervals by the trapezoid rule (the paper does not name the quadrature).
+ * Returns n, or -1 if cap is too small; 0 when the axis misses the grid.
+ * ------------------------------------------------------------------------- */
+int or_depth_table_trilinear(const or_grid* g, const float* rho, const or_beamlet* bl, double h, double* out,
+                             int cap) {
+    if (!bl->hit) return 0;
+    double L = bl->tB - bl->tA;
+    int n = (int)ceil(L / h) + 1;
+    if (n > cap) return -1;
+    double s_prev = 0.0, r_prev = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double s = k * h;
+        if (s > L) s = L;
+        double t = bl->tA + s;
+        double p[3] = {bl->S[0] + t * bl->e[0], bl->S[1] + t * bl->e[1], bl->S[2] + t * bl->e[2]};
+        double r = or_trilinear(g, rho, p);
+        out[k] = k == 0 ? 0.0 : out[k - 1] + (s - s_prev) * 0.5 * (r_prev + r);
+        s_prev = s;
+        r_prev = r;
+    }
+    return n;
+}
+
 /* depth at O' (Section 2.2): linear interpolation of the two neighbouring
  * table entries; s = |AO'| along the axis, clamped to [0, |AB|] */
 double or_depth_interp(const double* tab, int n, double h, double s) {
@@ -316,14 +369,15 @@ static int row_locate(const or_beam* beams, int nbeams, int64_t row, int* b, int
 }
 
 static void eval_row(const or_grid* g, const float* rho, const or_model* m, const or_beam* bm, int iu, int iv,
-                     double h, int full_scan, rowres* rr) {
+                     double h, int full_scan, int table_mode, rowres* rr) {
     or_beamlet bl;
     or_beamlet_setup(g, bm, iu, iv, &bl);
     rr->rowmax = 0.0;
     if (!bl.hit) return;
     int cap = (int)ceil((bl.tB - bl.tA) / h) + 2;
     double* tab = (double*)malloc(sizeof(double) * cap);
-    int n = or_depth_table(g, rho, &bl, h, tab, cap);
+    int n = table_mode == 1 ? or_depth_table_trilinear(g, rho, &bl, h, tab, cap)
+                            : or_depth_table(g, rho, &bl, h, tab, cap);
 
     /* voxel index box that holds the VOI: the VOI between the smallest and
      * largest t of the grid's corners is the convex hull of its two end
@@ -418,7 +472,7 @@ void or_free_result(or_result* r) {
  * available (nthreads <= 0: the runtime default). */
 int or_compute(const or_grid* g, const float* rho, const or_model* m, const or_beam* beams, int nbeams,
                double tau, double h_frac, const int64_t* rows, int64_t nsel, int nthreads, int full_scan,
-               or_result* out) {
+               int table_mode, or_result* out) {
     memset(out, 0, sizeof *out);
     int64_t total = 0;
     for (int k = 0; k < nbeams; ++k) total += (int64_t)beams[k].n_u * beams[k].n_v;
@@ -436,7 +490,7 @@ int or_compute(const or_grid* g, const float* rho, const or_model* m, const or_b
         int64_t row = rows ? rows[r] : r;
         int b, iu, iv;
         if (!row_locate(beams, nbeams, row, &b, &iu, &iv)) { bad |= 1; continue; }
-        eval_row(g, rho, m, &beams[b], iu, iv, h, full_scan, &rr[r]);
+        eval_row(g, rho, m, &beams[b], iu, iv, h, full_scan, table_mode, &rr[r]);
     }
     (void)nthreads;
     if (bad) { free(rr); return -1; }
@@ -512,14 +566,16 @@ int or_beamlets(const or_grid* g, const or_beam* beams, int nbeams, double h_fra
     return 0;
 }
 
-/* depth table of one row (b, iu, iv); returns n or -1 */
+/* depth table of one row (b, iu, iv): table_mode 0 the exact integral
+ * (Siddon), 1 trilinear samples (trapezoid); returns n or -1 */
 int or_row_table(const or_grid* g, const float* rho, const or_beam* bm, int iu, int iv, double h_frac,
-                 double* out, int cap) {
+                 int table_mode, double* out, int cap) {
     double dmin = g->dx < g->dy ? g->dx : g->dy;
     if (g->dz < dmin) dmin = g->dz;
     or_beamlet bl;
     or_beamlet_setup(g, bm, iu, iv, &bl);
-    return or_depth_table(g, rho, &bl, h_frac * dmin, out, cap);
+    return table_mode == 1 ? or_depth_table_trilinear(g, rho, &bl, h_frac * dmin, out, cap)
+                           : or_depth_table(g, rho, &bl, h_frac * dmin, out, cap);
 }
 
 /* D at arbitrary pencil-beam coordinates with the depth given (for pins):

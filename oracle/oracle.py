@@ -74,13 +74,15 @@ def lib():
         L = C.CDLL(path)
         L.or_compute.restype = C.c_int
         L.or_compute.argtypes = [C.POINTER(OrGrid), C.c_void_p, C.POINTER(OrModel), C.POINTER(OrBeam), C.c_int,
-                                 C.c_double, C.c_double, C.c_void_p, C.c_int64, C.c_int, C.c_int,
+                                 C.c_double, C.c_double, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int,
                                  C.POINTER(OrResult)]
         L.or_free_result.argtypes = [C.POINTER(OrResult)]
         L.or_beamlets.argtypes = [C.POINTER(OrGrid), C.POINTER(OrBeam), C.c_int, C.c_double, C.c_void_p]
         L.or_row_table.restype = C.c_int
         L.or_row_table.argtypes = [C.POINTER(OrGrid), C.c_void_p, C.POINTER(OrBeam), C.c_int, C.c_int,
-                                   C.c_double, C.c_void_p, C.c_int]
+                                   C.c_double, C.c_int, C.c_void_p, C.c_int]
+        L.or_trilinear.restype = C.c_double
+        L.or_trilinear.argtypes = [C.POINTER(OrGrid), C.c_void_p, C.c_void_p]
         L.or_depth_interp.restype = C.c_double
         L.or_depth_interp.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
         L.or_lut_eval.argtypes = [C.POINTER(OrModel), C.c_double, C.c_void_p]
@@ -153,8 +155,10 @@ class OracleCSR:
         return set(self.amb_col[m].tolist())
 
 
-def compute(grid, density, model, beams, tau=1e-3, h_frac=0.5, rows=None, nthreads=0, full_scan=False):
-    """D_ij over ``rows`` (global row indices) or every row."""
+def compute(grid, density, model, beams, tau=1e-3, h_frac=0.5, rows=None, nthreads=0, full_scan=False,
+            table_mode=0):
+    """D_ij over ``rows`` (global row indices) or every row.  table_mode 0:
+    depth table = exact integral (Siddon); 1: trilinear samples, trapezoid."""
     L = lib()
     g = _grid(grid)
     mr = _ModelRef(model)
@@ -168,7 +172,7 @@ def compute(grid, density, model, beams, tau=1e-3, h_frac=0.5, rows=None, nthrea
         rows = np.ascontiguousarray(rows, dtype=np.int64)
         rp, nsel = rows.ctypes.data, int(rows.size)
     rc = L.or_compute(C.byref(g), rho.ctypes.data, C.byref(mr.s), ba, len(beams), float(tau), float(h_frac),
-                      rp, nsel, int(nthreads), int(bool(full_scan)), C.byref(res))
+                      rp, nsel, int(nthreads), int(bool(full_scan)), int(table_mode), C.byref(res))
     if rc != 0:
         raise ValueError("oracle: bad row index")
     try:
@@ -179,7 +183,7 @@ def compute(grid, density, model, beams, tau=1e-3, h_frac=0.5, rows=None, nthrea
 
 def compute_workload(w, rows=None, nthreads=0, full_scan=False):
     return compute(w.grid, w.density, w.model, w.beams, tau=w.tau, h_frac=w.h_frac, rows=rows,
-                   nthreads=nthreads, full_scan=full_scan)
+                   nthreads=nthreads, full_scan=full_scan, table_mode=getattr(w, "table_mode", 0))
 
 
 def beamlets(grid, beams, h_frac=0.5) -> np.ndarray:
@@ -190,15 +194,22 @@ def beamlets(grid, beams, h_frac=0.5) -> np.ndarray:
     return out[:n]
 
 
-def row_table(grid, density, beam, iu, iv, h_frac=0.5) -> np.ndarray:
+def row_table(grid, density, beam, iu, iv, h_frac=0.5, table_mode=0) -> np.ndarray:
     rho = np.ascontiguousarray(density, dtype=np.float32)
     cap = 1 << 16
     out = np.zeros(cap, dtype=np.float64)
     n = lib().or_row_table(C.byref(_grid(grid)), rho.ctypes.data, C.byref(_beams([beam])[0]), int(iu), int(iv),
-                           float(h_frac), out.ctypes.data, cap)
+                           float(h_frac), int(table_mode), out.ctypes.data, cap)
     if n < 0:
         raise ValueError("table too long")
     return out[:n].copy()
+
+
+def trilinear(grid, density, p) -> float:
+    """Density at point p (mm) by trilinear interpolation of the voxel centres."""
+    rho = np.ascontiguousarray(density, dtype=np.float32)
+    q = np.ascontiguousarray(p, dtype=np.float64)
+    return float(lib().or_trilinear(C.byref(_grid(grid)), rho.ctypes.data, q.ctypes.data))
 
 
 def depth_interp(table, h, s) -> float:

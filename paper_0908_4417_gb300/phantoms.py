@@ -155,6 +155,9 @@ class Model:
     cutoff_k: float = 3.0
 
 
+# depth-table construction of a workload
+TABLE_EXACT, TABLE_TRILINEAR = 0, 1
+
 @dataclasses.dataclass
 class Workload:
     name: str
@@ -165,6 +168,7 @@ class Workload:
     tau: float = 1e-3        # relative threshold on the per-beamlet maximum
     h_frac: float = 0.5      # depth-table spacing as a fraction of min voxel side
     value_dtype: int = VALUE_F32
+    table_mode: int = 0      # TABLE_EXACT (Siddon integral) or TABLE_TRILINEAR (the paper's sampled table)
 
     @property
     def nrows(self) -> int:

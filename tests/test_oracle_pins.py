@@ -440,3 +440,101 @@ def test_voi_count_against_table1(case):
     assert abs(w.grid.dx - vox * 10) < 0.05 * vox * 10
     r = O.compute_workload(w)
     assert 0.5 <= r.pairs / nprime <= 1.0, r.pairs / nprime
+
+
+# ---------------------------------------------------------------------------
+# the paper's trilinear-sampled depth table (Section 2.2; NEXT-1)
+# ---------------------------------------------------------------------------
+def _tri_grid():
+    return P.Grid(7, 9, 6, 2.0, 1.5, 2.5, (-7.0, -6.75, -7.5))
+
+
+def _centre(g, ix, iy, iz):
+    return np.array([g.origin[0] + (ix + 0.5) * g.dx, g.origin[1] + (iy + 0.5) * g.dy,
+                     g.origin[2] + (iz + 0.5) * g.dz])
+
+
+def test_trilinear_reproduces_voxel_values_at_centres():
+    g = _tri_grid()
+    rho = P.random_grid_density(11, (g.nz, g.ny, g.nx))
+    for ix, iy, iz in [(0, 0, 0), (3, 4, 2), (6, 8, 5), (1, 7, 3)]:
+        assert O.trilinear(g, rho, _centre(g, ix, iy, iz)) == pytest.approx(float(rho[iz, iy, ix]), abs=1e-12)
+
+
+def test_trilinear_is_exact_on_linear_fields_and_clamps_at_the_edge():
+    """A field linear in x, y, z (stored at the voxel centres) is reproduced
+    exactly between the centre planes; past the outermost centre plane the
+    edge plane's value holds (clamp to edge), along each axis separately."""
+    g = _tri_grid()
+    a, bx, by, bz = 1.0, 0.03, -0.02, 0.05
+    zc, yc, xc = np.meshgrid(*[g.origin[k] + (np.arange(n) + 0.5) * d
+                               for k, n, d in ((2, g.nz, g.dz), (1, g.ny, g.dy), (0, g.nx, g.dx))], indexing="ij")
+    rho = (a + bx * xc + by * yc + bz * zc).astype(np.float32)
+    lin = lambda p: a + bx * p[0] + by * p[1] + bz * p[2]
+    lo = _centre(g, 0, 0, 0)
+    hi = _centre(g, g.nx - 1, g.ny - 1, g.nz - 1)
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        p = lo + rng.random(3) * (hi - lo)
+        assert O.trilinear(g, rho, p) == pytest.approx(lin(p), abs=2e-7)
+    # outside the centre span: coordinates clamp to the outermost centre, per axis
+    for p in (np.array([g.origin[0] + 0.3, 0.2, 0.1]), np.array([0.4, g.origin[1] + g.ny * g.dy, -0.2]),
+              np.array([lo[0] - 0.7, hi[1] + 0.4, hi[2] + 1.0])):
+        q = np.minimum(np.maximum(p, lo), hi)
+        assert O.trilinear(g, rho, p) == pytest.approx(lin(q), abs=2e-7)
+
+
+@pytest.mark.parametrize("gantry", [0.0, 41.0, 90.0, 222.0])
+def test_trilinear_table_uniform_density(gantry):
+    g = P.centred_grid(24, 20, 16, 3.0, 2.5, 4.0)
+    rho = np.full(g.shape, 0.83, np.float32)
+    beam = P.Beam(gantry, 400.0, (3.0, -2.0, 1.0), 6.0, 5.0, 3, 2)
+    bl = O.beamlets(g, [beam])
+    h = 0.5 * 2.5
+    for r, iu, iv in rows_of(beam):
+        tab = O.row_table(g, rho, beam, iu, iv, table_mode=1)
+        L = bl[r, 13] - bl[r, 12]
+        assert tab.size == int(math.ceil(L / h)) + 1
+        expect = float(np.float32(0.83)) * np.minimum(np.arange(tab.size) * h, L)
+        assert np.allclose(tab, expect, rtol=0, atol=1e-10)
+
+
+def test_trilinear_table_linear_field_along_the_ray():
+    """Ray along +y (gantry 0, one beamlet through the isocentre), density
+    linear in y between the first and last centre planes and clamped beyond.
+    With h = dy/2 the kinks fall on sample points, so the trapezoid rule is
+    exact: d(s) = integral of the clamped line.  The isocentre sits off the
+    voxel centres in x and z so the x and z weights matter (the field is
+    also linear in x with zero y-x coupling)."""
+    g = P.Grid(6, 10, 5, 2.0, 1.5, 2.0, (-6.0, -7.5, -5.0))
+    a, by, bx = 0.9, 0.04, 0.02
+    zc, yc, xc = np.meshgrid(*[g.origin[k] + (np.arange(n) + 0.5) * d
+                               for k, n, d in ((2, g.nz, g.dz), (1, g.ny, g.dy), (0, g.nx, g.dx))], indexing="ij")
+    rho = (a + by * yc + bx * xc).astype(np.float32)
+    x0, z0 = 0.37, -0.61
+    beam = P.Beam(0.0, 300.0, (x0, 0.0, z0), 1.0, 1.0, 1, 1)
+    tab = O.row_table(g, rho, beam, 0, 0, h_frac=0.5, table_mode=1)
+    y_first = g.origin[1] + 0.5 * g.dy
+    y_last = g.origin[1] + (g.ny - 0.5) * g.dy
+
+    def rho_y(y):
+        return a + bx * x0 + by * np.clip(y, y_first, y_last)
+
+    def integral(y1):                      # from the entry face y = origin to y1
+        ys = np.linspace(g.origin[1], y1, 20001)
+        return np.trapezoid(rho_y(ys), ys) if hasattr(np, "trapezoid") else np.trapz(rho_y(ys), ys)
+    h = 0.5 * g.dy
+    for k in range(tab.size):
+        y1 = g.origin[1] + min(k * h, g.ny * g.dy)
+        assert tab[k] == pytest.approx(integral(y1), abs=1e-6)
+
+
+def test_trilinear_table_converges_at_second_order():
+    """Halving the element length on a random field: the table's end value
+    converges to the line integral of the trilinear field at rate ~4."""
+    g = _tri_grid()
+    rho = P.random_grid_density(3, (g.nz, g.ny, g.nx))
+    beam = P.Beam(27.0, 80.0, (0.4, -0.3, 0.2), 1.0, 1.0, 1, 1)
+    ends = [O.row_table(g, rho, beam, 0, 0, h_frac=f, table_mode=1)[-1] for f in (1 / 2, 1 / 4, 1 / 8, 1 / 16)]
+    d1, d2, d3 = abs(ends[0] - ends[1]), abs(ends[1] - ends[2]), abs(ends[2] - ends[3])
+    assert d1 > 0 and d2 / d3 > 3.0 and d1 / d2 > 3.0
