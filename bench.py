@@ -2,7 +2,7 @@
 """Benchmark of the FSPB D_ij path: voxel-beamlet pairs/s and 9-field latency.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload prostate_256|slabs_128|water_32|batched|serving]
+                    [--workload prostate_256|slabs_128|water_32|batched|serving|table_study]
 
 One step = the whole path (beamlet set-up, Siddon depth tables, VOI
 enumeration, FSPB evaluation, threshold + CSR compaction) for the 9-field
@@ -554,6 +554,75 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+def run_table_study(args):
+    """The paper's element-length study (Section 3.2): the depth table at
+    full, 1/2, 1/3 and 1/4 voxel spacing, built both as the exact integral
+    (Siddon) and as the paper's trilinear samples, on the 9-field prostate.
+    Per configuration: the table stage and the whole computation's device
+    time (median of `steps`), and the change of the kept D_ij against the
+    finest trilinear table (max relative change over entries kept by both,
+    entries kept by only one)."""
+    import numpy as np
+    import torch
+    from paper_0908_4417_gb300 import build as B
+    B.build()
+    from paper_0908_4417_gb300 import dsc, phantoms as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    sp = stream.cuda_stream
+    w = P.get("prostate_256")
+    g = dsc.geometry_from_workload(w, sp)
+    fracs = [(1.0, "1"), (0.5, "1/2"), (1.0 / 3.0, "1/3"), (0.25, "1/4")]
+    # h = fraction x min voxel side (2 mm); the voxel's own size along a ray is 2-2.5 mm
+    confs = [(mode, f, lab) for mode in (0, 1) for f, lab in fracs]
+
+    def keys(c):
+        rows = np.repeat(np.arange(c.nrows, dtype=np.int64), np.diff(c.row_ptr))
+        return rows * c.ncols + c.col.astype(np.int64)
+
+    def run(mode, f, timing):
+        flags = (dsc.DSC_FLAG_TRILINEAR_TABLE if mode else 0) | (dsc.DSC_FLAG_TIMING if timing else 0)
+        return dsc.dsc_compute_dij(g, dsc.compute_opts(w.tau, w.value_dtype, f, flags), sp)
+
+    with torch.cuda.stream(stream):
+        r = run(1, 0.25, False)
+        ref = dsc.HostCSR(r)
+        dsc.dsc_release_result(r)
+        ref_k = keys(ref)
+        out = []
+        for mode, f, lab in confs:
+            for _ in range(max(1, args.warmup)):
+                dsc.dsc_release_result(run(mode, f, True))
+            tab_ms, tot_ms = [], []
+            for _ in range(args.steps):
+                r = run(mode, f, True)
+                t = dsc.dsc_get_stage_times(r)
+                tab_ms.append(t["siddon"])
+                tot_ms.append(t["total"])
+                dsc.dsc_release_result(r)
+            r = run(mode, f, False)
+            c = dsc.HostCSR(r)
+            dsc.dsc_release_result(r)
+            k = keys(c)
+            _, ia, ib = np.intersect1d(k, ref_k, assume_unique=True, return_indices=True)
+            rel = np.abs(c.val[ia].astype(np.float64) / ref.val[ib].astype(np.float64) - 1.0)
+            out.append({"table": "trilinear" if mode else "exact", "element": lab + " voxel",
+                        "h_mm": f * min(w.grid.dx, w.grid.dy, w.grid.dz),
+                        "table_ms": round(statistics.median(tab_ms), 4), "total_ms": round(statistics.median(tot_ms), 4),
+                        "nnz": int(c.nnz), "max_rel_change_vs_finest": float(rel.max()) if rel.size else 0.0,
+                        "mean_rel_change_vs_finest": float(rel.mean()) if rel.size else 0.0,
+                        "only_here": int(k.size - ia.size), "only_in_finest": int(ref_k.size - ib.size)})
+    dsc.dsc_destroy_geometry(g)
+    tri = [o for o in out if o["table"] == "trilinear"]
+    line = {"metric": "depth-table element-length study (9-field prostate)", "value": tri[1]["total_ms"],
+            "unit": "ms (trilinear table at 1/2 voxel, whole computation)", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "prostate_256", "reference": "trilinear, 1/4 voxel",
+                                           "configs": out}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -562,6 +631,8 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "table_study":
+        run_table_study(args)
     else:
         run_ours(args)
 

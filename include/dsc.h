@@ -105,7 +105,12 @@ typedef struct {
 
 enum { DSC_VALUE_F32 = 0, DSC_VALUE_BF16 = 1 };
 enum {
-    DSC_FLAG_TIMING = 1      /* record CUDA events around each stage (dsc_get_stage_times) */
+    DSC_FLAG_TIMING = 1,     /* record CUDA events around each stage (dsc_get_stage_times) */
+    /* depth table as the paper builds it (Section 2.2): density sampled by
+     * trilinear interpolation of the voxel centres (clamped to the edge) at
+     * the table points, accumulated by the trapezoid rule.  Default: the
+     * exact integral of the piecewise-constant density (Siddon). */
+    DSC_FLAG_TRILINEAR_TABLE = 2
 };
 
 typedef struct {

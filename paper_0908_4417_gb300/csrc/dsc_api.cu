@@ -34,6 +34,7 @@ namespace dsc {
 // kernels (dsc_kernels.cu)
 __global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
+__global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
 __global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*, const int*);
 __global__ void k_item_rows(const long long*, int, int*);
 __global__ void k_tile_map(const long long*, const long long*, long long, long long*, long long*);
@@ -630,7 +631,10 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s));
   TRY(record(ev, 1, s));
   // a2: radiological-depth tables
-  k_siddon<<<P->nrows, kSiddonThreads, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride);
+  if (P->opts.flags & DSC_FLAG_TRILINEAR_TABLE)
+    k_trilinear_table<<<P->nrows, kSiddonThreads, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride);
+  else
+    k_siddon<<<P->nrows, kSiddonThreads, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride);
   CHECK_LAUNCH();
   TRY(record(ev, 2, s));
   // a3: candidate pairs per work item

@@ -355,6 +355,95 @@ __global__ void __launch_bounds__(kSiddonThreads) k_siddon(const DInst* __restri
 }
 
 // ---------------------------------------------------------------------------
+// k_trilinear_table: the paper's own table construction (Section 2.2).  The
+// density is sampled by software trilinear interpolation of the voxel-centred
+// values (clamped to the edge) at the n points s_k = min(k h, |AB|) of AB, and
+// entry k is the depth from A to point k, accumulated over the sample
+// intervals by the trapezoid rule.  One CTA per beamlet axis; each lane takes
+// a contiguous run of intervals (one extra sample at its start), sums its
+// trapezoids with a compensated FP32 sum, and the CTA prefix of the lane
+// totals is added in FP64, as in k_siddon.  Sample positions and cell
+// fractions in FP64, the blend of the eight densities in FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float trilinear_at(const DInst& G, double px, double py, double pz) {
+  const double f[3] = {(px - G.ox) * G.idx - 0.5, (py - G.oy) * G.idy - 0.5, (pz - G.oz) * G.idz - 0.5};
+  const int n[3] = {G.nx, G.ny, G.nz};
+  int i0[3], i1[3];
+  float w[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (f[a] <= 0.0) { i0[a] = 0; i1[a] = 0; w[a] = 0.0f; }
+    else if (f[a] >= n[a] - 1) { i0[a] = n[a] - 1; i1[a] = n[a] - 1; w[a] = 0.0f; }
+    else {
+      const double fl = floor(f[a]);
+      i0[a] = (int)fl; i1[a] = i0[a] + 1; w[a] = (float)(f[a] - fl);
+    }
+  }
+  const float* rho = G.rho;
+  const long long sy = G.nx, sz = (long long)G.nx * G.ny;
+  const long long y0 = i0[1] * sy, y1 = i1[1] * sy, z0 = i0[2] * sz, z1 = i1[2] * sz;
+  const float c000 = __ldg(rho + i0[0] + y0 + z0), c100 = __ldg(rho + i1[0] + y0 + z0);
+  const float c010 = __ldg(rho + i0[0] + y1 + z0), c110 = __ldg(rho + i1[0] + y1 + z0);
+  const float c001 = __ldg(rho + i0[0] + y0 + z1), c101 = __ldg(rho + i1[0] + y0 + z1);
+  const float c011 = __ldg(rho + i0[0] + y1 + z1), c111 = __ldg(rho + i1[0] + y1 + z1);
+  const float c00 = fmaf(w[0], c100 - c000, c000), c10 = fmaf(w[0], c110 - c010, c010);
+  const float c01 = fmaf(w[0], c101 - c001, c001), c11 = fmaf(w[0], c111 - c011, c011);
+  const float c0 = fmaf(w[1], c10 - c00, c00), c1 = fmaf(w[1], c11 - c01, c01);
+  return fmaf(w[2], c1 - c0, c0);
+}
+
+__global__ void __launch_bounds__(kSiddonThreads) k_trilinear_table(const DInst* __restrict__ inst,
+                                                                     const DRow* __restrict__ rows, int nrows,
+                                                                     float* __restrict__ tables, int stride) {
+  __shared__ double wsum[kSiddonThreads / 32];
+  const int ray = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (ray >= nrows) return;
+  const DRow& R = rows[ray];
+  const int n = R.n_table;
+  if (n <= 0) return;                                // uniform over the CTA
+  const DInst& G = inst[R.inst];
+  float* tab = tables + (size_t)ray * stride;
+  if (threadIdx.x == 0) tab[0] = 0.0f;
+  const int nint = n - 1;                            // intervals
+  const int Q = (nint + kSiddonThreads - 1) / kSiddonThreads;
+  const int k0 = min((int)threadIdx.x * Q, nint), k1 = min(k0 + Q, nint);
+  const double L = R.tB - R.tA;
+  const double h = G.hd;
+  double total = 0.0;
+  if (k0 < k1) {
+    double s_prev = fmin(k0 * h, L);
+    double t = R.tA + s_prev;
+    float r_prev = trilinear_at(G, fma(t, R.e[0], R.S[0]), fma(t, R.e[1], R.S[1]), fma(t, R.e[2], R.S[2]));
+    float sum = 0.0f, comp = 0.0f;                     // Kahan sum of the lane
+    for (int k = k0; k < k1; ++k) {
+      const double s = fmin((k + 1) * h, L);
+      t = R.tA + s;
+      const float r = trilinear_at(G, fma(t, R.e[0], R.S[0]), fma(t, R.e[1], R.S[1]), fma(t, R.e[2], R.S[2]));
+      const float y = fmaf((float)(s - s_prev) * 0.5f, r_prev + r, -comp);
+      const float tt = sum + y;
+      comp = (tt - sum) - y;
+      sum = tt;
+      tab[k + 1] = sum - comp;                         // lane-local, fixed below
+      s_prev = s;
+      r_prev = r;
+    }
+    total = (double)sum - (double)comp;
+  }
+  double incl = total;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  double prefix = incl - total;
+  for (int i = 0; i < w; ++i) prefix += wsum[i];
+  for (int k = k0; k < k1; ++k) tab[k + 1] = (float)(prefix + (double)tab[k + 1]);
+}
+
+// ---------------------------------------------------------------------------
 // x-lines of a work item
 // ---------------------------------------------------------------------------
 struct LineSm {

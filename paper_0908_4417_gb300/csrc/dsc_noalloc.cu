@@ -26,6 +26,7 @@
 namespace dsc {
 __global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
+__global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
 __global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*, const int*);
 __global__ void k_item_rows(const long long*, int, int*);
 __global__ void k_tile_map(const long long*, const long long*, long long, long long*, long long*);
@@ -259,7 +260,10 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
     return na_fail(DSC_E_INVAL, "needs more than %zu bytes of working memory (the fixed maximum): %lld work items",
                    kNoAllocBytes, n_items);
   const long long* n_items_dev = d_rib + nrows;
-  k_siddon<<<nrows, kSiddonThreads, 0, s>>>(d_inst, d_rows, nrows, d_tables, stride);
+  if (opts->flags & DSC_FLAG_TRILINEAR_TABLE)
+    k_trilinear_table<<<nrows, kSiddonThreads, 0, s>>>(d_inst, d_rows, nrows, d_tables, stride);
+  else
+    k_siddon<<<nrows, kSiddonThreads, 0, s>>>(d_inst, d_rows, nrows, d_tables, stride);
   NA_LAUNCH();
   k_item_rows<<<(nrows + 127) / 128, 128, 0, s>>>(d_rib, nrows, d_item_row);
   NA_LAUNCH();

@@ -23,6 +23,7 @@ DSC_E_BUSY = 8
 DSC_CUTOFF_VOI6, DSC_CUTOFF_SIGMA, DSC_CUTOFF_NONE = 0, 1, 2
 DSC_VALUE_F32, DSC_VALUE_BF16 = 0, 1
 DSC_FLAG_TIMING = 1
+DSC_FLAG_TRILINEAR_TABLE = 2
 STAGES = ("setup", "siddon", "count", "eval", "beam_scale", "compact", "finish", "total")
 
 EXPORTS = [
@@ -375,5 +376,7 @@ def compute_workload(w, stream=0, flags=0, value_dtype=None):
     """One-shot: geometry, D_ij, host CSR.  Returns (HostCSR, result handle, geometry handle)."""
     g = geometry_from_workload(w, stream)
     dt = w.value_dtype if value_dtype is None else value_dtype
+    if getattr(w, "table_mode", 0) == 1:
+        flags |= DSC_FLAG_TRILINEAR_TABLE
     res = dsc_compute_dij(g, compute_opts(w.tau, dt, w.h_frac, flags), stream)
     return HostCSR(res), res, g

@@ -138,6 +138,48 @@ def test_depth_tables_match_oracle(dsc, name):
 
 
 # ---------------------------------------------------------------------------
+# the paper's trilinear-sampled depth table (DSC_FLAG_TRILINEAR_TABLE)
+# ---------------------------------------------------------------------------
+def with_table(w, mode, h_frac=None):
+    import dataclasses
+    return dataclasses.replace(w, table_mode=mode, h_frac=w.h_frac if h_frac is None else h_frac)
+
+
+@pytest.mark.parametrize("name,h_frac", [("prostate_256", 0.5), ("slabs_128", 0.5), ("slabs_128", 1.0 / 3.0),
+                                         ("prostate_256", 1.0)])
+def test_trilinear_tables_match_oracle(dsc, name, h_frac):
+    """Sampled rows' tables against the oracle's; FP32 blend of FP32
+    densities (a few ulp per sample, not all of one sign) plus FP32 storage."""
+    w = with_table(P.get(name), P.TABLE_TRILINEAR, h_frac)
+    csr, res, g = run(dsc, w)
+    tabs = dsc.dsc_get_depth_tables(res, w.nrows)
+    rng = np.random.default_rng(4)
+    for r in rng.choice(w.nrows, 24, replace=False):
+        b, local = divmod(int(r), w.beams[0].nbeamlets)
+        iv, iu = divmod(local, w.beams[b].n_u)
+        ref = O.row_table(w.grid, w.density, w.beams[b], iu, iv, w.h_frac, table_mode=1)
+        got = tabs[r, :ref.size].astype(np.float64)
+        assert np.all(np.abs(got - ref) <= 1e-6 * np.abs(ref) + 2 * np.spacing(np.float32(np.maximum(ref, 1.0)))), r
+    cleanup(dsc, res, g)
+
+
+def test_trilinear_table_full_parity(dsc):
+    """D_ij with the trilinear table: slabs in full and sampled prostate rows
+    against the oracle computing with the same table."""
+    w = with_table(P.slabs_128(value_dtype=P.VALUE_F32), P.TABLE_TRILINEAR)
+    csr, res, g = run(dsc, w)
+    orc = O.compute_workload(w)
+    print("slabs trilinear", compare(gpu_rows(csr, range(w.nrows)), orc, TOL))
+    cleanup(dsc, res, g)
+    w = with_table(P.prostate_256(), P.TABLE_TRILINEAR)
+    csr, res, g = run(dsc, w)
+    rows = np.sort(np.random.default_rng(9).choice(w.nrows, 40, replace=False))
+    orc = O.compute_workload(w, rows=rows)
+    print("prostate trilinear", compare(gpu_rows(csr, rows), orc, TOL))
+    cleanup(dsc, res, g)
+
+
+# ---------------------------------------------------------------------------
 # edge cases: ragged grids, oblique/anisotropic, cutoff modes, misses, empties
 # ---------------------------------------------------------------------------
 def edge_cases():
