@@ -186,6 +186,23 @@ def compute_workload(w, rows=None, nthreads=0, full_scan=False):
                    nthreads=nthreads, full_scan=full_scan, table_mode=getattr(w, "table_mode", 0))
 
 
+def _sparse(orc: "OracleCSR", nvox: int):
+    import scipy.sparse
+    return scipy.sparse.csr_matrix((orc.val, orc.col, orc.row_ptr), shape=(len(orc.row_ptr) - 1, int(nvox)))
+
+
+def dose(orc: "OracleCSR", w, nvox: int) -> np.ndarray:
+    """Eq. 1: the dose at every voxel, sum over the rows j of w_j D_j(voxel),
+    in FP64 (a sparse matrix-vector product of the oracle's own D_ij)."""
+    return _sparse(orc, nvox).T @ np.asarray(w, dtype=np.float64)
+
+
+def beamlet_dot(orc: "OracleCSR", g, nvox: int) -> np.ndarray:
+    """Per row j: sum over voxels of D_j(voxel) g(voxel), the product with
+    the transpose of Eq. 1's operator (an optimiser's gradient), in FP64."""
+    return _sparse(orc, nvox) @ np.asarray(g, dtype=np.float64)
+
+
 def beamlets(grid, beams, h_frac=0.5) -> np.ndarray:
     """Per row: S[3] e[3] x[3] z[3] tA tB theta hit n_table h a b (20 doubles)."""
     n = sum(b.n_u * b.n_v for b in beams)

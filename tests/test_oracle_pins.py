@@ -538,3 +538,42 @@ def test_trilinear_table_converges_at_second_order():
     ends = [O.row_table(g, rho, beam, 0, 0, h_frac=f, table_mode=1)[-1] for f in (1 / 2, 1 / 4, 1 / 8, 1 / 16)]
     d1, d2, d3 = abs(ends[0] - ends[1]), abs(ends[1] - ends[2]), abs(ends[2] - ends[3])
     assert d1 > 0 and d2 / d3 > 3.0 and d1 / d2 > 3.0
+
+
+# ---------------------------------------------------------------------------
+# Eq. 1: dose superposition on the oracle's D_ij (NEXT-3)
+# ---------------------------------------------------------------------------
+def test_weighted_superposition_equals_a_half_field():
+    """Parallel limit, water, no cutoff, no threshold: weights 1 on the two
+    left columns of a 4 x 3 field of 4 x 6 mm beamlets and 0 elsewhere give
+    the dose of one 8 x 18 mm beamlet centred on the left half (Eq. 1 with
+    the erf tiling of Section 2.1); a row-order or weight slip moves it."""
+    g = P.centred_grid(16, 12, 10, 3.0, 3.0, 3.0)
+    rho = np.ones(g.shape, np.float32)
+    m = P.synthetic_model(cutoff_mode=P.CUTOFF_NONE)
+    sad = 1e9
+    small = P.Beam(0.0, sad, (0.0, 0.0, 0.0), 4.0, 6.0, 4, 3)
+    half = P.Beam(0.0, sad, (-4.0, 0.0, 0.0), 8.0, 18.0, 1, 1)
+    rs = O.compute(g, rho, m, [small], tau=0.0)
+    rh = O.compute(g, rho, m, [half], tau=0.0)
+    w = np.array([1.0 if iu < 2 else 0.0 for _, iu, _ in rows_of(small)])
+    d = O.dose(rs, w, g.nvox)
+    ref = dense(rh, 1, g.nvox)[0]
+    assert ref.min() > 0
+    assert np.abs(d / ref - 1).max() < 1e-6
+    # and the right half is the mirror image: weights on the right columns
+    d_right = O.dose(rs, 1.0 - w, g.nvox).reshape(g.shape)
+    assert np.abs(d_right[:, :, ::-1] - d.reshape(g.shape)).max() < 1e-9 * d.max()
+
+
+def test_dose_and_beamlet_dot_are_adjoint():
+    """<dose(w), g> = <w, beamlet_dot(g)> for random w, g (the two products
+    are transposes of one operator; a transposed operand breaks it)."""
+    w_ = P.water_32()
+    orc = O.compute_workload(w_)
+    rng = np.random.default_rng(2)
+    wv = rng.random(w_.nrows)
+    gv = rng.standard_normal(w_.grid.nvox)
+    lhs = np.dot(O.dose(orc, wv, w_.grid.nvox), gv)
+    rhs = np.dot(wv, O.beamlet_dot(orc, gv, w_.grid.nvox))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
