@@ -209,6 +209,23 @@ dsc_status dsc_copy_csr_to_host(dsc_result* res, int64_t* row_ptr, int32_t* col,
                                 void* stream);
 void dsc_release_result(dsc_result* res);
 
+/* --- products with the resident D_ij (no copy to the host) -------------- */
+/* Eq. 1 (Section 2.1): dose[v] = sum_j w[j] D_jv over the result's rows j
+ * (its beamlets; one instance of a batch), for every voxel v of its grid.
+ * w_dev: nrows floats, dose_dev: ncols floats (voxel order ix + nx (iy + ny
+ * iz)), both device pointers, caller-owned.  Queued on `stream` after the
+ * computation; the call does not wait.  Each product w_j D_jv is formed
+ * exactly and summed in 64-bit fixed point scaled to a bound on |dose|, so
+ * the result does not depend on thread order (bit-identical across calls)
+ * and lies within one FP32 rounding of the exact sum; BF16 results use
+ * D_jv = bf16 value x beam_scale.  Scratch: 8 bytes per voxel for the call. */
+dsc_status dsc_dose(dsc_result* res, const float* w_dev, float* dose_dev, void* stream);
+/* out[j] = sum_v D_jv g[v] for every row j (the product with the transpose
+ * of Eq. 1's operator, which an optimiser's gradient needs).  g_dev: ncols
+ * floats, out_dev: nrows floats, device pointers; FP64 sums per row in a fixed
+ * order, queued on `stream`. */
+dsc_status dsc_beamlet_dot(dsc_result* res, const float* g_dev, float* out_dev, void* stream);
+
 /* --- stage inspection (per-step parity and timing) ---------------------- */
 /* Per row 16 doubles: S[3] e[3] x'[3] z'[3] tA tB hit n_table. */
 dsc_status dsc_get_beamlets(dsc_result* res, double* out, int64_t cap_rows);

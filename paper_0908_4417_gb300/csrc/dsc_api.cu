@@ -43,6 +43,12 @@ __global__ void k_beam_scale(const DBeam*, int, const unsigned*, const OutSlot*)
 __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_tile_prep(CompactParams);
 __global__ void k_lut_pairs(const float4*, int, float4*);
+__global__ void k_dose_scale(const unsigned*, const float*, int, int*);
+__global__ void k_dose_scatter(const long long*, const long long*, const int*, const void*, int, const DRow*, int,
+                               const float*, const float*, int, const int*, unsigned long long*);
+__global__ void k_dose_finish(const unsigned long long*, long long, const int*, float*);
+__global__ void k_beamlet_dot(const long long*, const long long*, const int*, const void*, int, const DRow*, int,
+                              const float*, const float*, int, float*);
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
@@ -1044,6 +1050,49 @@ extern "C" dsc_status dsc_get_depth_tables(dsc_result* r, float* out, int64_t ca
   CU(cudaEventSynchronize(r->done));
   CU(cudaMemcpy(out, r->plan->d_tables + (size_t)r->row_base * r->plan->stride,
                 sizeof(float) * (size_t)r->nrows * r->plan->stride, cudaMemcpyDeviceToHost));
+  return DSC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// products with the resident D_ij (Eq. 1 and its transpose)
+// ---------------------------------------------------------------------------
+static unsigned row_warps_grid(int nrows) {
+  return (unsigned)std::max(1, std::min((nrows + 7) / 8, 152 * 16));   // 8 warps (rows) per 256-thread block
+}
+
+extern "C" dsc_status dsc_dose(dsc_result* r, const float* w_dev, float* dose_dev, void* stream) {
+  if (!r || !w_dev || !dose_dev) return fail(DSC_E_INVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(cudaStreamWaitEvent(s, r->done, 0));
+  const OutSlot& q = r->out->slot;
+  unsigned long long* acc = nullptr;
+  int* ex = nullptr;
+  TRY(dalloc(&acc, (size_t)r->ncols, s));
+  TRY(dalloc(&ex, 1, s));
+  CU(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)r->ncols, s));
+  k_dose_scale<<<1, 1024, 0, s>>>(q.row_max + r->row_base, w_dev, r->nrows, ex);
+  CHECK_LAUNCH();
+  k_dose_scatter<<<row_warps_grid(r->nrows), 256, 0, s>>>(q.row_ptr + r->rp_off, q.inst_begin + r->inst, q.col, q.val,
+                                                          r->value_dtype, r->plan->d_rows, r->row_base, q.beam_scale,
+                                                          w_dev, r->nrows, ex, acc);
+  CHECK_LAUNCH();
+  const long long nb = std::min<long long>((r->ncols + 255) / 256, 152 * 32);
+  k_dose_finish<<<(unsigned)std::max(1ll, nb), 256, 0, s>>>(acc, r->ncols, ex, dose_dev);
+  CHECK_LAUNCH();
+  CU(cudaFreeAsync(acc, s));
+  CU(cudaFreeAsync(ex, s));
+  return DSC_OK;
+}
+
+extern "C" dsc_status dsc_beamlet_dot(dsc_result* r, const float* g_dev, float* out_dev, void* stream) {
+  if (!r || !g_dev || !out_dev) return fail(DSC_E_INVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(cudaStreamWaitEvent(s, r->done, 0));
+  const OutSlot& q = r->out->slot;
+  k_beamlet_dot<<<row_warps_grid(r->nrows), 256, 0, s>>>(q.row_ptr + r->rp_off, q.inst_begin + r->inst, q.col, q.val,
+                                                         r->value_dtype, r->plan->d_rows, r->row_base, q.beam_scale,
+                                                         g_dev, r->nrows, out_dev);
+  CHECK_LAUNCH();
   return DSC_OK;
 }
 

@@ -32,7 +32,7 @@ EXPORTS = [
     "dsc_compute_dij", "dsc_compute_dij_batch", "dsc_result_wait", "dsc_get_csr", "dsc_copy_csr_to_host",
     "dsc_release_result", "dsc_get_beamlets", "dsc_get_depth_tables", "dsc_get_row_stats", "dsc_get_stage_times",
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
-    "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune",
+    "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune", "dsc_dose", "dsc_beamlet_dot",
 ]
 
 
@@ -112,6 +112,8 @@ def lib():
             "dsc_server_destroy": (None, [P]),
             "dsc_compute_dij_noalloc": (C.c_int, [C.POINTER(GridDesc), P, C.POINTER(FspbModel), C.POINTER(BeamDesc),
                                                   I32, C.POINTER(ComputeOpts), P, P, P, I64, C.POINTER(I64), P]),
+            "dsc_dose": (C.c_int, [P, P, P, P]),
+            "dsc_beamlet_dot": (C.c_int, [P, P, P, P]),
             "dsc_set_tuning": (C.c_int, [C.POINTER(Tuning)]),
             "dsc_get_tuning": (C.c_int, [C.POINTER(Tuning)]),
             "dsc_autotune": (C.c_int, [C.POINTER(P), I32, C.POINTER(ComputeOpts), P, I32, C.POINTER(Tuning),
@@ -237,6 +239,16 @@ def dsc_autotune(geoms, opts: ComputeOpts, stream=0, reps: int = 3) -> tuple:
     t, ms = Tuning(), C.c_float()
     _check(lib().dsc_autotune(arr, n, C.byref(opts), stream, int(reps), C.byref(t), C.byref(ms)))
     return (int(t.target_cand), int(t.eval_blocks_per_sm)), float(ms.value)
+
+
+def dsc_dose(res, w_ptr: int, dose_ptr: int, stream=0):
+    """Eq. 1 on the device: dose (ncols floats) = sum_j w_j D_j; pointers are device addresses."""
+    _check(lib().dsc_dose(res, w_ptr, dose_ptr, stream))
+
+
+def dsc_beamlet_dot(res, g_ptr: int, out_ptr: int, stream=0):
+    """out (nrows floats) = D g on the device; pointers are device addresses."""
+    _check(lib().dsc_beamlet_dot(res, g_ptr, out_ptr, stream))
 
 
 def dsc_result_wait(res):

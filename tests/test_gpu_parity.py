@@ -180,6 +180,81 @@ def test_trilinear_table_full_parity(dsc):
 
 
 # ---------------------------------------------------------------------------
+# Eq. 1 on the resident D_ij: dose superposition and its transpose product
+# ---------------------------------------------------------------------------
+def dose_products(dsc, res, w, g):
+    dev = torch.device("cuda", 0)
+    wt = torch.from_numpy(np.asarray(w, np.float32)).to(dev)
+    gt = torch.from_numpy(np.asarray(g, np.float32)).to(dev)
+    d = torch.empty(len(g), dtype=torch.float32, device=dev)
+    o = torch.empty(len(w), dtype=torch.float32, device=dev)
+    dsc.dsc_dose(res, wt.data_ptr(), d.data_ptr(), 0)
+    dsc.dsc_beamlet_dot(res, gt.data_ptr(), o.data_ptr(), 0)
+    torch.cuda.synchronize()
+    return d.cpu().numpy().astype(np.float64), o.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("name", ["water_32", "slabs_128"])
+def test_dose_superposition_matches_oracle(dsc, name):
+    """dose = sum_j w_j D_j and D g against the oracle's FP64 products of its
+    own D_ij; voxels (rows) touched by the oracle's ambiguity bands are left
+    out; deterministic: a second call is bit-identical."""
+    w_ = P.get(name)
+    w_ = w_ if w_.value_dtype == P.VALUE_F32 else P.slabs_128(value_dtype=P.VALUE_F32)
+    csr, res, g = run(dsc, w_)
+    orc = O.compute_workload(w_)
+    rng = np.random.default_rng(12)
+    wv = rng.random(w_.nrows).astype(np.float32)
+    gv = rng.random(w_.grid.nvox).astype(np.float32)
+    d, o = dose_products(dsc, res, wv, gv)
+    d_ref = O.dose(orc, wv, w_.grid.nvox)
+    o_ref = O.beamlet_dot(orc, gv, w_.grid.nvox)
+    keep = np.ones(w_.grid.nvox, bool)
+    keep[orc.amb_col] = False
+    assert np.abs(d - d_ref)[keep].max() <= 1e-5 * d_ref.max()
+    rkeep = np.ones(w_.nrows, bool)
+    rkeep[orc.amb_row] = False
+    assert np.all(np.abs(o - o_ref)[rkeep] <= 1e-5 * np.abs(o_ref)[rkeep] + 1e-9 * np.abs(o_ref).max())
+    d2, o2 = dose_products(dsc, res, wv, gv)
+    assert np.array_equal(d, d2) and np.array_equal(o, o2)
+    # adjointness on the device products
+    assert abs(np.dot(d, gv) - np.dot(wv, o)) <= 1e-5 * abs(np.dot(d, gv))
+    cleanup(dsc, res, g)
+
+
+def test_dose_bf16_and_batch_instances(dsc):
+    """BF16 storage (value x per-beam scale) within the BF16 rounding of the
+    FP32 dose; a batch instance's dose equals the same geometry computed alone."""
+    w_ = P.slabs_128(value_dtype=P.VALUE_BF16)
+    csr, res, g = run(dsc, w_)
+    csr32, res32, g32 = run(dsc, P.slabs_128(value_dtype=P.VALUE_F32))
+    rng = np.random.default_rng(13)
+    wv = rng.random(w_.nrows).astype(np.float32)
+    gv = rng.random(w_.grid.nvox).astype(np.float32)
+    d16, o16 = dose_products(dsc, res, wv, gv)
+    d32, o32 = dose_products(dsc, res32, wv, gv)
+    assert np.abs(d16 - d32).max() <= 2.0 ** -8 * d32.max()
+    assert np.all(np.abs(o16 - o32) <= 2.0 ** -8 * np.abs(o32) + 1e-6 * np.abs(o32).max())
+    cleanup(dsc, res, g)
+    cleanup(dsc, res32, g32)
+    ws = small_instances(3)
+    gs = [dsc.geometry_from_workload(x) for x in ws]
+    opts = dsc.compute_opts(1e-3, 0, 0.5)
+    batch = dsc.dsc_compute_dij_batch(gs, opts)
+    for k, x in enumerate(ws):
+        wv = rng.random(x.nrows).astype(np.float32)
+        gv = rng.random(x.grid.nvox).astype(np.float32)
+        single = dsc.dsc_compute_dij(gs[k], opts)
+        assert all(np.array_equal(a, b) for a, b in zip(dose_products(dsc, batch[k], wv, gv),
+                                                         dose_products(dsc, single, wv, gv)))
+        dsc.dsc_release_result(single)
+    for r in batch:
+        dsc.dsc_release_result(r)
+    for x in gs:
+        dsc.dsc_destroy_geometry(x)
+
+
+# ---------------------------------------------------------------------------
 # edge cases: ragged grids, oblique/anisotropic, cutoff modes, misses, empties
 # ---------------------------------------------------------------------------
 def edge_cases():
