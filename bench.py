@@ -2,7 +2,7 @@
 """Benchmark of the FSPB D_ij path: voxel-beamlet pairs/s and 9-field latency.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload prostate_256|slabs_128|water_32|batched|serving|table_study]
+                    [--workload prostate_256|slabs_128|water_32|batched|serving|table_study|superposition|table1]
 
 One step = the whole path (beamlet set-up, Siddon depth tables, VOI
 enumeration, FSPB evaluation, threshold + CSR compaction) for the 9-field
@@ -623,6 +623,128 @@ def run_table_study(args):
     print(json.dumps(line), flush=True)
 
 
+def run_superposition(args):
+    """Eq. 1 on the resident D_ij of the 9-field prostate: dose = sum_j w_j D_j
+    (dsc_dose) and the transpose product D g (dsc_beamlet_dot), each timed
+    over K calls with CUDA events after W warm-up calls, against HBM
+    bandwidth (algorithmic bytes: the CSR read once, 8 B per kept entry, plus
+    the per-voxel and per-row vectors)."""
+    import numpy as np
+    import torch
+    from paper_0908_4417_gb300 import build as B
+    B.build()
+    from paper_0908_4417_gb300 import dsc, phantoms as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    sp = stream.cuda_stream
+    w = P.get("prostate_256")
+    g = dsc.geometry_from_workload(w, sp)
+    res = dsc.dsc_compute_dij(g, dsc.compute_opts(w.tau, w.value_dtype, w.h_frac, 0), sp)
+    v = dsc.dsc_get_csr(res, False)
+    nrows, ncols, nnz = int(v.nrows), int(v.ncols), int(v.nnz)
+    rng = np.random.default_rng(1)
+    wt = torch.from_numpy(rng.random(nrows).astype(np.float32)).to(dev)
+    gt = torch.from_numpy(rng.random(ncols).astype(np.float32)).to(dev)
+    dose = torch.empty(ncols, dtype=torch.float32, device=dev)
+    out = torch.empty(nrows, dtype=torch.float32, device=dev)
+    peak = None
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        stream.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    with torch.cuda.stream(stream):
+        n0 = dsc.dsc_launch_count()
+        t_dose = timed(lambda: dsc.dsc_dose(res, wt.data_ptr(), dose.data_ptr(), sp))
+        t_dot = timed(lambda: dsc.dsc_beamlet_dot(res, gt.data_ptr(), out.data_ptr(), sp))
+        launches = dsc.dsc_launch_count() - n0
+    b_dose = nnz * 8 + (nrows + 1) * 8 + nrows * 4 + ncols * (8 + 8 + 4)
+    b_dot = nnz * 8 + (nrows + 1) * 8 + ncols * 4 + nrows * 4
+    dsc.dsc_release_result(res)
+    dsc.dsc_destroy_geometry(g)
+    gbs_dose, gbs_dot = b_dose / t_dose / 1e6, b_dot / t_dot / 1e6
+    line = {"metric": "dose superposition (Eq. 1) on the resident CSR", "value": t_dose, "unit": "ms per dose",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "prostate_256", "nrows": nrows, "ncols": ncols, "nnz": nnz,
+                       "dose_ms": t_dose, "beamlet_dot_ms": t_dot},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak,
+                         "dose": {"achieved": gbs_dose, "frac": gbs_dose / peak if peak else None, "bytes": b_dose},
+                         "beamlet_dot": {"achieved": gbs_dot, "frac": gbs_dot / peak if peak else None,
+                                         "bytes": b_dot}}}
+    print(json.dumps(line), flush=True)
+
+
+def run_table1(args):
+    """The paper's Table 1 water sweep (Section 3.1) as a second workload:
+    five coplanar 10 x 10 cm beams on a 30 cm water cube, voxels 0.50-0.25 cm,
+    beamlets 0.20-0.50 cm.  Per case: candidate pairs (the paper's N'_voxel),
+    kept entries, device ms per computation (median of K graph replays, L2
+    flushed between them) and pairs/s; the paper's own N' and C1060 time
+    are carried for context."""
+    import torch
+    from paper_0908_4417_gb300 import build as B
+    B.build()
+    from paper_0908_4417_gb300 import dsc, phantoms as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    sp = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    paper = {1: (0.864e7, 0.06), 2: (1.80e7, 0.10), 3: (3.23e7, 0.18), 4: (5.27e7, 0.30), 5: (4.97e7, 0.29),
+             6: (4.70e7, 0.27), 7: (4.39e7, 0.24)}
+    cases = []
+    n0 = dsc.dsc_launch_count()
+    with torch.cuda.stream(stream):
+        for c in range(1, 8):
+            w = P.table1_water(c)
+            g = dsc.geometry_from_workload(w, sp)
+            opts = dsc.compute_opts(w.tau, w.value_dtype, w.h_frac, 0)
+            for _ in range(max(3, args.warmup)):
+                dsc.dsc_release_result(dsc.dsc_compute_dij(g, opts, sp))
+            r = dsc.dsc_compute_dij(g, opts, sp)
+            v = dsc.dsc_get_csr(r, False)
+            pairs, nnz = int(v.pairs), int(v.nnz)
+            dsc.dsc_release_result(r)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for k, (a, b) in enumerate(evs):
+                flush.fill_(k & 0xff)
+                a.record(stream)
+                r = dsc.dsc_compute_dij(g, opts, sp)
+                b.record(stream)
+                dsc.dsc_release_result(r)
+            stream.synchronize()
+            ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+            dsc.dsc_destroy_geometry(g)
+            cases.append({"case": c, "voxel_cm": round(w.grid.dx / 10, 4), "beamlet_cm": w.beams[0].a / 10,
+                          "grid": w.grid.nx, "beamlets": w.nrows, "pairs": pairs, "nnz": nnz, "ms": round(ms, 4),
+                          "pairs_per_s": pairs / (ms / 1e3), "paper_nprime": paper[c][0],
+                          "paper_c1060_s": paper[c][1]})
+    launches = dsc.dsc_launch_count() - n0
+    big = max(cases, key=lambda x: x["pairs"])
+    line = {"metric": "voxel-beamlet pairs/s (Table 1 water sweep)", "value": big["pairs_per_s"], "unit": "pairs/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "table1_water", "value_case": big["case"],
+                       "l2": "flushed between steps (256 MB write)", "cases": cases},
+            "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -633,6 +755,10 @@ def main():
         run_serving(args)
     elif args.workload == "table_study":
         run_table_study(args)
+    elif args.workload == "superposition":
+        run_superposition(args)
+    elif args.workload == "table1":
+        run_table1(args)
     else:
         run_ours(args)
 
