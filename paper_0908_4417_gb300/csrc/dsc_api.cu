@@ -1056,8 +1056,8 @@ extern "C" dsc_status dsc_get_depth_tables(dsc_result* r, float* out, int64_t ca
 // ---------------------------------------------------------------------------
 // products with the resident D_ij (Eq. 1 and its transpose)
 // ---------------------------------------------------------------------------
-static unsigned row_warps_grid(int nrows) {
-  return (unsigned)std::max(1, std::min((nrows + 7) / 8, 152 * 16));   // 8 warps (rows) per 256-thread block
+static unsigned row_blocks_grid(int nrows) {
+  return (unsigned)std::max(1, std::min(nrows, 152 * 32));   // one 256-thread block per row, grid-stride beyond
 }
 
 extern "C" dsc_status dsc_dose(dsc_result* r, const float* w_dev, float* dose_dev, void* stream) {
@@ -1072,7 +1072,7 @@ extern "C" dsc_status dsc_dose(dsc_result* r, const float* w_dev, float* dose_de
   CU(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)r->ncols, s));
   k_dose_scale<<<1, 1024, 0, s>>>(q.row_max + r->row_base, w_dev, r->nrows, ex);
   CHECK_LAUNCH();
-  k_dose_scatter<<<row_warps_grid(r->nrows), 256, 0, s>>>(q.row_ptr + r->rp_off, q.inst_begin + r->inst, q.col, q.val,
+  k_dose_scatter<<<row_blocks_grid(r->nrows), 256, 0, s>>>(q.row_ptr + r->rp_off, q.inst_begin + r->inst, q.col, q.val,
                                                           r->value_dtype, r->plan->d_rows, r->row_base, q.beam_scale,
                                                           w_dev, r->nrows, ex, acc);
   CHECK_LAUNCH();
@@ -1089,7 +1089,7 @@ extern "C" dsc_status dsc_beamlet_dot(dsc_result* r, const float* g_dev, float* 
   cudaStream_t s = (cudaStream_t)stream;
   CU(cudaStreamWaitEvent(s, r->done, 0));
   const OutSlot& q = r->out->slot;
-  k_beamlet_dot<<<row_warps_grid(r->nrows), 256, 0, s>>>(q.row_ptr + r->rp_off, q.inst_begin + r->inst, q.col, q.val,
+  k_beamlet_dot<<<row_blocks_grid(r->nrows), 256, 0, s>>>(q.row_ptr + r->rp_off, q.inst_begin + r->inst, q.col, q.val,
                                                          r->value_dtype, r->plan->d_rows, r->row_base, q.beam_scale,
                                                          g_dev, r->nrows, out_dev);
   CHECK_LAUNCH();

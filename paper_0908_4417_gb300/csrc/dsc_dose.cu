@@ -5,23 +5,44 @@
 //                                    gradient needs)
 //
 // Both read one instance's CSR where the computation left it (rows = the
-// instance's beamlets, columns = voxel indices).  The dose is a scatter over
-// rows: every product w_j D_jv is formed exactly in FP64, scaled by a power
-// of two chosen from a bound on |dose|, rounded to a 64-bit integer and added
-// with integer atomics, so the sum does not depend on the order the atomics
-// land in (deterministic, within one FP32 rounding of the exact sum of the
-// products).  The transpose product is a gather per row, one warp per row,
-// FP64 sums reduced in a fixed order.
+// instance's beamlets, columns = voxel indices).  FP64 arithmetic is slow on
+// this GPU, so no per-entry step uses it.  The dose is a scatter over rows:
+// every product w_j D_jv is formed exactly as an FP32 pair (product and its
+// FMA residual), each part is converted exactly (integer shifts of its
+// mantissa) to 64-bit fixed point at a power-of-two scale chosen from a bound
+// on |dose|, and added with integer atomics, so the sum does not depend on
+// the order the atomics land in (deterministic, within one FP32 rounding of
+// the exact sum of the products).  The transpose product is a gather per
+// row, one warp per row, compensated FP32 sums per lane reduced in FP64 in
+// a fixed order.
 #include "dsc_internal.h"
 
 #include <cuda_bf16.h>
 
 namespace dsc {
 
+constexpr int kRowThreads = 256;   // threads per row of the products
+
 namespace {
-__device__ __forceinline__ double entry_value(const void* val, int dtype, long long k, float scale) {
-  if (dtype == 1) return (double)__bfloat162float(((const __nv_bfloat16*)val)[k]) * (double)scale;
-  return (double)((const float*)val)[k];
+// the stored D_jv as FP32 (BF16 values times the beam's scale, rounded once)
+__device__ __forceinline__ float entry_value(const void* val, int dtype, long long k, float scale) {
+  if (dtype == 1) return __bfloat162float(((const __nv_bfloat16*)val)[k]) * scale;
+  return ((const float*)val)[k];
+}
+
+// x * 2^e rounded to a 64-bit integer (ties away from zero), from the FP32
+// bits with integer operations only; |x| 2^e < 2^62 by the choice of e
+__device__ __forceinline__ long long fixed_of(float x, int e) {
+  const unsigned b = __float_as_uint(x);
+  const int E = (int)((b >> 23) & 0xffu);
+  if (E == 0 && (b & 0x7fffffu) == 0) return 0;
+  const long long m = (long long)((b & 0x7fffffu) | (E ? 0x800000u : 0u));
+  const int sh = (E ? E : 1) - 150 + e;           // x = m 2^((E ? E : 1) - 150)
+  long long q;
+  if (sh >= 0) q = m << sh;
+  else if (sh > -40) q = (m + (1ll << (-sh - 1))) >> -sh;
+  else q = 0;
+  return (b >> 31) ? -q : q;
 }
 }  // namespace
 
@@ -45,24 +66,34 @@ __global__ void __launch_bounds__(1024) k_dose_scale(const unsigned* __restrict_
   }
 }
 
-__global__ void k_dose_scatter(const long long* __restrict__ row_ptr, const long long* __restrict__ inst_begin,
-                               const int* __restrict__ col, const void* __restrict__ val, int dtype,
-                               const DRow* __restrict__ rows, int row_base, const float* __restrict__ beam_scale,
-                               const float* __restrict__ w, int nrows, const int* __restrict__ exp_in,
-                               unsigned long long* __restrict__ acc) {
-  const int lane = threadIdx.x & 31;
+// one block per row (grid-stride over rows), four entries in flight per thread
+__global__ void __launch_bounds__(kRowThreads) k_dose_scatter(
+    const long long* __restrict__ row_ptr, const long long* __restrict__ inst_begin, const int* __restrict__ col,
+    const void* __restrict__ val, int dtype, const DRow* __restrict__ rows, int row_base,
+    const float* __restrict__ beam_scale, const float* __restrict__ w, int nrows, const int* __restrict__ exp_in,
+    unsigned long long* __restrict__ acc) {
   const long long base = *inst_begin;
   const int e = *exp_in;
-  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long j = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); j < nrows; j += nw) {
-    const double wj = (double)w[j];
-    if (wj == 0.0) continue;                          // warp-uniform
+  for (int j = blockIdx.x; j < nrows; j += gridDim.x) {
+    const float wj = w[j];
+    if (wj == 0.0f) continue;                         // block-uniform
     const float sc = dtype == 1 ? beam_scale[rows[row_base + j].beam] : 1.0f;
     const long long a = base + row_ptr[j], b = base + row_ptr[j + 1];
-    for (long long k = a + lane; k < b; k += 32) {
-      const double p = wj * entry_value(val, dtype, k, sc);   // exact: FP32 x FP32 (x power of two)
-      const long long q = __double2ll_rn(ldexp(p, e));
-      atomicAdd(acc + col[k], (unsigned long long)q);
+    for (long long k0 = a + threadIdx.x; k0 < b; k0 += 4 * kRowThreads) {
+      int c[4];
+      float D[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long k = k0 + (long long)u * kRowThreads;
+        c[u] = k < b ? col[k] : -1;
+        D[u] = k < b ? entry_value(val, dtype, k, sc) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (c[u] < 0) continue;
+        const float hi = wj * D[u], lo = fmaf(wj, D[u], -hi);   // w D = hi + lo exactly
+        atomicAdd(acc + c[u], (unsigned long long)(fixed_of(hi, e) + fixed_of(lo, e)));
+      }
     }
   }
 }
@@ -71,24 +102,49 @@ __global__ void k_dose_finish(const unsigned long long* __restrict__ acc, long l
                               float* __restrict__ dose) {
   const int e = *exp_in;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
-    dose[v] = (float)ldexp((double)(long long)acc[v], -e);
+    dose[v] = ldexpf(__ll2float_rn((long long)acc[v]), -e);   // one rounding to FP32
 }
 
-__global__ void k_beamlet_dot(const long long* __restrict__ row_ptr, const long long* __restrict__ inst_begin,
-                              const int* __restrict__ col, const void* __restrict__ val, int dtype,
-                              const DRow* __restrict__ rows, int row_base, const float* __restrict__ beam_scale,
-                              const float* __restrict__ g, int nrows, float* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
+// one block per row (grid-stride over rows), four entries in flight per
+// thread, compensated FP32 sums per thread, then FP64 over the block in a
+// fixed order
+__global__ void __launch_bounds__(kRowThreads) k_beamlet_dot(
+    const long long* __restrict__ row_ptr, const long long* __restrict__ inst_begin, const int* __restrict__ col,
+    const void* __restrict__ val, int dtype, const DRow* __restrict__ rows, int row_base,
+    const float* __restrict__ beam_scale, const float* __restrict__ g, int nrows, float* __restrict__ out) {
+  __shared__ double part[kRowThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long base = *inst_begin;
-  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long j = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); j < nrows; j += nw) {
+  for (int j = blockIdx.x; j < nrows; j += gridDim.x) {
     const float sc = dtype == 1 ? beam_scale[rows[row_base + j].beam] : 1.0f;
     const long long a = base + row_ptr[j], b = base + row_ptr[j + 1];
-    double s = 0.0;
-    for (long long k = a + lane; k < b; k += 32) s = fma(entry_value(val, dtype, k, sc), (double)g[col[k]], s);
+    float sum = 0.0f, comp = 0.0f;                    // compensated FP32 sum of the thread
+    for (long long k0 = a + threadIdx.x; k0 < b; k0 += 4 * kRowThreads) {
+      float p[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long k = k0 + (long long)u * kRowThreads;
+        p[u] = k < b ? entry_value(val, dtype, k, sc) * g[col[k]] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float y = p[u] - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+      }
+    }
+    double s = (double)sum - (double)comp;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[j] = (float)s;
+    if (lane == 0) part[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < kRowThreads / 32; ++i) t += part[i];
+      out[j] = (float)t;
+    }
+    __syncthreads();
   }
 }
 
