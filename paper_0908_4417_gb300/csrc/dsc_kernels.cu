@@ -817,7 +817,7 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
 // persistent: CTAs take work items from a queue; every candidate's D goes to
 // vals[item_off[item] + k] and the row maximum is kept with atomicMax on the
 // float bits (D >= 0)
-__global__ void __launch_bounds__(kEvalThreads) k_eval(EvalParams p) {
+__global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
   __shared__ LineSm sm;
   const long long ni = *p.n_items;
   for (;;) {
@@ -845,16 +845,29 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalParams p) {
     for (int w0 = 0; w0 < total; w0 += kWindow) {
       int wl = min(kWindow, total - w0);
       item_map(sm, w0, wl);
-      for (int j = threadIdx.x; j < wl; j += kEvalThreads) {
+      // two candidates per thread per pass: independent chains to interleave
+      for (int j = threadIdx.x; j < wl; j += 2 * kEvalThreads) {
+        const int j2 = j + kEvalThreads;
+        const bool two = j2 < wl;
+        const int jb = two ? j2 : j;
         int li = min((int)sm.map[j], sm.nl - 1);
-        float4 sx = sm.sx[li];
-        float4 zc = sm.zc[li];
+        int lb = min((int)sm.map[jb], sm.nl - 1);
+        float4 sx = sm.sx[li], sxb = sm.sx[lb];
+        float4 zc = sm.zc[li], zcb = sm.zc[lb];
         int ix = __float_as_int(zc.z) + (w0 + j - sm.off[li]);
+        int ixb = __float_as_int(zcb.z) + (w0 + jb - sm.off[lb]);
         float D = eval_pair(C, (float)ix, sx, make_float2(zc.x, zc.y), mode);
+        float Db = eval_pair(C, (float)ixb, sxb, make_float2(zcb.x, zcb.y), mode);
         out[w0 + j] = D;
         outc[w0 + j] = __float_as_int(zc.w) + ix;
         vmax = fmaxf(vmax, D);
         if (mode == 1) valid += D >= 0.0f;
+        if (two) {
+          out[w0 + jb] = Db;
+          outc[w0 + jb] = __float_as_int(zcb.w) + ixb;
+          vmax = fmaxf(vmax, Db);
+          if (mode == 1) valid += Db >= 0.0f;
+        }
       }
       __syncthreads();
     }
