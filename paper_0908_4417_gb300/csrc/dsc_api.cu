@@ -552,7 +552,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   CU(cudaMemsetAsync(P->d_tables, 0, sizeof(float) * (size_t)P->nrows * P->stride, s));
 
   // sizes: items (from the set-up) and candidates (from the count)
-  k_setup<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
+  k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
                                                  P->d_row_items, P->target_cand);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s));
@@ -631,7 +631,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   CU(cudaMemsetAsync(P->d_row_cand, 0, sizeof(long long) * P->nrows, s));
   CU(cudaMemsetAsync(P->d_counter, 0, sizeof(int) * 4, s));
   // a1: beamlet frames, entry/exit, VOI box, work items
-  k_setup<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
+  k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
                                                  P->d_row_items, P->target_cand);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s));

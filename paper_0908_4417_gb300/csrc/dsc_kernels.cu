@@ -530,25 +530,27 @@ __device__ __forceinline__ int block_excl_scan(int v, int& excl, int* wscan) {
   return tot;
 }
 
-// line (iy, iz) of line index l of row R
-__device__ __forceinline__ void line_yz(const DRow& R, long long l, int& iy, int& iz) {
-  int nyb = R.iy1 - R.iy0 + 1;
-  iz = R.iz0 + (int)(l / nyb);
-  iy = R.iy0 + (int)(l - (long long)(iz - R.iz0) * nyb);
+// line (iy, iz) of line index l of row R (a row's VOI box has fewer than
+// 2^31 lines: the grid has fewer than 2^31 voxels)
+__device__ __forceinline__ void line_yz(const DRow& R, int l, int& iy, int& iz) {
+  const unsigned nyb = (unsigned)(R.iy1 - R.iy0 + 1);
+  const unsigned q = (unsigned)l / nyb;
+  iz = R.iz0 + (int)q;
+  iy = R.iy0 + (int)((unsigned)l - q * nyb);
 }
 
 // lines of a work item: [chunk * lpc, min(+lpc, lines of the row))
-__device__ __forceinline__ int item_nlines(const DRow& R, long long chunk, long long& l0) {
-  long long nlines = (long long)(R.iy1 - R.iy0 + 1) * (R.iz1 - R.iz0 + 1);
-  l0 = chunk * R.lpc;
-  return (int)min((long long)R.lpc, nlines - l0);
+__device__ __forceinline__ int item_nlines(const DRow& R, long long chunk, int& l0) {
+  const int nlines = (R.iy1 - R.iy0 + 1) * (R.iz1 - R.iz0 + 1);
+  l0 = (int)chunk * R.lpc;
+  return min(R.lpc, nlines - l0);
 }
 
 // set up all lines of an item in shared memory (each thread takes lines t and
 // t + kEvalThreads); returns the candidate count
 __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, long long chunk) {
   constexpr int per = kMaxLinesPerItem / kEvalThreads;
-  long long l0;
+  int l0;
   int nl = item_nlines(R, chunk, l0);
   int t = threadIdx.x;
   int len[per];
@@ -656,7 +658,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
     int row = item_row[item];
     const DRow& R = rows[row];
     const DInst& G = inst[R.inst];
-    long long l0;
+    int l0;
     int nl = item_nlines(R, item - row_item_base[row], l0);
     int cnt = 0;
     for (int li = lane; li < nl; li += 32) {

@@ -245,7 +245,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   const int grid_items = (nb > 0 ? nb : 1) * sms;
 
   // set-up and work items
-  k_setup<<<(nrows + 127) / 128, 128, 0, s>>>(d_inst, d_beams, nbeams, d_rows, nrows, d_row_items, target_cand);
+  k_setup<<<(nrows + 31) / 32, 32, 0, s>>>(d_inst, d_beams, nbeams, d_rows, nrows, d_row_items, target_cand);
   NA_LAUNCH();
   st = na_scan(d_row_items, nullptr, nrows, d_scan, d_rib, s);
   if (st != DSC_OK) return st;
