@@ -56,6 +56,8 @@ __global__ void k_copy_stats(const unsigned*, const long long*, int, const OutSl
 __global__ void k_scan_partial(const int*, const long long*, long long, long long*);
 __global__ void k_scan_blocks(long long*);
 __global__ void k_scan_final(const int*, const long long*, long long, const long long*, long long*);
+__global__ void k_scan_small(const int*, const long long*, long long, long long*);
+__global__ void k_scan_small(const int*, const long long*, long long, long long*);
 }  // namespace dsc
 
 using namespace dsc;
@@ -463,8 +465,15 @@ extern "C" void dsc_destroy_geometry(dsc_geometry* g) {
 // ---------------------------------------------------------------------------
 // planning
 // ---------------------------------------------------------------------------
+// n_host: the input length as the host knows it (the plan's sizes); short
+// inputs take the one-block scan
 static dsc_status scan_launch(const int* in, const long long* n_dev, long long n_const, long long* tmp, long long* out,
-                              cudaStream_t s) {
+                              cudaStream_t s, long long n_host) {
+  if (n_host <= kSmallScan) {
+    k_scan_small<<<1, 1024, 0, s>>>(in, n_dev, n_const, out);
+    CHECK_LAUNCH();
+    return DSC_OK;
+  }
   k_scan_partial<<<kScanBlocks, kScanThreads, 0, s>>>(in, n_dev, n_const, tmp);
   CHECK_LAUNCH();
   k_scan_blocks<<<1, kScanBlocks, 0, s>>>(tmp);
@@ -555,7 +564,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
                                                  P->d_row_items, P->target_cand);
   CHECK_LAUNCH();
-  TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s));
+  TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s, P->nrows));
   CU(cudaMemcpyAsync(&P->n_items, P->d_row_item_base + P->nrows, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   TRY(dalloc(&P->d_item_cand, P->n_items, s));
@@ -574,7 +583,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, P->d_row_item_base, P->nrows,
                                                  P->d_row_item_base + P->nrows, P->d_item_cand, P->d_item_row);
   CHECK_LAUNCH();
-  TRY(scan_launch(P->d_item_cand, P->d_row_item_base + P->nrows, 0, P->d_scan, P->d_item_off, s));
+  TRY(scan_launch(P->d_item_cand, P->d_row_item_base + P->nrows, 0, P->d_scan, P->d_item_off, s, P->n_items));
   CU(cudaMemcpyAsync(&P->n_cand, P->d_item_off + P->n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   P->n_tiles = (P->n_cand + kTile - 1) / kTile;
@@ -634,7 +643,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
                                                  P->d_row_items, P->target_cand);
   CHECK_LAUNCH();
-  TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s));
+  TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s, P->nrows));
   TRY(record(ev, 1, s));
   // a2: radiological-depth tables
   if (P->opts.flags & DSC_FLAG_TRILINEAR_TABLE)
@@ -649,7 +658,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, P->d_row_item_base, P->nrows, n_items,
                                                  P->d_item_cand, P->d_item_row);
   CHECK_LAUNCH();
-  TRY(scan_launch(P->d_item_cand, n_items, 0, P->d_scan, P->d_item_off, s));
+  TRY(scan_launch(P->d_item_cand, n_items, 0, P->d_scan, P->d_item_off, s, P->n_items));
   k_tile_map<<<256, 256, 0, s>>>(P->d_item_off, n_items, P->n_cand, P->d_tile_item0, P->d_tile_first);
   CHECK_LAUNCH();
   TRY(record(ev, 3, s));
@@ -703,7 +712,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   const unsigned tiles = (unsigned)std::max<long long>(1, (P->n_tiles + kEvalThreads / 32 - 1) / (kEvalThreads / 32));
   k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_cnt);
   CHECK_LAUNCH();
-  TRY(scan_launch(P->d_tile_cnt, nullptr, P->n_tiles, P->d_scan, P->d_tile_off, s));
+  TRY(scan_launch(P->d_tile_cnt, nullptr, P->n_tiles, P->d_scan, P->d_tile_off, s, P->n_tiles));
   k_tile_write<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_off);
   CHECK_LAUNCH();
   TRY(record(ev, 6, s));

@@ -16,6 +16,7 @@ constexpr int kWindow = 2048;         // candidates mapped to lines per pass of 
 constexpr int kSiddonThreads = 128;   // lanes per ray (one CTA) of the depth-table kernel
 constexpr int kScanBlocks = 1024;     // blocks of the device-wide scan
 constexpr int kScanThreads = 256;
+constexpr long long kSmallScan = 4096;   // inputs up to this length use the one-block scan
 
 // float-float value: hi + lo with |lo| <= ulp(hi)/2 (compensated FP32)
 struct ff { float hi, lo; };

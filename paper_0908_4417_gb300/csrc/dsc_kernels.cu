@@ -1169,6 +1169,44 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partial(const int* __rest
   }
 }
 
+// the same scan in one block, for short inputs (one launch instead of three):
+// each thread takes a contiguous run, the block scans the run totals
+__global__ void __launch_bounds__(1024) k_scan_small(const int* __restrict__ in, const long long* n_ptr,
+                                                     long long n_const, long long* out) {
+  __shared__ long long ws[32];
+  const long long n = n_ptr ? *n_ptr : n_const;
+  const long long per = (n + 1023) / 1024;
+  const long long a = threadIdx.x * per, b = min(a + per, n);
+  long long s = 0;
+  for (long long i = a; i < b; ++i) s += (long long)in[i];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long x = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) ws[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const long long v = ws[lane];
+    long long vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long x = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += x;
+    }
+    ws[lane] = vi - v;
+    if (lane == 31) out[n] = vi;                    // total
+  }
+  __syncthreads();
+  long long run = ws[w] + incl - s;
+  for (long long i = a; i < b; ++i) {
+    out[i] = run;
+    run += (long long)in[i];
+  }
+}
+
 __global__ void __launch_bounds__(kScanBlocks) k_scan_blocks(long long* block_sums) {
   __shared__ long long ws[kScanBlocks / 32];
   int t = threadIdx.x, lane = t & 31, w = t >> 5;

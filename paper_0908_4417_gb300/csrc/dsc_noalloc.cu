@@ -40,6 +40,7 @@ __global__ void k_row_ptr(const long long*, const long long*, const long long*, 
 __global__ void k_scan_partial(const int*, const long long*, long long, long long*);
 __global__ void k_scan_blocks(long long*);
 __global__ void k_scan_final(const int*, const long long*, long long, const long long*, long long*);
+__global__ void k_scan_small(const int*, const long long*, long long, long long*);
 }  // namespace dsc
 
 using namespace dsc;
@@ -110,7 +111,12 @@ struct Carve {
 };
 
 static dsc_status na_scan(const int* in, const long long* n_dev, long long n_const, long long* tmp, long long* out,
-                          cudaStream_t s) {
+                          cudaStream_t s, long long n_host) {
+  if (n_host <= kSmallScan) {
+    k_scan_small<<<1, 1024, 0, s>>>(in, n_dev, n_const, out);
+    NA_LAUNCH();
+    return DSC_OK;
+  }
   k_scan_partial<<<kScanBlocks, kScanThreads, 0, s>>>(in, n_dev, n_const, tmp);
   NA_LAUNCH();
   k_scan_blocks<<<1, kScanBlocks, 0, s>>>(tmp);
@@ -247,7 +253,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   // set-up and work items
   k_setup<<<(nrows + 31) / 32, 32, 0, s>>>(d_inst, d_beams, nbeams, d_rows, nrows, d_row_items, target_cand);
   NA_LAUNCH();
-  st = na_scan(d_row_items, nullptr, nrows, d_scan, d_rib, s);
+  st = na_scan(d_row_items, nullptr, nrows, d_scan, d_rib, s, nrows);
   if (st != DSC_OK) return st;
   long long n_items = 0;
   NA_CU(cudaMemcpyAsync(&n_items, d_rib + nrows, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -269,7 +275,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   NA_LAUNCH();
   k_count<<<grid_items, kEvalThreads, 0, s>>>(d_inst, d_rows, d_rib, nrows, n_items_dev, d_item_cand, d_item_row);
   NA_LAUNCH();
-  st = na_scan(d_item_cand, n_items_dev, 0, d_scan, d_item_off, s);
+  st = na_scan(d_item_cand, n_items_dev, 0, d_scan, d_item_off, s, n_items);
   if (st != DSC_OK) return st;
   long long n_cand = 0;
   NA_CU(cudaMemcpyAsync(&n_cand, d_item_off + n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -344,7 +350,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   const unsigned tiles = (unsigned)(n_tiles > 0 ? (n_tiles + kEvalThreads / 32 - 1) / (kEvalThreads / 32) : 1);
   k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, d_tile_cnt);
   NA_LAUNCH();
-  st = na_scan(d_tile_cnt, nullptr, n_tiles, d_scan, d_tile_off, s);
+  st = na_scan(d_tile_cnt, nullptr, n_tiles, d_scan, d_tile_off, s, n_tiles);
   if (st != DSC_OK) return st;
   long long nnz = 0;
   int status = 0;
