@@ -47,6 +47,7 @@ typedef struct {
     double c1[3], c2[3];
     int cutoff_mode;    /* 0 VOI6, 1 SIGMA, 2 NONE */
     double cutoff_k;
+    int profile;        /* lateral spread kernel: 0 Gaussian (Eq. 3), 1 Laplace, 2 logistic */
 } or_model;
 
 /* one beamlet's frame (Fig. 1b): source S, unit axis e, lateral axes x, z */
@@ -299,7 +300,7 @@ void or_lut_eval(const or_model* m, double d, double* out4) {
 }
 
 /* Eq. 3: F(x', d, z', C) with the beamlet sides a_t, b_t at the depth of O' */
-double or_profile_F(const or_model* m, const double* c3, double xp, double zp, double a_t, double b_t) {
+static double profile_erf(const or_model* m, const double* c3, double xp, double zp, double a_t, double b_t) {
     double F = 0.0;
     for (int i = 0; i < 3; ++i) {
         double s = sqrt(2.0) * c3[i];
@@ -310,6 +311,49 @@ double or_profile_F(const or_model* m, const double* c3, double xp, double zp, d
         F += m->c1[i] / 4.0 * X * Z;
     }
     return F;
+}
+
+/* Other FSPB kernels the paper admits (Section 2.1: any profile that keeps
+ * the self-consistency and normalisation conditions; Jelen et al. combine
+ * exponentials, Lin et al. use the Boltzmann function).  Both are written
+ * like Eq. 3, as the beamlet's box convolved per axis with a spread kernel
+ * of standard deviation c3(d), i.e. per axis
+ *     P(x) = G(( |x| - h) / s) - G((|x| + h) / s),   h = c2 a_t / 2,
+ * with G the kernel's complementary distribution function, and
+ * F = sum_i c1_i P_x P_z (Eq. 3 is the Gaussian case, G = erfc(y / sqrt 2) / 2).
+ *   profile 1, Laplace (exponential) kernel: s = c3 / sqrt 2,
+ *              G(y) = exp(-y) / 2 for y >= 0, 1 - exp(y) / 2 for y < 0;
+ *   profile 2, logistic kernel (the Boltzmann function): s = c3 sqrt 3 / pi,
+ *              G(y) = 1 / (1 + exp(y)).
+ * Each G(y) for y < 0 is taken as 1 - G(-y) so the tails never cancel. */
+static double tail_laplace(double y) { return y >= 0.0 ? 0.5 * exp(-y) : 1.0 - 0.5 * exp(y); }
+static double tail_logistic(double y) {
+    if (y >= 0.0) { double e = exp(-y); return e / (1.0 + e); }
+    double e = exp(y);
+    return 1.0 - e / (1.0 + e);
+}
+
+static double profile_sum(const or_model* m, const double* c3, double xp, double zp, double a_t, double b_t) {
+    double F = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        double s = m->profile == 1 ? c3[i] / sqrt(2.0) : c3[i] * sqrt(3.0) / OR_PI;
+        double hx = m->c2[i] * a_t / 2.0, hz = m->c2[i] * b_t / 2.0;
+        double ax = fabs(xp), az = fabs(zp);
+        double Px, Pz;
+        if (m->profile == 1) {
+            Px = tail_laplace((ax - hx) / s) - tail_laplace((ax + hx) / s);
+            Pz = tail_laplace((az - hz) / s) - tail_laplace((az + hz) / s);
+        } else {
+            Px = tail_logistic((ax - hx) / s) - tail_logistic((ax + hx) / s);
+            Pz = tail_logistic((az - hz) / s) - tail_logistic((az + hz) / s);
+        }
+        F += m->c1[i] * Px * Pz;
+    }
+    return F;
+}
+
+double or_profile_F(const or_model* m, const double* c3, double xp, double zp, double a_t, double b_t) {
+    return m->profile == 0 ? profile_erf(m, c3, xp, zp, a_t, b_t) : profile_sum(m, c3, xp, zp, a_t, b_t);
 }
 
 /* signed lateral cutoff margin (mm, > 0 inside): VOI of 6x the side

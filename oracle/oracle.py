@@ -40,7 +40,7 @@ class OrBeam(C.Structure):
 class OrModel(C.Structure):
     _fields_ = [("n", C.c_int), ("d_max", C.c_double), ("lut", C.c_void_p),
                 ("c1", C.c_double * 3), ("c2", C.c_double * 3),
-                ("cutoff_mode", C.c_int), ("cutoff_k", C.c_double)]
+                ("cutoff_mode", C.c_int), ("cutoff_k", C.c_double), ("profile", C.c_int)]
 
 
 class OrResult(C.Structure):
@@ -120,7 +120,7 @@ class _ModelRef:
         self.s = OrModel(int(self.lut.shape[0]), float(m.d_max), self.lut.ctypes.data,
                          (C.c_double * 3)(*[float(v) for v in m.c1]),
                          (C.c_double * 3)(*[float(v) for v in m.c2]),
-                         int(m.cutoff_mode), float(m.cutoff_k))
+                         int(m.cutoff_mode), float(m.cutoff_k), int(getattr(m, "profile", 0)))
 
 
 class OracleCSR:

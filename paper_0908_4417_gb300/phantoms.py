@@ -153,7 +153,11 @@ class Model:
     c2: tuple = (1.0, 1.0, 1.0)
     cutoff_mode: int = CUTOFF_VOI6
     cutoff_k: float = 3.0
+    profile: int = 0         # PROFILE_ERF (Eq. 3), PROFILE_LAPLACE or PROFILE_LOGISTIC
 
+
+# lateral spread kernel of the FSPB profile
+PROFILE_ERF, PROFILE_LAPLACE, PROFILE_LOGISTIC = 0, 1, 2
 
 # depth-table construction of a workload
 TABLE_EXACT, TABLE_TRILINEAR = 0, 1
@@ -180,7 +184,7 @@ class Workload:
 # --------------------------------------------------------------------------
 def synthetic_model(n: int = 256, d_max: float = 300.0, cutoff_mode: int = CUTOFF_VOI6,
                     cutoff_k: float = 3.0, c1=(0.90, 0.08, 0.02), c2=(1.0, 1.0, 1.0),
-                    c3_slopes=(0.010, 0.030, 0.050), c3_at0=(1.5, 4.0, 10.0)) -> Model:
+                    c3_slopes=(0.010, 0.030, 0.050), c3_at0=(1.5, 4.0, 10.0), profile: int = 0) -> Model:
     """Tabulated depth-dose T(d) and depth-dependent widths c3^(i)(d).
 
     T(d) = [0.4 + 0.6 (1 - exp(-d/5))] exp(-0.0045 d), scaled to a maximum of
@@ -195,7 +199,7 @@ def synthetic_model(n: int = 256, d_max: float = 300.0, cutoff_mode: int = CUTOF
     for i in range(3):
         lut[:, 1 + i] = c3_at0[i] + c3_slopes[i] * d
     return Model(lut=lut.astype(np.float32), d_max=float(d_max), c1=tuple(c1), c2=tuple(c2),
-                 cutoff_mode=cutoff_mode, cutoff_k=float(cutoff_k))
+                 cutoff_mode=cutoff_mode, cutoff_k=float(cutoff_k), profile=int(profile))
 
 
 # --------------------------------------------------------------------------

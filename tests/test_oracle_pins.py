@@ -239,9 +239,11 @@ def test_profile_integral_closed_form():
     assert abs(integral / expect - 1) < 1e-6, integral / expect
 
 
-def test_profile_is_the_erf_box_in_the_narrow_limit():
-    """sigma -> 0: each erf pair is 2 inside |x'| < c2 a_t/2 and 0 outside."""
-    m = P.synthetic_model(c1=(0.5, 0.3, 0.2), c2=(1.0, 0.5, 0.25))
+@pytest.mark.parametrize("profile", [P.PROFILE_ERF, P.PROFILE_LAPLACE, P.PROFILE_LOGISTIC])
+def test_profile_is_the_erf_box_in_the_narrow_limit(profile):
+    """sigma -> 0: each erf pair is 2 inside |x'| < c2 a_t/2 and 0 outside
+    (every profile: the box convolved with a vanishing spread kernel)."""
+    m = P.synthetic_model(c1=(0.5, 0.3, 0.2), c2=(1.0, 0.5, 0.25), profile=profile)
     c3 = np.array([1e-7, 1e-7, 1e-7])
     a_t, b_t = 8.0, 4.0
     for x, z, expect in [(0.1, 0.1, 1.0), (3.0, 0.5, 0.5), (1.5, 0.2, 0.8), (3.0, 1.2, 0.5),
@@ -249,12 +251,14 @@ def test_profile_is_the_erf_box_in_the_narrow_limit():
         assert abs(O.profile_F(m, c3, x, z, a_t, b_t) - expect) < 1e-12, (x, z)
 
 
-def test_beamlets_tile_a_broad_beam():
+@pytest.mark.parametrize("profile", [P.PROFILE_ERF, P.PROFILE_LAPLACE, P.PROFILE_LOGISTIC])
+def test_beamlets_tile_a_broad_beam(profile):
     """Parallel limit, water, no cutoff, no threshold: the sum over a field of
-    n_u x n_v beamlets equals the dose of one beamlet of the whole field."""
+    n_u x n_v beamlets equals the dose of one beamlet of the whole field (the
+    self-consistency condition of Section 2.1, for every profile)."""
     g = P.centred_grid(16, 12, 10, 3.0, 3.0, 3.0)
     rho = np.ones(g.shape, np.float32)
-    m = P.synthetic_model(cutoff_mode=P.CUTOFF_NONE)
+    m = P.synthetic_model(cutoff_mode=P.CUTOFF_NONE, profile=profile)
     sad = 1e9
     small = P.Beam(0.0, sad, (0.0, 0.0, 0.0), 4.0, 6.0, 4, 3)
     broad = P.Beam(0.0, sad, (0.0, 0.0, 0.0), 16.0, 18.0, 1, 1)
@@ -577,3 +581,66 @@ def test_dose_and_beamlet_dot_are_adjoint():
     lhs = np.dot(O.dose(orc, wv, w_.grid.nvox), gv)
     rhs = np.dot(wv, O.beamlet_dot(orc, gv, w_.grid.nvox))
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+
+# ---------------------------------------------------------------------------
+# other FSPB kernels (Section 2.1; NEXT-4): Laplace and logistic spread
+# ---------------------------------------------------------------------------
+def _one_component(profile, i, c2=1.2):
+    c1 = [0.0, 0.0, 0.0]
+    c1[i] = 1.0
+    c2s = [1.0, 1.0, 1.0]
+    c2s[i] = c2
+    return P.synthetic_model(c1=tuple(c1), c2=tuple(c2s), profile=profile)
+
+
+def _spread(profile, c3):
+    return c3 / math.sqrt(2.0) if profile == P.PROFILE_LAPLACE else c3 * math.sqrt(3.0) / math.pi
+
+
+def _P_closed(profile, x, h, s):
+    """box of half-width h convolved with the kernel, written out from the
+    kernel's density by hand: Laplace density exp(-|u|/s)/(2s), logistic
+    density exp(-u/s)/(s (1 + exp(-u/s))^2)."""
+    if profile == P.PROFILE_LAPLACE:
+        x = abs(x)
+        if x <= h:
+            return 1.0 - math.exp(-h / s) * math.cosh(x / s)
+        return math.sinh(h / s) * math.exp(-x / s)
+    cdf = lambda u: 1.0 / (1.0 + math.exp(-u / s))
+    return cdf(x + h) - cdf(x - h)
+
+
+@pytest.mark.parametrize("profile", [P.PROFILE_LAPLACE, P.PROFILE_LOGISTIC])
+def test_new_profiles_closed_form_points(profile):
+    c3 = np.array([1.3, 3.7, 8.2])
+    a_t, b_t = 5.0, 3.0
+    for i in range(3):
+        m = _one_component(profile, i)
+        s = _spread(profile, c3[i])
+        hx, hz = 1.2 * a_t / 2, 1.2 * b_t / 2
+        for x, z in [(0.0, 0.0), (hx, 0.0), (0.4 * hx, 1.3 * hz), (2.5 * hx, 0.2), (-1.1 * hx, -2 * hz)]:
+            expect = _P_closed(profile, x, hx, s) * _P_closed(profile, z, hz, s)
+            assert O.profile_F(m, c3, x, z, a_t, b_t) == pytest.approx(expect, rel=1e-12, abs=1e-300)
+
+
+@pytest.mark.parametrize("profile", [P.PROFILE_LAPLACE, P.PROFILE_LOGISTIC])
+def test_new_profiles_normalisation(profile):
+    """Per axis the profile integrates to the beamlet side 2h (the
+    normalisation condition): integral of F(x, 0) dx = 2 h_x P_z(0), with
+    P_z(0) = F(0, 0) / P_x(0) and P(0) closed form."""
+    c3 = np.array([1.3, 3.7, 8.2])
+    a_t, b_t = 5.0, 3.0
+    for i in range(3):
+        m = _one_component(profile, i)
+        s = _spread(profile, c3[i])
+        hx = 1.2 * a_t / 2
+        R = hx + 40 * s
+        xs = np.linspace(-R, R, 40001)
+        fx = np.array([O.profile_F(m, c3, x, 0.0, a_t, b_t) for x in xs])
+        w = np.ones(xs.size)
+        w[1:-1:2], w[2:-1:2] = 4.0, 2.0
+        integral = (w @ fx) * (xs[1] - xs[0]) / 3.0
+        pz0 = O.profile_F(m, c3, 0.0, 0.0, a_t, b_t) / _P_closed(profile, 0.0, hx, s)
+        assert integral == pytest.approx(2 * hx * pz0, rel=2e-7)
