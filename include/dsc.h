@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define DSC_ABI_VERSION 1
+#define DSC_ABI_VERSION 2
 
 typedef enum {
     DSC_OK = 0,
@@ -79,10 +79,22 @@ enum {
     DSC_CUTOFF_NONE = 2      /* every voxel in front of the source */
 };
 
+/* Lateral profile F of Eq. 2.  Section 2.1 admits any FSPB kernel that keeps
+ * the self-consistency and normalisation conditions; each profile here is the
+ * beamlet's box convolved per axis with a spread kernel whose standard
+ * deviation is c3_i(d):  F = sum_i c1_i P_x P_z with
+ * P(x) = G((|x| - h)/s) - G((|x| + h)/s), h = c2_i a_t / 2, G the kernel's
+ * complementary distribution function. */
+enum {
+    DSC_PROFILE_ERF = 0,      /* Gaussian kernel: Eq. 3 (Jiang's three erf terms) */
+    DSC_PROFILE_LAPLACE = 1,  /* exponential (Laplace) kernel, s = c3 / sqrt 2 */
+    DSC_PROFILE_LOGISTIC = 2  /* logistic kernel, G = Boltzmann function 1/(1 + e^y), s = c3 sqrt 3 / pi */
+};
+
 /* FSPB beam model (Eq. 2-3).  table4 holds n rows {T(d), c3_1(d), c3_2(d),
  * c3_3(d)} at n equally spaced depths on [0, d_max]; values are interpolated
  * linearly and clamped to the last row beyond d_max.  c1, c2 are the
- * depth-independent weights and width factors of the three erf terms.  The
+ * depth-independent weights and width factors of the three terms.  The
  * table is copied; the caller keeps ownership of table4. */
 typedef struct {
     int32_t n;               /* 2 <= n <= 4096 */
@@ -92,6 +104,7 @@ typedef struct {
     double c2[3];
     int32_t cutoff_mode;     /* DSC_CUTOFF_* */
     double cutoff_k;         /* k of DSC_CUTOFF_SIGMA */
+    int32_t profile;         /* DSC_PROFILE_* */
 } dsc_fspb_model;
 
 /* One broad beam from a point source, divided into n_u x n_v beamlets. */

@@ -147,6 +147,7 @@ struct dsc_geometry {
   double c1[3], c2[3];
   int cutoff_mode;
   double cutoff_k;
+  int profile = 0;                   // DSC_PROFILE_*
   float c3max;
   float* d_rho = nullptr;
   float4* d_lut = nullptr;
@@ -372,6 +373,7 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
   if (model->n < 2 || model->n > 4096 || !model->table4 || !(model->d_max > 0))
     return fail(DSC_E_INVAL, "model table: need 2 <= n <= 4096, d_max > 0");
   if (model->cutoff_mode < 0 || model->cutoff_mode > 2) return fail(DSC_E_INVAL, "cutoff_mode");
+  if (model->profile < 0 || model->profile > 2) return fail(DSC_E_INVAL, "profile: DSC_PROFILE_ERF, _LAPLACE or _LOGISTIC");
   int dev;
   TRY(ensure_device(&dev));
   cudaStream_t s = (cudaStream_t)stream;
@@ -384,6 +386,7 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
   for (int i = 0; i < 3; ++i) { g->c1[i] = model->c1[i]; g->c2[i] = model->c2[i]; }
   g->cutoff_mode = model->cutoff_mode;
   g->cutoff_k = model->cutoff_k;
+  g->profile = model->profile;
   float c3max = 0.f;
   for (int k = 0; k < model->n; ++k) {
     float v = model->table4[4 * k + 1];
@@ -511,6 +514,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
     for (int i = 0; i < 3; ++i) { I.c1q[i] = (float)(g->c1[i] / 4.0); I.c2h[i] = (float)(g->c2[i] / 2.0); }
     I.cutoff_mode = g->cutoff_mode;
     I.cutoff_k = (float)g->cutoff_k;
+    I.profile = g->profile;
     double dmin = std::min(g->grid.dx, std::min(g->grid.dy, g->grid.dz));
     I.hd = o->h_frac * dmin;
     I.h = (float)I.hd;
@@ -1342,6 +1346,7 @@ extern "C" dsc_status dsc_server_submit(dsc_server* S, dsc_geometry* geom, const
   for (int i = 0; i < 3; ++i) { q->view.c1[i] = geom->c1[i]; q->view.c2[i] = geom->c2[i]; }
   q->view.cutoff_mode = geom->cutoff_mode;
   q->view.cutoff_k = geom->cutoff_k;
+  q->view.profile = geom->profile;
   q->view.c3max = geom->c3max;
   q->view.d_rho = geom->d_rho;
   q->view.d_lut = geom->d_lut;

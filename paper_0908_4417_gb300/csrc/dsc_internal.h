@@ -36,6 +36,7 @@ struct DInst {
   float c2h[3];            // c2 / 2
   int cutoff_mode;
   float cutoff_k;
+  int profile;             // lateral profile: 0 erf (Eq. 3), 1 Laplace, 2 logistic
   int row_base, nrows;     // rows of this instance in the flat row list
   int beam_base, nbeams;
   float h;                 // depth-table spacing

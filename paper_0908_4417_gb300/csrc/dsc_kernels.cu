@@ -700,21 +700,45 @@ __device__ __forceinline__ void erfc_parts(float2 t, float2 v, const float2* __r
   tp = __fmul2_rn(t, p);
 }
 
-// The X and Z factors of one Eq. 3 component together:
-//   erf(u1) + erf(u2) = erfc(-u1) - erfc(u2),
-//   u1 = (h - |x'|)/s, u2 = (h + |x'|)/s, h = c2/2 a_t (b_t for Z),
-// from the scaled arguments v = u sqrt(log2 e).  erfc(-u1) is erfc(|u1|)
-// outside the beamlet and 2 - erfc(|u1|) inside (no cancellation of 1 - erf
-// in the tails); the sign bit of -u1 picks the form.  abt = (a_t, b_t),
-// axz = (|x'|, |z'|), c2hn = -c2/2; h -/+ |x'| and the final sums round once.
+// The X and Z factors of one profile term together.  Every profile is the
+// beamlet's box convolved per axis with a spread kernel: with G the kernel's
+// complementary distribution function and y1 = (|x'| - h)/s,
+// y2 = (|x'| + h)/s (h = c2/2 a_t, b_t for Z),
+//   X = 2 [G(y1) - G(y2)],   2 G(y1) = (1 - sgn y1) + sgn(y1) T(|y1|),
+// T(y) = 2 G(y) for y >= 0 the kernel's tail; the sign bit of y1 picks the
+// form, so the tails never cancel.  For Eq. 3 (Gaussian) X is the erf pair
+// erf(u1) + erf(u2) = erfc(-u1) - erfc(u2), T = erfc.  Arguments arrive
+// scaled (v = y in the units the tail wants: Prof<P>::K / c3); abt = (a_t,
+// b_t), axz = (|x'|, |z'|), c2hn = -c2/2; |x'| -/+ h and the sums round once.
+//   P = 0  Gaussian:  T = erfc(u), v = u sqrt(log2 e)
+//   P = 1  Laplace:   T = exp(-y) = 2^-v,                 s = c3 / sqrt 2
+//   P = 2  logistic:  T = 2 exp(-y) / (1 + exp(-y)),      s = c3 sqrt 3 / pi
+template <int PROF> struct Prof;
+template <> struct Prof<0> { static constexpr float K = 0.84932180028801904272f; };   // sqrt(log2(e) / 2)
+template <> struct Prof<1> { static constexpr float K = 2.04027889319357896350f; };   // log2(e) sqrt 2
+template <> struct Prof<2> { static constexpr float K = 2.61675934794826075443f; };   // log2(e) pi / sqrt 3
+
+template <int PROF>
 __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, float2 axz, float inv_s) {
-  constexpr float kPs = kErfcP * kInvSqrtL;   // p / sqrt(log2 e)
-  const float2 x = __fmul2_rn(__ffma2_rn(f2(c2hn), abt, axz), f2(inv_s));   // -u1 sqrt(log2 e)
-  const float2 v2 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, axz), f2(inv_s));  //  u2 sqrt(log2 e) >= 0
+  const float2 x = __fmul2_rn(__ffma2_rn(f2(c2hn), abt, axz), f2(inv_s));   // y1, scaled
+  const float2 v2 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, axz), f2(inv_s));  // y2, scaled (>= 0)
   float2 tp1, e1, tp2n, e2;
-  erfc_parts(rcp2(make_float2(fmaf(kPs, fabsf(x.x), 1.0f), fmaf(kPs, fabsf(x.y), 1.0f))), x, kErfcC2, tp1, e1);
-  erfc_parts(rcp2(__ffma2_rn(f2(kPs), v2, f2(1.0f))), v2, kErfcC2n, tp2n, e2);
-  // erfc(x) = (1 - s) + s tp e, s = +-1 the sign of x (its sign bit on 1.0f)
+  if (PROF == 0) {
+    constexpr float kPs = kErfcP * kInvSqrtL;   // p / sqrt(log2 e)
+    erfc_parts(rcp2(make_float2(fmaf(kPs, fabsf(x.x), 1.0f), fmaf(kPs, fabsf(x.y), 1.0f))), x, kErfcC2, tp1, e1);
+    erfc_parts(rcp2(__ffma2_rn(f2(kPs), v2, f2(1.0f))), v2, kErfcC2n, tp2n, e2);
+  } else {
+    e1 = make_float2(ex2_approx(-fabsf(x.x)), ex2_approx(-fabsf(x.y)));
+    e2 = make_float2(ex2_approx(-v2.x), ex2_approx(-v2.y));
+    if (PROF == 1) {
+      tp1 = f2(1.0f);
+      tp2n = f2(-1.0f);
+    } else {                                  // 2 / (1 + e) from the reciprocal of (1 + e) / 2
+      tp1 = rcp2(__ffma2_rn(e1, f2(0.5f), f2(0.5f)));
+      tp2n = rcp2(__ffma2_rn(e2, f2(-0.5f), f2(-0.5f)));
+    }
+  }
+  // 2 G(y1) = (1 - s) + s tp e, s = +-1 the sign of y1 (its sign bit on 1.0f)
   const float2 sg = make_float2(__uint_as_float((__float_as_uint(x.x) & 0x80000000u) | 0x3f800000u),
                                 __uint_as_float((__float_as_uint(x.y) & 0x80000000u) | 0x3f800000u));
   const float2 erfc_x = __ffma2_rn(__fmul2_rn(sg, tp1), e1, __ffma2_rn(sg, f2(-1.0f), f2(1.0f)));
@@ -735,6 +759,7 @@ struct RowConst {
 };
 
 // D for candidate ix of a line; returns -1 outside the SIGMA cutoff
+template <int PROF>
 __device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 sx, float2 zz, int mode) {
   // s = t - tA in float-float
   float ph = __fmul_rn(fi, C.Sx.hi);
@@ -779,15 +804,15 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 s
     float lim = C.cutoff_k * Pxy.y;
     if (axz.x > fmaf(0.5f, abt.x, lim) || axz.y > fmaf(0.5f, abt.y, lim)) return -1.0f;
   }
-  // Eq. 3: three erf-pair products; arguments scaled by sqrt(log2 e):
-  // 1/(sqrt(2) c3) * sqrt(log2 e) = sqrt(log2(e)/2) / c3
-  constexpr float kSqrtHalfL = 0.84932180028801904272f;
+  // Eq. 3 (or another profile): three pair products, arguments scaled by
+  // Prof<PROF>::K / c3 (for Eq. 3: 1/(sqrt(2) c3) * sqrt(log2 e))
+  constexpr float kSqrtHalfL = Prof<PROF>::K;
   const float c3[3] = {Pxy.y, Pzw.x, Pzw.y};
   float F = 0.0f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const float inv_s = kSqrtHalfL * rcp_approx(c3[i]);
-    const float2 XZ = erf_pair2(C.c2h[i], C.c2hn[i], abt, axz, inv_s);
+    const float2 XZ = erf_pair2<PROF>(C.c2h[i], C.c2hn[i], abt, axz, inv_s);
     F = fmaf(C.c1q[i] * XZ.x, XZ.y, F);
   }
   // Eq. 2 with A = T(d) (SAD/t)^2; 1/t with one Newton step
@@ -814,6 +839,36 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
   C.lut_last = (float)(G.n_lut - 1);
   for (int i = 0; i < 3; ++i) { C.c1q[i] = G.c1q[i]; C.c2h[i] = G.c2h[i]; C.c2hn[i] = -G.c2h[i]; }
   C.cutoff_k = G.cutoff_k;
+}
+
+// the candidates [w0, w0 + wl) of an item's window, profile PROF (block-uniform)
+template <int PROF>
+__device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm, int w0, int wl, float* out,
+                                            int* outc, int mode, float& vmax, int& valid) {
+  // two candidates per thread per pass: independent chains to interleave
+  for (int j = threadIdx.x; j < wl; j += 2 * kEvalThreads) {
+    const int j2 = j + kEvalThreads;
+    const bool two = j2 < wl;
+    const int jb = two ? j2 : j;
+    int li = min((int)sm.map[j], sm.nl - 1);
+    int lb = min((int)sm.map[jb], sm.nl - 1);
+    float4 sx = sm.sx[li], sxb = sm.sx[lb];
+    float4 zc = sm.zc[li], zcb = sm.zc[lb];
+    int ix = __float_as_int(zc.z) + (w0 + j - sm.off[li]);
+    int ixb = __float_as_int(zcb.z) + (w0 + jb - sm.off[lb]);
+    float D = eval_pair<PROF>(C, (float)ix, sx, make_float2(zc.x, zc.y), mode);
+    float Db = eval_pair<PROF>(C, (float)ixb, sxb, make_float2(zcb.x, zcb.y), mode);
+    out[w0 + j] = D;
+    outc[w0 + j] = __float_as_int(zc.w) + ix;
+    vmax = fmaxf(vmax, D);
+    if (mode == 1) valid += D >= 0.0f;
+    if (two) {
+      out[w0 + jb] = Db;
+      outc[w0 + jb] = __float_as_int(zcb.w) + ixb;
+      vmax = fmaxf(vmax, Db);
+      if (mode == 1) valid += Db >= 0.0f;
+    }
+  }
 }
 
 // persistent: CTAs take work items from a queue; every candidate's D goes to
@@ -847,29 +902,10 @@ __global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
     for (int w0 = 0; w0 < total; w0 += kWindow) {
       int wl = min(kWindow, total - w0);
       item_map(sm, w0, wl);
-      // two candidates per thread per pass: independent chains to interleave
-      for (int j = threadIdx.x; j < wl; j += 2 * kEvalThreads) {
-        const int j2 = j + kEvalThreads;
-        const bool two = j2 < wl;
-        const int jb = two ? j2 : j;
-        int li = min((int)sm.map[j], sm.nl - 1);
-        int lb = min((int)sm.map[jb], sm.nl - 1);
-        float4 sx = sm.sx[li], sxb = sm.sx[lb];
-        float4 zc = sm.zc[li], zcb = sm.zc[lb];
-        int ix = __float_as_int(zc.z) + (w0 + j - sm.off[li]);
-        int ixb = __float_as_int(zcb.z) + (w0 + jb - sm.off[lb]);
-        float D = eval_pair(C, (float)ix, sx, make_float2(zc.x, zc.y), mode);
-        float Db = eval_pair(C, (float)ixb, sxb, make_float2(zcb.x, zcb.y), mode);
-        out[w0 + j] = D;
-        outc[w0 + j] = __float_as_int(zc.w) + ix;
-        vmax = fmaxf(vmax, D);
-        if (mode == 1) valid += D >= 0.0f;
-        if (two) {
-          out[w0 + jb] = Db;
-          outc[w0 + jb] = __float_as_int(zcb.w) + ixb;
-          vmax = fmaxf(vmax, Db);
-          if (mode == 1) valid += Db >= 0.0f;
-        }
+      switch (G.profile) {
+        case 1: eval_window<1>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+        case 2: eval_window<2>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+        default: eval_window<0>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
       }
       __syncthreads();
     }

@@ -137,8 +137,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
       (long long)grid->nx * grid->ny * grid->nz >= (1ll << 31))
     return na_fail(DSC_E_INVAL, "grid: need dimensions >= 1, sides > 0, fewer than 2^31 voxels");
   if (model->n < 2 || model->n > 4096 || !model->table4 || !(model->d_max > 0) || model->cutoff_mode < 0 ||
-      model->cutoff_mode > 2)
-    return na_fail(DSC_E_INVAL, "model: need 2 <= n <= 4096, d_max > 0, cutoff_mode 0..2");
+      model->cutoff_mode > 2 || model->profile < 0 || model->profile > 2)
+    return na_fail(DSC_E_INVAL, "model: need 2 <= n <= 4096, d_max > 0, cutoff_mode 0..2, profile 0..2");
   if (opts->value_dtype != DSC_VALUE_F32 || !(opts->rel_threshold >= 0) || !(opts->h_frac > 0 && opts->h_frac <= 1))
     return na_fail(DSC_E_INVAL, "opts: FP32 values only, rel_threshold >= 0, 0 < h_frac <= 1");
   if (capacity < 0) return na_fail(DSC_E_INVAL, "capacity < 0");
@@ -166,6 +166,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   for (int i = 0; i < 3; ++i) { I.c1q[i] = (float)(model->c1[i] / 4.0); I.c2h[i] = (float)(model->c2[i] / 2.0); }
   I.cutoff_mode = model->cutoff_mode;
   I.cutoff_k = (float)model->cutoff_k;
+  I.profile = model->profile;
   double dmin = grid->dx < grid->dy ? grid->dx : grid->dy;
   dmin = grid->dz < dmin ? grid->dz : dmin;
   I.hd = opts->h_frac * dmin;

@@ -22,6 +22,7 @@ DSC_OK = 0
 DSC_E_BUSY = 8
 DSC_CUTOFF_VOI6, DSC_CUTOFF_SIGMA, DSC_CUTOFF_NONE = 0, 1, 2
 DSC_VALUE_F32, DSC_VALUE_BF16 = 0, 1
+DSC_PROFILE_ERF, DSC_PROFILE_LAPLACE, DSC_PROFILE_LOGISTIC = 0, 1, 2
 DSC_FLAG_TIMING = 1
 DSC_FLAG_TRILINEAR_TABLE = 2
 STAGES = ("setup", "siddon", "count", "eval", "beam_scale", "compact", "finish", "total")
@@ -43,7 +44,8 @@ class GridDesc(C.Structure):
 
 class FspbModel(C.Structure):
     _fields_ = [("n", C.c_int32), ("d_max", C.c_double), ("table4", C.c_void_p),
-                ("c1", C.c_double * 3), ("c2", C.c_double * 3), ("cutoff_mode", C.c_int32), ("cutoff_k", C.c_double)]
+                ("c1", C.c_double * 3), ("c2", C.c_double * 3), ("cutoff_mode", C.c_int32), ("cutoff_k", C.c_double),
+                ("profile", C.c_int32)]
 
 
 class BeamDesc(C.Structure):
@@ -154,7 +156,7 @@ class _ModelRef:
         self.table = np.ascontiguousarray(m.lut, dtype=np.float32)
         self.s = FspbModel(int(self.table.shape[0]), float(m.d_max), self.table.ctypes.data,
                            (C.c_double * 3)(*[float(v) for v in m.c1]), (C.c_double * 3)(*[float(v) for v in m.c2]),
-                           int(m.cutoff_mode), float(m.cutoff_k))
+                           int(m.cutoff_mode), float(m.cutoff_k), int(getattr(m, "profile", 0)))
 
 
 # ---------------------------------------------------------------------------

@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_library_metadata(lib):
-    assert dsc.dsc_abi_version() == 1
+    assert dsc.dsc_abi_version() == 2
     assert lib.dsc_status_str(0) == b"ok"
     assert lib.dsc_status_str(5) == b"device wait timed out"
     assert dsc.dsc_launch_count() >= 0
@@ -53,6 +53,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(dsc.ComputeOpts) == 32
     assert C.sizeof(dsc.CsrView) == 3 * 8 + 3 * 8 + 8 + 8 + 8 + 8
     assert C.sizeof(dsc.Tuning) == 8
+    assert C.sizeof(dsc.FspbModel) == 8 + 8 + 8 + 48 + 8 + 8 + 8
 
 
 def test_tuning_is_validated_and_round_trips(lib):

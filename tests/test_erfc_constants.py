@@ -55,7 +55,12 @@ def test_fitted_form_error_fp64_and_fp32():
 def test_scaling_constants():
     src = open(os.path.join(CSRC, "dsc_kernels.cu")).read()
     inv_sqrt_l = float(re.search(r"kInvSqrtL = ([0-9.]+)f", src).group(1))
-    sqrt_half_l = float(re.search(r"kSqrtHalfL = ([0-9.]+)f", src).group(1))
+    K = {int(m.group(1)): float(m.group(2)) for m in
+         re.finditer(r"struct Prof<(\d)> \{ static constexpr float K = ([0-9.]+)f", src)}
+    sqrt_half_l = K[0]
+    # the other profiles' scales: Laplace s = c3/sqrt 2, logistic s = c3 sqrt 3/pi, both in log2 units
+    assert abs(K[1] - math.sqrt(2.0) / math.log(2.0)) < 1e-15
+    assert abs(K[2] - math.pi / math.sqrt(3.0) / math.log(2.0)) < 1e-15
     log2e = 1.0 / math.log(2.0)
     assert abs(inv_sqrt_l - 1.0 / math.sqrt(log2e)) < 1e-15
     assert abs(sqrt_half_l - math.sqrt(log2e / 2.0)) < 1e-15

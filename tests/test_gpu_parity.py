@@ -269,6 +269,20 @@ def test_table1_water_cases_sampled_rows(dsc, case):
     cleanup(dsc, res, g)
 
 
+@pytest.mark.parametrize("profile", [P.PROFILE_LAPLACE, P.PROFILE_LOGISTIC])
+@pytest.mark.parametrize("name", ["water_32", "slabs_128"])
+def test_other_profiles_match_oracle(dsc, name, profile):
+    """The FSPB kernel replaced (Section 2.1): Laplace (exponential) and
+    logistic (Boltzmann) spread, against the oracle's FP64 forms."""
+    import dataclasses
+    w = P.get(name)
+    w = dataclasses.replace(w, model=dataclasses.replace(w.model, profile=profile), value_dtype=P.VALUE_F32)
+    csr, res, g = run(dsc, w)
+    orc = O.compute_workload(w)
+    print(f"{name} profile {profile}", compare(gpu_rows(csr, range(w.nrows)), orc, TOL))
+    cleanup(dsc, res, g)
+
+
 # ---------------------------------------------------------------------------
 # edge cases: ragged grids, oblique/anisotropic, cutoff modes, misses, empties
 # ---------------------------------------------------------------------------
