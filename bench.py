@@ -310,17 +310,35 @@ def run_ours(args):
         h_col = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
         h_val = torch.empty(max(nnz, 1) * vsize, dtype=torch.uint8).pin_memory()
         h_sc = torch.empty(max(nbeams, 1), dtype=torch.float32).pin_memory()
+        # Pipelined across steps: step k+1's upload and computation are queued
+        # before step k's CSR is read back (on a second stream), so the host
+        # link and the SMs work at the same time.  Every step still moves its
+        # own input up and its own result down inside the timed region.
         e2e_steps = max(3, args.steps // 2)
+        cstream = torch.cuda.Stream(dev)
+        csp = cstream.cuda_stream
+
+        def read_back(res):
+            dsc.dsc_copy_csr_to_host(res, h_rp.data_ptr(), h_col.data_ptr(), h_val.data_ptr(), h_sc.data_ptr(), csp)
+            dsc.dsc_release_result(res)
+
+        pending = None
         for k in range(e2e_steps + 2):
             if k == 2:
                 stream.synchronize()
+                cstream.synchronize()
                 t0 = time.perf_counter()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
             dsc.dsc_upload_density(g, host_rho.data_ptr(), False, sp)
             r = dsc.dsc_compute_dij(g, plain, sp)
-            dsc.dsc_copy_csr_to_host(r, h_rp.data_ptr(), h_col.data_ptr(), h_val.data_ptr(), h_sc.data_ptr(), sp)
-            dsc.dsc_release_result(r)
+            if pending is not None:
+                read_back(pending)             # the previous step's result (its copy is in the window)
+            pending = r
+        read_back(pending)
+        join = torch.cuda.Event()
+        join.record(cstream)
+        stream.wait_event(join)
         e1 = torch.cuda.Event(enable_timing=True)
         e1.record(stream)
         stream.synchronize()
