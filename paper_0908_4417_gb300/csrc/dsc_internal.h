@@ -13,7 +13,7 @@ namespace dsc {
 constexpr int kEvalThreads = 128;     // threads per CTA of the evaluation / compaction kernels
 constexpr int kMaxLinesPerItem = 512;  // x-lines handled by one work item (multiple of kEvalThreads)
 constexpr int kWindow = 2048;         // candidates mapped to lines per pass of an item
-constexpr int kSiddonThreads = 128;   // lanes per ray (one CTA) of the depth-table kernel
+constexpr int kSiddonThreads = 32;    // lanes per ray (one warp, one CTA) of the depth-table kernels
 constexpr int kScanBlocks = 1024;     // blocks of the device-wide scan
 constexpr int kScanThreads = 256;
 constexpr long long kSmallScan = 4096;   // inputs up to this length use the one-block scan

@@ -332,6 +332,7 @@ WORKLOADS = {
     "prostate_256": prostate_256,
     "prostate_256_2f": lambda: prostate_256(fields=2),
 }
+WORKLOADS.update({f"table1_case{c}": (lambda c=c: table1_water(c)) for c in range(1, 8)})
 
 
 def get(name: str) -> Workload:
