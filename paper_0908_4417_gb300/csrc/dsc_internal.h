@@ -66,6 +66,9 @@ struct DRow {
   // voxel loop, compensated FP32: value at voxel (0,0,0) and per-index slopes
   ff S0, X0, Z0;           // s = t - tA, x', z' at voxel (0,0,0)
   ff Ss[3], Xs[3], Zs[3];  // change of s, x', z' per step in ix, iy, iz
+  // s again in 64-bit fixed point, units of h 2^-32 (the depth-table cell is
+  // the high word, the fraction the low word): value at voxel (0,0,0), steps
+  long long sfx0, sfx_s[3];
   float tA_f;
   float kx, kz, bx, bz;    // lateral cutoff |x'| <= kx t + bx, |z'| <= kz t + bz
   float a_sad, b_sad;      // a / SAD, b / SAD (a_t = a_sad * t)

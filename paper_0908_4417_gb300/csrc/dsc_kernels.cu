@@ -158,6 +158,11 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
     R.Xs[k] = ff_from_double(sp[k] * x[k]);
     R.Zs[k] = ff_from_double(sp[k] * z[k]);
   }
+  {
+    const double u = ldexp(1.0, 32) / G.hd;        // fixed-point units per mm
+    R.sfx0 = __double2ll_rn((dot3(w0, e) - R.tA) * u);
+    for (int k = 0; k < 3; ++k) R.sfx_s[k] = __double2ll_rn(sp[k] * e[k] * u);
+  }
   R.sad = (float)B.sad;
   R.a_sad = (float)(B.a / B.sad);
   R.b_sad = (float)(B.b / B.sad);
@@ -447,8 +452,9 @@ __global__ void __launch_bounds__(kSiddonThreads) k_trilinear_table(const DInst*
 // x-lines of a work item
 // ---------------------------------------------------------------------------
 struct LineSm {
-  float4 sx[kMaxLinesPerItem];        // s hi, s lo, x' hi, x' lo at ix = 0
-  float4 zc[kMaxLinesPerItem];        // z' hi, z' lo, first ix (int bits), nx (iy + ny iz) (int bits)
+  float4 sx[kMaxLinesPerItem];        // t, x' hi, x' lo, z' hi at ix = 0
+  float4 zc[kMaxLinesPerItem];        // z' lo, first ix (int bits), nx (iy + ny iz) (int bits), unused
+  long long sf[kMaxLinesPerItem];     // s at ix = 0 in fixed point (units of h 2^-32)
   int off[kMaxLinesPerItem + 1];
   int wscan[kEvalThreads / 32];
   unsigned short map[kWindow];
@@ -565,8 +571,9 @@ __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, l
       ff s0, x0, z0;
       int lo;
       len[q] = line_setup(R, mode, nx, iy, iz, s0, x0, z0, lo);
-      sm.sx[li] = make_float4(s0.hi, s0.lo, x0.hi, x0.lo);
-      sm.zc[li] = make_float4(z0.hi, z0.lo, __int_as_float(lo), __int_as_float(nx * (iy + ny * iz)));
+      sm.sx[li] = make_float4(R.tA_f + s0.hi, x0.hi, x0.lo, z0.hi);
+      sm.zc[li] = make_float4(z0.lo, __int_as_float(lo), __int_as_float(nx * (iy + ny * iz)), 0.0f);
+      sm.sf[li] = R.sfx0 + (long long)iy * R.sfx_s[1] + (long long)iz * R.sfx_s[2];
     }
     mine += len[q];
   }
@@ -747,9 +754,10 @@ __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, f
 
 // everything the per-pair evaluation reads, loaded once per work item
 struct RowConst {
-  ff Sx;                 // slope of s per ix
+  long long dsf;         // slope of s per ix, fixed point (units of h 2^-32)
+  float tx;              // slope of t per ix
   float Xxh, Xxl, Zxh, Zxl;
-  float tA, h, inv_h, sad, a_sad, b_sad;
+  float sad, a_sad, b_sad;
   int n_table;
   const float* tab;      // the row's depth table
   const float4* lut;     // beam-model table
@@ -760,34 +768,25 @@ struct RowConst {
 
 // D for candidate ix of a line; returns -1 outside the SIGMA cutoff
 template <int PROF>
-__device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 sx, float2 zz, int mode) {
-  // s = t - tA in float-float
-  float ph = __fmul_rn(fi, C.Sx.hi);
-  float pl = fmaf(fi, C.Sx.hi, -ph);
-  ff a = two_sum(sx.x, ph);
-  float s_lo = __fadd_rn(a.lo, __fadd_rn(pl, fmaf(fi, C.Sx.lo, sx.y)));
-  float s_hi = a.hi;
-  float xp = fmaf(fi, C.Xxh, sx.z) + fmaf(fi, C.Xxl, sx.w);
-  float zp = fmaf(fi, C.Zxh, zz.x) + fmaf(fi, C.Zxl, zz.y);
-  float t = s_hi + C.tA;
+__device__ __forceinline__ float eval_pair(const RowConst& C, int ix, float4 sx, float zlo, long long sf, int mode) {
+  // t, x', z' of voxel ix on the line (compensated FP32 for x', z')
+  const float fi = (float)ix;
+  const float t = fmaf(fi, C.tx, sx.x);
+  const float xp = fmaf(fi, C.Xxh, sx.y) + fmaf(fi, C.Xxl, sx.z);
+  const float zp = fmaf(fi, C.Zxh, sx.w) + fmaf(fi, C.Zxl, zlo);
 
   // radiological depth at O' (Section 2.2): linear interpolation of the
-  // table; the cell and fraction come from the float-float s.  s <= 0 gives
-  // depth 0 (cell 0, fraction 0), past the last entry the last value.
-  float kf = floorf(s_hi * C.inv_h);
-  float khh = __fmul_rn(kf, C.h);
-  float khl = fmaf(kf, C.h, -khh);
-  float r = __fadd_rn(__fsub_rn(__fsub_rn(s_hi, khh), khl), s_lo);
-  kf = r < 0.0f ? kf - 1.0f : kf;
-  r = r < 0.0f ? r + C.h : r;
-  kf = r >= C.h ? kf + 1.0f : kf;
-  r = r >= C.h ? r - C.h : r;
-  const bool neg = (s_hi + s_lo) <= 0.0f;
-  const bool past = kf >= (float)(C.n_table - 1);
-  int k = neg ? 0 : (past ? C.n_table - 2 : (int)kf);
-  float f = neg ? 0.0f : r * C.inv_h;
-  float d0 = __ldg(C.tab + k), d1 = __ldg(C.tab + k + 1);
-  float d = past ? d1 : fmaf(f, d1 - d0, d0);
+  // table; s = t - tA in fixed point (units of h 2^-32): the cell is the
+  // high word, the fraction the low word.  s <= 0 gives depth 0 (cell 0,
+  // fraction 0), past the last entry the last value.
+  const long long s = sf + (long long)ix * C.dsf;
+  const int cell = (int)(s >> 32);
+  const bool neg = s <= 0;
+  const bool past = cell >= C.n_table - 1;
+  const int k = neg ? 0 : (past ? C.n_table - 2 : cell);
+  const float f = neg ? 0.0f : __uint_as_float(((unsigned)s >> 9) | 0x3f800000u) - 1.0f;   // low word / 2^32
+  const float d0 = __ldg(C.tab + k), d1 = __ldg(C.tab + k + 1);
+  const float d = past ? d1 : fmaf(f, d1 - d0, d0);
 
   // beam-model table: T(d), c3_1..3(d); past the end, the last row
   float g = fmaxf(d * C.lut_scale, 0.0f);   // also maps a NaN depth to 0
@@ -823,12 +822,10 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 s
 }
 
 __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const DInst& G, const float* tab) {
-  C.Sx = R.Ss[0];
+  C.dsf = R.sfx_s[0];
+  C.tx = R.Ss[0].hi;
   C.Xxh = R.Xs[0].hi; C.Xxl = R.Xs[0].lo;
   C.Zxh = R.Zs[0].hi; C.Zxl = R.Zs[0].lo;
-  C.tA = R.tA_f;
-  C.h = G.h;
-  C.inv_h = G.inv_h;
   C.sad = R.sad;
   C.a_sad = R.a_sad;
   C.b_sad = R.b_sad;
@@ -854,17 +851,17 @@ __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm,
     int lb = min((int)sm.map[jb], sm.nl - 1);
     float4 sx = sm.sx[li], sxb = sm.sx[lb];
     float4 zc = sm.zc[li], zcb = sm.zc[lb];
-    int ix = __float_as_int(zc.z) + (w0 + j - sm.off[li]);
-    int ixb = __float_as_int(zcb.z) + (w0 + jb - sm.off[lb]);
-    float D = eval_pair<PROF>(C, (float)ix, sx, make_float2(zc.x, zc.y), mode);
-    float Db = eval_pair<PROF>(C, (float)ixb, sxb, make_float2(zcb.x, zcb.y), mode);
+    int ix = __float_as_int(zc.y) + (w0 + j - sm.off[li]);
+    int ixb = __float_as_int(zcb.y) + (w0 + jb - sm.off[lb]);
+    float D = eval_pair<PROF>(C, ix, sx, zc.x, sm.sf[li], mode);
+    float Db = eval_pair<PROF>(C, ixb, sxb, zcb.x, sm.sf[lb], mode);
     out[w0 + j] = D;
-    outc[w0 + j] = __float_as_int(zc.w) + ix;
+    outc[w0 + j] = __float_as_int(zc.z) + ix;
     vmax = fmaxf(vmax, D);
     if (mode == 1) valid += D >= 0.0f;
     if (two) {
       out[w0 + jb] = Db;
-      outc[w0 + jb] = __float_as_int(zcb.w) + ixb;
+      outc[w0 + jb] = __float_as_int(zcb.z) + ixb;
       vmax = fmaxf(vmax, Db);
       if (mode == 1) valid += Db >= 0.0f;
     }
