@@ -113,7 +113,7 @@ struct OutSlot {
   int* status;             // nonzero when a bounded device wait expired
 };
 
-constexpr int kTilePer = 16;                      // candidates per thread of the compaction
+constexpr int kTilePer = 8;                       // candidates per thread of the compaction
 constexpr int kTile = 32 * kTilePer;              // candidates per compaction tile (one warp)
 
 struct CompactParams {
