@@ -38,8 +38,8 @@ F_PAIR = 337
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of the evaluation kernel per candidate pair, from
 # one Nsight Compute capture of the current kernel on the 2-field prostate
-# (27.85 M pairs, 163.9 MB); the full workload's traffic is this times its pairs
-KEVAL_DRAM_BYTES_PER_PAIR = 5.886
+# (27.85 M pairs, 164.3 MB); the full workload's traffic is this times its pairs
+KEVAL_DRAM_BYTES_PER_PAIR = 5.900
 
 
 def parse():
