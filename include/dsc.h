@@ -95,7 +95,8 @@ enum {
  * c3_3(d)} at n equally spaced depths on [0, d_max]; values are interpolated
  * linearly and clamped to the last row beyond d_max.  c1, c2 are the
  * depth-independent weights and width factors of the three terms.  The
- * table is copied; the caller keeps ownership of table4. */
+ * table is copied; the caller keeps ownership of table4.  DSC_E_INVAL unless
+ * every c3 is finite and > 0 and every T finite. */
 typedef struct {
     int32_t n;               /* 2 <= n <= 4096 */
     double d_max;            /* > 0 */
@@ -258,7 +259,8 @@ dsc_status dsc_get_stage_times(dsc_result* res, float* ms, int32_t n);
 dsc_status dsc_server_create(size_t hbm_budget_bytes, int32_t max_inflight, int32_t max_batch, dsc_server** out);
 /* Queues D_ij for `geom` with an explicit beam set (the geometry's own beam
  * list is not used).  Never blocks; DSC_E_NOMEM_BUDGET if the request could
- * never fit the budget. */
+ * never fit the budget.  The geometry (its density and model table) must
+ * stay alive until the request has been polled. */
 dsc_status dsc_server_submit(dsc_server* srv, dsc_geometry* geom, const dsc_beam_desc* beams, int32_t nbeams,
                              const dsc_compute_opts* opts, uint64_t* req_id);
 /* Waits up to wait_ms (0 = do not wait, < 0 = forever) for request req_id;

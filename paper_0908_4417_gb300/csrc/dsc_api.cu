@@ -374,6 +374,15 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
     return fail(DSC_E_INVAL, "model table: need 2 <= n <= 4096, d_max > 0");
   if (model->cutoff_mode < 0 || model->cutoff_mode > 2) return fail(DSC_E_INVAL, "cutoff_mode");
   if (model->profile < 0 || model->profile > 2) return fail(DSC_E_INVAL, "profile: DSC_PROFILE_ERF, _LAPLACE or _LOGISTIC");
+  float c3max = 0.f;
+  for (int k = 0; k < model->n; ++k) {
+    for (int c = 1; c <= 3; ++c) {
+      const float v = model->table4[4 * k + c];
+      if (!(v > 0.f) || !std::isfinite(v)) return fail(DSC_E_INVAL, "c3 widths must be finite and > 0");
+    }
+    if (!std::isfinite(model->table4[4 * k])) return fail(DSC_E_INVAL, "T(d) must be finite");
+    c3max = std::max(c3max, model->table4[4 * k + 1]);
+  }
   int dev;
   TRY(ensure_device(&dev));
   cudaStream_t s = (cudaStream_t)stream;
@@ -387,12 +396,6 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
   g->cutoff_mode = model->cutoff_mode;
   g->cutoff_k = model->cutoff_k;
   g->profile = model->profile;
-  float c3max = 0.f;
-  for (int k = 0; k < model->n; ++k) {
-    float v = model->table4[4 * k + 1];
-    if (!(v > 0.f)) { delete g; return fail(DSC_E_INVAL, "c3 widths must be > 0"); }
-    c3max = std::max(c3max, v);
-  }
   g->c3max = c3max;
   size_t nvox = (size_t)grid->nx * grid->ny * grid->nz;
   dsc_status st = dalloc(&g->d_rho, nvox, s);

@@ -158,8 +158,12 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   I.lut_scale = (float)((model->n - 1) / model->d_max);
   float c3max = 0.f;
   for (int k = 0; k < model->n; ++k) {
+    for (int c = 1; c <= 3; ++c) {
+      const float w = model->table4[4 * k + c];
+      if (!(w > 0.f) || !std::isfinite(w)) return na_fail(DSC_E_INVAL, "model: c3 widths must be finite and > 0");
+    }
+    if (!std::isfinite(model->table4[4 * k])) return na_fail(DSC_E_INVAL, "model: T(d) must be finite");
     float v = model->table4[4 * k + 1];
-    if (!(v > 0.f)) return na_fail(DSC_E_INVAL, "model: c3 widths must be > 0");
     c3max = v > c3max ? v : c3max;
   }
   I.c3max = c3max;

@@ -69,3 +69,24 @@ def test_tuning_is_validated_and_round_trips(lib):
     dsc.dsc_set_tuning(*before)
     assert lib.dsc_set_tuning(None) == 1 and lib.dsc_get_tuning(None) == 1
     assert lib.dsc_autotune(None, 0, None, None, 1, None, None) == 1
+
+
+def test_model_validation_before_any_device_work(lib):
+    """Every width c3_i must be finite and > 0 and T finite; rejected on the
+    host before a device is touched (CPU only)."""
+    import ctypes as C
+    import numpy as np
+    from paper_0908_4417_gb300 import phantoms as P
+    m = P.synthetic_model()
+    g = dsc.grid_desc(P.centred_grid(4, 4, 4, 2.0, 2.0, 2.0))
+    rho = np.ones(64, np.float32)
+    out = C.c_void_p()
+    for col, bad in ((2, 0.0), (3, -1.0), (1, float("nan")), (0, float("inf"))):
+        lut = m.lut.copy()
+        lut[7, col] = bad
+        mm = dsc._ModelRef(P.Model(lut=lut, d_max=m.d_max))
+        st = lib.dsc_create_geometry(C.byref(g), rho.ctypes.data, 0, C.byref(mm.s), None, C.byref(out))
+        assert st == 1, (col, bad)
+        assert b"finite" in lib.dsc_last_error()
+    bad_profile = dsc._ModelRef(P.Model(lut=m.lut, d_max=m.d_max, profile=3))
+    assert lib.dsc_create_geometry(C.byref(g), rho.ctypes.data, 0, C.byref(bad_profile.s), None, C.byref(out)) == 1
