@@ -1223,6 +1223,12 @@ static size_t estimate_footprint(const dsc_geometry& g, const dsc_compute_opts& 
 
 static dsc_status fetch_counts(dsc_result* r);
 
+// options compared field by field (the struct has padding bytes)
+static bool same_opts(const dsc_compute_opts& a, const dsc_compute_opts& b) {
+  return a.rel_threshold == b.rel_threshold && a.value_dtype == b.value_dtype && a.h_frac == b.h_frac &&
+         a.flags == b.flags;
+}
+
 static void srv_finish_slot(dsc_server* S, SrvSlot& sl) {
   double t = now_s();
   for (auto& q : sl.reqs) {
@@ -1274,7 +1280,7 @@ static void srv_loop(dsc_server* S) {
       size_t fp = 0;
       while (!S->queue.empty() && (int)batch.size() < S->max_batch) {
         auto& q = S->queue.front();
-        if (!batch.empty() && memcmp(&q->opts, &batch[0]->opts, sizeof(dsc_compute_opts)) != 0) break;
+        if (!batch.empty() && !same_opts(q->opts, batch[0]->opts)) break;
         if (S->used + fp + q->footprint > S->budget) break;
         fp += q->footprint;
         batch.push_back(q);
