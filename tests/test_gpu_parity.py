@@ -444,6 +444,19 @@ def test_tile_shapes_are_bit_identical_and_autotune(dsc):
             dsc.dsc_destroy_geometry(g)
 
 
+def test_empty_results_and_products(dsc):
+    """A field whose every beamlet axis misses the grid: an empty CSR, zero
+    dose and zero transpose product, no error."""
+    g0 = P.centred_grid(8, 8, 6, 2.0, 2.0, 2.0)
+    w = P.Workload("all_miss", g0, np.ones(g0.shape, np.float32), P.synthetic_model(),
+                   [P.Beam(0.0, 500.0, (200.0, 0.0, 0.0), 2.0, 2.0, 3, 3)])
+    csr, res, g = run(dsc, w)
+    assert csr.nnz == 0 and csr.pairs == 0 and np.all(csr.row_ptr == 0)
+    d, o = dose_products(dsc, res, np.ones(w.nrows), np.ones(w.grid.nvox))
+    assert np.all(d == 0) and np.all(o == 0)
+    cleanup(dsc, res, g)
+
+
 def test_server_results_same_alone_and_in_mix(dsc):
     ws = small_instances(3)
     gs = [dsc.geometry_from_workload(w) for w in ws]

@@ -42,7 +42,8 @@ def noalloc(dsc, w, capacity):
     row_ptr = torch.full((w.nrows + 1,), -1, dtype=torch.int64, device=dev)
     col = torch.full((capacity,), -1, dtype=torch.int32, device=dev)
     val = torch.full((capacity,), -1.0, dtype=torch.float32, device=dev)
-    opts = dsc.compute_opts(w.tau, P.VALUE_F32, w.h_frac)
+    flags = dsc.DSC_FLAG_TRILINEAR_TABLE if getattr(w, "table_mode", 0) == P.TABLE_TRILINEAR else 0
+    opts = dsc.compute_opts(w.tau, P.VALUE_F32, w.h_frac, flags)
     stream = torch.cuda.current_stream(dev)
     nnz = dsc.dsc_compute_dij_noalloc(w.grid, rho.data_ptr(), w.model, w.beams, opts, row_ptr.data_ptr(),
                                       col.data_ptr(), val.data_ptr(), capacity, stream.cuda_stream)
@@ -60,6 +61,19 @@ def test_two_calls_in_a_row_match_compute_dij(dsc):
         assert np.array_equal(col, ref.col)
         rel = np.abs(val.astype(np.float64) - ref.val) / ref.val
         assert rel.max() <= TOL
+
+
+def test_trilinear_table_and_logistic_profile(dsc):
+    """The option flags and the model's profile reach the fixed-memory path
+    too: same CSR as the allocating entry point."""
+    import dataclasses
+    w = dataclasses.replace(P.slabs_128(value_dtype=P.VALUE_F32), table_mode=P.TABLE_TRILINEAR)
+    w = dataclasses.replace(w, model=dataclasses.replace(w.model, profile=P.PROFILE_LOGISTIC))
+    ref = reference(dsc, w)
+    nnz, row_ptr, col, val = noalloc(dsc, w, ref.nnz + 16)
+    assert nnz == ref.nnz
+    assert np.array_equal(row_ptr, ref.row_ptr) and np.array_equal(col, ref.col)
+    assert np.array_equal(val, ref.val.astype(np.float32))
 
 
 def test_rejects_requests_beyond_the_fixed_memory(dsc):
