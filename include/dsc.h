@@ -228,11 +228,12 @@ void dsc_release_result(dsc_result* res);
  * (its beamlets; one instance of a batch), for every voxel v of its grid.
  * w_dev: nrows floats, dose_dev: ncols floats (voxel order ix + nx (iy + ny
  * iz)), both device pointers, caller-owned.  Queued on `stream` after the
- * computation; the call does not wait.  Each product w_j D_jv is formed
- * exactly and summed in 64-bit fixed point scaled to a bound on |dose|, so
- * the result does not depend on thread order (bit-identical across calls)
- * and lies within one FP32 rounding of the exact sum; BF16 results use
- * D_jv = bf16 value x beam_scale.  Scratch: 8 bytes per voxel for the call. */
+ * computation; the call does not wait.  Each product w_j D_jv is rounded to
+ * FP32 and summed exactly in 64-bit fixed point scaled to a bound on |dose|,
+ * so the result does not depend on thread order (bit-identical across
+ * calls); relative error at most 2^-24 per term plus one final FP32
+ * rounding.  BF16 results use D_jv = bf16 value x beam_scale.  Scratch: 8
+ * bytes per voxel for the call. */
 dsc_status dsc_dose(dsc_result* res, const float* w_dev, float* dose_dev, void* stream);
 /* out[j] = sum_v D_jv g[v] for every row j (the product with the transpose
  * of Eq. 1's operator, which an optimiser's gradient needs).  g_dev: ncols

@@ -7,12 +7,11 @@
 // Both read one instance's CSR where the computation left it (rows = the
 // instance's beamlets, columns = voxel indices).  FP64 arithmetic is slow on
 // this GPU, so no per-entry step uses it.  The dose is a scatter over rows:
-// every product w_j D_jv is formed exactly as an FP32 pair (product and its
-// FMA residual), each part is converted exactly (integer shifts of its
-// mantissa) to 64-bit fixed point at a power-of-two scale chosen from a bound
-// on |dose|, and added with integer atomics, so the sum does not depend on
-// the order the atomics land in (deterministic, within one FP32 rounding of
-// the exact sum of the products).  The transpose product is a gather per
+// every product w_j D_jv is rounded once to FP32, converted exactly (integer
+// shifts of its mantissa) to 64-bit fixed point at a power-of-two scale
+// chosen from a bound on |dose|, and added with integer atomics, so the sum
+// does not depend on the order the atomics land in (deterministic; each term
+// within 2^-24 of its exact product, the sum rounded once to FP32).  The transpose product is a gather per
 // row, one warp per row, compensated FP32 sums per lane reduced in FP64 in
 // a fixed order.
 #include "dsc_internal.h"
@@ -91,8 +90,7 @@ __global__ void __launch_bounds__(kRowThreads) k_dose_scatter(
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (c[u] < 0) continue;
-        const float hi = wj * D[u], lo = fmaf(wj, D[u], -hi);   // w D = hi + lo exactly
-        atomicAdd(acc + c[u], (unsigned long long)(fixed_of(hi, e) + fixed_of(lo, e)));
+        atomicAdd(acc + c[u], (unsigned long long)fixed_of(wj * D[u], e));   // the FP32 product, exactly
       }
     }
   }
