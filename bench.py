@@ -36,6 +36,14 @@ sys.path.insert(0, ROOT)
 # evaluations x 20, inverse square and product 4.
 F_PAIR = 337
 FP32_LANES_PER_SM = 128
+# MUFU operations (rcp.approx, ex2.approx) of one pair in the evaluation
+# kernel's formulation, by lateral profile.  Per profile term one reciprocal
+# 1/s and four tails (X and Z at y1 and y2); a Gaussian tail (erfc) is one
+# reciprocal t = 1/(1 + p y) and one ex2, a Laplace tail one ex2, a logistic
+# tail one ex2 and one reciprocal; one reciprocal 1/t per pair.
+MUFU_PAIR = {0: {"rcp": 16, "ex2": 12}, 1: {"rcp": 4, "ex2": 12}, 2: {"rcp": 16, "ex2": 12}}
+# HBM3e bandwidth of the part as specified (GB/s), next to the measured copy
+HBM_NOMINAL_GBS = 7900.0
 # DRAM bytes (read + write) of the evaluation kernel per candidate pair, from
 # one Nsight Compute capture of the current kernel on the 2-field prostate
 # (27.85 M pairs, 164.3 MB); the full workload's traffic is this times its pairs
@@ -81,15 +89,17 @@ def whole_job_rate(units_per_rank_step: int, steps: int, world: int, seconds: fl
     return world * units_per_rank_step * steps / seconds
 
 
-def oracle_sample(w, stride):
-    """Oracle pairs/s on every `stride`-th row of the workload (all host cores)."""
+def oracle_sample(w, stride, nthreads=0):
+    """Oracle pairs/s on every `stride`-th row of the workload (all host
+    cores, or `nthreads` of them)."""
     import numpy as np
     from oracle import oracle as O
     rows = np.arange(0, w.nrows, stride, dtype=np.int64)
     t = time.perf_counter()
-    r = O.compute_workload(w, rows=rows)
+    r = O.compute_workload(w, rows=rows, nthreads=nthreads)
     dt = time.perf_counter() - t
-    return {"value": r.pairs / dt, "unit": "pairs/s", "cores": O.max_threads(), "kind": "oracle",
+    cores = nthreads if nthreads > 0 else O.max_threads()
+    return {"value": r.pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
             "sample": f"{rows.size} of {w.nrows} rows (every {stride}th), {r.pairs} pairs, {dt:.2f} s",
             "seconds": dt, "pairs": int(r.pairs)}
 
@@ -252,6 +262,8 @@ def run_ours(args):
         from oracle import oracle as O
         O.build()
         cpu = oracle_sample(w, args.cpu_sample_stride)
+        cpu1 = oracle_sample(w, args.cpu_sample_stride * 4, nthreads=1)
+        cpu["single_core"] = {k: cpu1[k] for k in ("value", "unit", "cores", "sample")}
 
     g = dsc.dsc_create_geometry(w.grid, w.density, False, w.model, sp)
     for b in w.beams:
@@ -286,6 +298,8 @@ def run_ours(args):
             dsc.dsc_result_wait(r)
             v = dsc.dsc_get_csr(r, False)
             pairs, nnz, nrows, nbeams = int(v.pairs), int(v.nnz), int(v.nrows), int(v.nbeams)
+            if k == 0:
+                table_entries = int(dsc.dsc_get_beamlets(r, nrows)[:, 15].sum())
             dsc.dsc_release_result(r)
         # ---- timed region: K steps, device time ----
         stream.synchronize()
@@ -345,6 +359,11 @@ def run_ours(args):
         e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
         wall_s = max_over_ranks(time.perf_counter() - t0, dev)
 
+        # ---- the ALU denominators measured on this GPU (outside the timed region) ----
+        pclk = Clocks(gpu_id(props, local if world > 1 else 0))
+        alu = dsc.dsc_measure_alu_peaks(200.0, sp)
+        alu["clocks"] = pclk.stop()
+
     dsc.dsc_destroy_geometry(g)
     if rank != 0:
         return
@@ -362,6 +381,22 @@ def run_ours(args):
     stage_ms = {k: round(statistics.mean(s[k] for s in stages), 4) for k in stages[0]}
     h2d = int(host_rho.numel() * 4)
     d2h = int((nrows + 1) * 8 + nnz * 4 + nnz * vsize + nbeams * 4)
+    sms = props.multi_processor_count
+    # MUFU bound of the evaluation kernel: the time its reciprocals and
+    # exponentials take at the measured rates, as a share of its time
+    m_pair = MUFU_PAIR[int(w.model.profile)]
+    mufu_ms = 1e3 * pairs * (m_pair["rcp"] / (alu["rcp_tops"] * 1e12) + m_pair["ex2"] / (alu["ex2_tops"] * 1e12))
+    fp32_ms = 1e3 * F_PAIR * pairs / (alu["fp32_tflops"] * 1e12)
+    # HBM bound of the step: the bytes the path must move (CSR out, density
+    # in once, depth tables written and read back) over the step's time
+    step_bytes = nnz * (4 + vsize) + 8 * (nrows + 1) + 4 * nbeams + h2d + 2 * 4 * table_entries
+    step_gbs = step_bytes / (ms / 1e3) / 1e9
+    eval_gbs = KEVAL_DRAM_BYTES_PER_PAIR * pairs / (eval_ms / 1e3) / 1e9
+    hbm_meas = None
+    try:
+        hbm_meas = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
     out = {
         "metric": "voxel-beamlet pairs/s",
         "value": value,
@@ -394,12 +429,33 @@ def run_ours(args):
                      "traffic_basis": "ncu dram bytes per pair of k_eval on prostate_256_2f, times pairs",
                      "kernel": "k_eval",
                      "flop_per_pair": F_PAIR, "eval_ms": eval_ms,
-                     "peak_basis": f"FP32 FMA 2x{FP32_LANES_PER_SM} lanes x {props.multi_processor_count} SMs "
-                                   f"x {peak_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"},
+                     "peak_basis": f"FP32 FMA 2x{FP32_LANES_PER_SM} lanes x {sms} SMs "
+                                   f"x {peak_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+                     "measured_peak": alu["fp32_tflops"], "frac_of_measured": achieved / alu["fp32_tflops"],
+                     "fp32_bound_ms_measured": fp32_ms,
+                     "mufu": {"ops_per_pair": m_pair, "bound_ms": mufu_ms, "frac": mufu_ms / eval_ms,
+                              "rates_tops": {"rcp": alu["rcp_tops"], "ex2": alu["ex2_tops"]},
+                              "results_per_clk_sm": {
+                                  "rcp": alu["rcp_tops"] * 1e12 / (sms * alu["clocks"]["sm_mhz"] * 1e6)
+                                  if alu.get("clocks") else None,
+                                  "ex2": alu["ex2_tops"] * 1e12 / (sms * alu["clocks"]["sm_mhz"] * 1e6)
+                                  if alu.get("clocks") else None},
+                              "basis": "pairs x (rcp / rcp rate + ex2 / ex2 rate), rates from the library's "
+                                       "measured MUFU loops; frac = that time / k_eval time"},
+                     "hbm": {"step_bytes": step_bytes, "step_achieved": step_gbs, "unit": "GB/s",
+                             "peak_measured": hbm_meas, "peak_nominal": HBM_NOMINAL_GBS,
+                             "step_frac_of_measured": step_gbs / hbm_meas if hbm_meas else None,
+                             "step_frac_of_nominal": step_gbs / HBM_NOMINAL_GBS,
+                             "k_eval_achieved": eval_gbs,
+                             "k_eval_frac_of_measured": eval_gbs / hbm_meas if hbm_meas else None,
+                             "k_eval_frac_of_nominal": eval_gbs / HBM_NOMINAL_GBS,
+                             "step_bytes_basis": "CSR (col + value + row pointers + beam scales) + density once "
+                                                 "+ depth tables written and read"},
+                     "measured_alu": alu},
         "clocks": clocks,
     }
     if cpu is not None:
-        out["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        out["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "single_core")}
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

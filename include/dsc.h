@@ -241,6 +241,18 @@ dsc_status dsc_dose(dsc_result* res, const float* w_dev, float* dose_dev, void* 
  * order, queued on `stream`. */
 dsc_status dsc_beamlet_dot(dsc_result* res, const float* g_dev, float* out_dev, void* stream);
 
+/* --- arithmetic rates of this GPU ---------------------------------------- */
+/* The denominators of the evaluation kernel's roofline, measured: every SM
+ * filled with independent dependency chains of one operation, timed with CUDA
+ * events on `stream` over one launch of about ms_per_loop milliseconds (1 to
+ * 2000) after an untimed one, so that the clocks settle where a long run
+ * holds them.  out[0] = FP32 TFLOP/s of fused multiply-adds (2 flops each),
+ * out[1] = ex2.approx.ftz.f32 and out[2] = rcp.approx.ftz.f32 in 10^12
+ * operations/s (the MUFU unit), out[3..5] = device ms of the three timed
+ * launches; n >= 6.  Waits for the stream.  DSC_E_INVAL for a short `out` or
+ * ms_per_loop out of range. */
+dsc_status dsc_measure_alu_peaks(double ms_per_loop, double* out, int32_t n, void* stream);
+
 /* --- stage inspection (per-step parity and timing) ---------------------- */
 /* Per row 16 doubles: S[3] e[3] x'[3] z'[3] tA tB hit n_table. */
 dsc_status dsc_get_beamlets(dsc_result* res, double* out, int64_t cap_rows);

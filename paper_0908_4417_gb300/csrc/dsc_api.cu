@@ -329,6 +329,7 @@ extern "C" const char* dsc_status_str(dsc_status s) {
 }
 extern "C" const char* dsc_last_error(void) { return g_err.c_str(); }
 void dsc::set_error(const char* msg) { g_err = msg; }
+void dsc::count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 extern "C" int32_t dsc_abi_version(void) { return DSC_ABI_VERSION; }
 extern "C" int64_t dsc_launch_count(void) { return g_launches.load(); }
 

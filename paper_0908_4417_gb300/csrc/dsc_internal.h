@@ -137,10 +137,12 @@ struct CompactParams {
   const OutSlot* slot;
 };
 
-// sets the text dsc_last_error() returns on the calling thread
 // process-wide work decomposition (dsc_set_tuning): candidates per work item
 // and evaluation CTAs per SM (0 = occupancy limit)
 void current_tuning(int* target_cand, int* eval_blocks_per_sm);
+// sets the text dsc_last_error() returns on the calling thread
 void set_error(const char* msg);
+// adds n kernel launches to the process-wide count dsc_launch_count() returns
+void count_launches(long long n);
 
 }  // namespace dsc

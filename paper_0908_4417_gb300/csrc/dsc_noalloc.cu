@@ -72,6 +72,7 @@ static dsc_status na_fail(dsc_status s, const char* fmt, ...) {
   } while (0)
 #define NA_LAUNCH()                                                                                     \
   do {                                                                                                  \
+    dsc::count_launches(1);                                                                             \
     cudaError_t e_ = cudaGetLastError();                                                                \
     if (e_ != cudaSuccess) return na_fail(DSC_E_CUDA, "launch: %s", cudaGetErrorString(e_));          \
   } while (0)

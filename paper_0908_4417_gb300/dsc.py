@@ -34,6 +34,7 @@ EXPORTS = [
     "dsc_release_result", "dsc_get_beamlets", "dsc_get_depth_tables", "dsc_get_row_stats", "dsc_get_stage_times",
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
     "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune", "dsc_dose", "dsc_beamlet_dot",
+    "dsc_measure_alu_peaks",
 ]
 
 
@@ -120,6 +121,7 @@ def lib():
             "dsc_get_tuning": (C.c_int, [C.POINTER(Tuning)]),
             "dsc_autotune": (C.c_int, [C.POINTER(P), I32, C.POINTER(ComputeOpts), P, I32, C.POINTER(Tuning),
                                        C.POINTER(C.c_float)]),
+            "dsc_measure_alu_peaks": (C.c_int, [C.c_double, C.POINTER(C.c_double), I32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -251,6 +253,15 @@ def dsc_dose(res, w_ptr: int, dose_ptr: int, stream=0):
 def dsc_beamlet_dot(res, g_ptr: int, out_ptr: int, stream=0):
     """out (nrows floats) = D g on the device; pointers are device addresses."""
     _check(lib().dsc_beamlet_dot(res, g_ptr, out_ptr, stream))
+
+
+def dsc_measure_alu_peaks(ms_per_loop: float = 200.0, stream=0) -> dict:
+    """FP32 FMA and MUFU (ex2, rcp) rates of the current GPU, measured by the
+    library's own loops; TFLOP/s and 10^12 operations/s, with device ms."""
+    out = (C.c_double * 6)()
+    _check(lib().dsc_measure_alu_peaks(float(ms_per_loop), out, 6, stream))
+    return {"fp32_tflops": out[0], "ex2_tops": out[1], "rcp_tops": out[2],
+            "ms": {"fma": out[3], "ex2": out[4], "rcp": out[5]}}
 
 
 def dsc_result_wait(res):

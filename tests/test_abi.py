@@ -44,6 +44,12 @@ def test_null_arguments_are_rejected(lib):
     assert lib.dsc_create_geometry(None, None, 0, None, None, C.byref(out)) == 1
     assert b"null" in lib.dsc_last_error()
     assert lib.dsc_compute_dij(None, None, None, C.byref(out)) == 1
+    peaks = (C.c_double * 6)()
+    assert lib.dsc_measure_alu_peaks(200.0, None, 6, None) == 1
+    assert lib.dsc_measure_alu_peaks(200.0, peaks, 5, None) == 1
+    assert lib.dsc_measure_alu_peaks(0.5, peaks, 6, None) == 1
+    assert b"ms_per_loop" in lib.dsc_last_error()
+    assert lib.dsc_measure_alu_peaks(float("nan"), peaks, 6, None) == 1
 
 
 def test_struct_layouts_match_header():

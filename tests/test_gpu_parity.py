@@ -495,3 +495,23 @@ def test_server_budget_rejects_and_throttles(dsc):
     assert e.value.status == 3
     dsc.dsc_server_destroy(srv)
     dsc.dsc_destroy_geometry(g)
+
+
+def test_alu_peaks_are_plausible(dsc):
+    """The FP32 and MUFU loops report rates between a fifth of and just above
+    the part's nominal figures (lanes or MUFU results x SMs x maximum clock;
+    16 or 32 MUFU results per clock per SM, ex2 running at the double rate on
+    this part), and the loops take the time they were sized for."""
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    n0 = dsc.dsc_launch_count()
+    r = dsc.dsc_measure_alu_peaks(20.0, torch.cuda.current_stream().cuda_stream)
+    launches = dsc.dsc_launch_count() - n0
+    assert 3 * 3 <= launches <= 3 * 10         # per loop 1 to 8 probes, one untimed and one timed launch
+    fp32_nominal = 2 * 128 * sms * 2.07e9 / 1e12
+    mufu_nominal = 16 * sms * 2.07e9 / 1e12
+    assert 0.2 * fp32_nominal < r["fp32_tflops"] < 1.1 * fp32_nominal, r
+    for k in ("ex2_tops", "rcp_tops"):
+        assert 0.2 * mufu_nominal < r[k] < 1.1 * 2 * mufu_nominal, r
+    for ms in r["ms"].values():
+        assert 5.0 < ms < 200.0, r
