@@ -408,6 +408,38 @@ def test_batch_equals_single_and_oracle(dsc):
         dsc.dsc_destroy_geometry(g)
 
 
+def test_batch_past_32_bit_offsets(dsc):
+    """The largest launch: 36 copies of the 9-field prostate in one batch,
+    4.4e9 candidates and 2.6e9 kept entries (about 57 GB of device memory),
+    so the last instance's candidates sit past 2^32 and its kept entries past
+    2^31 in the launch's flat arrays.  Its CSR equals the first instance's and
+    a single computation's bit for bit, and sampled rows match the oracle."""
+    w = P.prostate_256()
+    n = 36
+    gs = [dsc.geometry_from_workload(w) for _ in range(n)]
+    opts = dsc.compute_opts(1e-3, 0, 0.5)
+    single = dsc.dsc_compute_dij(gs[0], opts)
+    ref = dsc.HostCSR(single)
+    dsc.dsc_release_result(single)
+    batch = dsc.dsc_compute_dij_batch(gs, opts)
+    try:
+        total_pairs = sum(int(dsc.dsc_get_csr(r, False).pairs) for r in batch)
+        total_nnz = sum(int(dsc.dsc_get_csr(r, False).nnz) for r in batch)
+        assert total_pairs > 2 ** 32 and total_nnz > 2 ** 31, (total_pairs, total_nnz)
+        for k in (0, n - 1):
+            c = dsc.HostCSR(batch[k])
+            assert c.pairs == ref.pairs and c.nnz == ref.nnz
+            assert np.array_equal(c.row_ptr, ref.row_ptr) and np.array_equal(c.col, ref.col)
+            assert np.array_equal(c.val, ref.val)
+        rows = np.array([0, 700, 1151, 1600, 2303])
+        compare(gpu_rows(c, rows), O.compute_workload(w, rows=rows), TOL)
+    finally:
+        for r in batch:
+            dsc.dsc_release_result(r)
+        for g in gs:
+            dsc.dsc_destroy_geometry(g)
+
+
 def test_tile_shapes_are_bit_identical_and_autotune(dsc):
     """The work decomposition (candidates per item, evaluation CTAs per SM)
     changes only the time: every shape gives the same CSR bit for bit; the
