@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 
 # FP32 operations of one voxel-beamlet pair as the model defines it (FMA = 2):
 # geometry 20, depth 7, beam-model table 15, three erf-pair terms 51 + 12 erf
-# evaluations x 20, inverse square and product 4.
-F_PAIR = 337
+# evaluations x 18 (degree-7 erfc), inverse square and product 4.
+F_PAIR = 313
 FP32_LANES_PER_SM = 128
 # MUFU operations (rcp.approx, ex2.approx) of one pair in the evaluation
 # kernel's formulation, by lateral profile.  Per profile term one reciprocal
@@ -46,8 +46,8 @@ MUFU_PAIR = {0: {"rcp": 16, "ex2": 12}, 1: {"rcp": 4, "ex2": 12}, 2: {"rcp": 16,
 HBM_NOMINAL_GBS = 7900.0
 # DRAM bytes (read + write) of the evaluation kernel per candidate pair, from
 # one Nsight Compute capture of the current kernel on the 2-field prostate
-# (27.85 M pairs, 164.3 MB); the full workload's traffic is this times its pairs
-KEVAL_DRAM_BYTES_PER_PAIR = 5.900
+# (27.85 M pairs, 163.7 MB); the full workload's traffic is this times its pairs
+KEVAL_DRAM_BYTES_PER_PAIR = 5.877
 
 
 def parse():
@@ -382,21 +382,23 @@ def run_ours(args):
     h2d = int(host_rho.numel() * 4)
     d2h = int((nrows + 1) * 8 + nnz * 4 + nnz * vsize + nbeams * 4)
     sms = props.multi_processor_count
-    # MUFU bound of the evaluation kernel: the time its reciprocals and
-    # exponentials take at the measured rates, as a share of its time
-    m_pair = MUFU_PAIR[int(w.model.profile)]
-    mufu_ms = 1e3 * pairs * (m_pair["rcp"] / (alu["rcp_tops"] * 1e12) + m_pair["ex2"] / (alu["ex2_tops"] * 1e12))
-    fp32_ms = 1e3 * F_PAIR * pairs / (alu["fp32_tflops"] * 1e12)
-    # HBM bound of the step: the bytes the path must move (CSR out, density
-    # in once, depth tables written and read back) over the step's time
-    step_bytes = nnz * (4 + vsize) + 8 * (nrows + 1) + 4 * nbeams + h2d + 2 * 4 * table_entries
-    step_gbs = step_bytes / (ms / 1e3) / 1e9
-    eval_gbs = KEVAL_DRAM_BYTES_PER_PAIR * pairs / (eval_ms / 1e3) / 1e9
     hbm_meas = None
     try:
         hbm_meas = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except (OSError, ValueError, KeyError):
         pass
+    # MUFU bound of the evaluation kernel: the time its reciprocals and
+    # exponentials take at the measured rates, as a share of its time
+    m_pair = MUFU_PAIR[int(w.model.profile)]
+    mufu_ms = 1e3 * pairs * (m_pair["rcp"] / (alu["rcp_tops"] * 1e12) + m_pair["ex2"] / (alu["ex2_tops"] * 1e12))
+    fp32_ms = 1e3 * F_PAIR * pairs / (alu["fp32_tflops"] * 1e12)
+    hbm_ms = 1e3 * KEVAL_DRAM_BYTES_PER_PAIR * pairs / (hbm_meas * 1e9) if hbm_meas else 0.0
+    binding = max((fp32_ms, "fp32"), (mufu_ms, "mufu"), (hbm_ms, "hbm"))
+    # HBM bound of the step: the bytes the path must move (CSR out, density
+    # in once, depth tables written and read back) over the step's time
+    step_bytes = nnz * (4 + vsize) + 8 * (nrows + 1) + 4 * nbeams + h2d + 2 * 4 * table_entries
+    step_gbs = step_bytes / (ms / 1e3) / 1e9
+    eval_gbs = KEVAL_DRAM_BYTES_PER_PAIR * pairs / (eval_ms / 1e3) / 1e9
     out = {
         "metric": "voxel-beamlet pairs/s",
         "value": value,
@@ -433,6 +435,9 @@ def run_ours(args):
                                    f"x {peak_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
                      "measured_peak": alu["fp32_tflops"], "frac_of_measured": achieved / alu["fp32_tflops"],
                      "fp32_bound_ms_measured": fp32_ms,
+                     "binding": {"resource": binding[1], "bound_ms": binding[0], "frac": binding[0] / eval_ms,
+                                 "basis": "the largest of the FP32, MUFU and DRAM times of k_eval's work at the "
+                                          "measured rates, over its measured time"},
                      "mufu": {"ops_per_pair": m_pair, "bound_ms": mufu_ms, "frac": mufu_ms / eval_ms,
                               "rates_tops": {"rcp": alu["rcp_tops"], "ex2": alu["ex2_tops"]},
                               "results_per_clk_sm": {

@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
 // erfc(u) for u >= 0, given v = u sqrt(log2 e):  t exp(-u^2) P(t) with
 // t = 1/(1 + p u) (coefficients from fit_erfc.py) and exp(-u^2) = 2^(-v^2).
 // Rounding v^2 to FP32 costs a relative error of about 4e-8 v^2 in the
-// exponential, below the fit's own 3.3e-7 where the terms matter.
+// exponential, below the fit's own 4.6e-7 where the terms matter.
 // Two arguments at once in packed FP32x2 arithmetic: one instruction per
 // pair of operations, each half rounded as the scalar fmaf / mul.
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
