@@ -42,7 +42,7 @@ __global__ void k_eval(EvalParams);
 __global__ void k_beam_scale(const DBeam*, int, const unsigned*, const OutSlot*);
 __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_tile_prep(CompactParams);
-__global__ void k_lut_pairs(const float4*, int, float4*);
+__global__ void k_lut_pairs(const float4*, int, int, float4*);
 __global__ void k_dose_scale(const unsigned*, const float*, int, int*);
 __global__ void k_dose_scatter(const long long*, const long long*, const int*, const void*, int, const DRow*, int,
                                const float*, const float*, int, const int*, unsigned long long*);
@@ -406,7 +406,7 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
   if (st != DSC_OK) { dsc_destroy_geometry(g); return st; }
   cudaError_t e = cudaMemcpyAsync(rows, model->table4, sizeof(float4) * model->n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(rows, model->n, g->d_lut);
+    k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(rows, model->n, model->profile, g->d_lut);
     e = cudaGetLastError();
   }
   cudaError_t ef = cudaFreeAsync(rows, s);

@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(kSiddonThreads) k_trilinear_table(const DInst*
 // ---------------------------------------------------------------------------
 // x-lines of a work item
 // ---------------------------------------------------------------------------
+constexpr int kTabSmem = 1024;   // depth-table entries a work item stages in shared memory
 struct LineSm {
   float4 sx[kMaxLinesPerItem];        // t, x' hi, x' lo, z' hi at ix = 0
   float4 zc[kMaxLinesPerItem];        // z' lo, first ix (int bits), nx (iy + ny iz) (int bits), unused
@@ -458,6 +459,7 @@ struct LineSm {
   int off[kMaxLinesPerItem + 1];
   int wscan[kEvalThreads / 32];
   unsigned short map[kWindow];
+  float tab[kTabSmem];                // the row's depth table, when it fits
   long long item;
   int row;
   int nl;
@@ -757,18 +759,20 @@ struct RowConst {
   long long dsf;         // slope of s per ix, fixed point (units of h 2^-32)
   float tx;              // slope of t per ix
   float Xxh, Xxl, Zxh, Zxl;
-  float sad, a_sad, b_sad;
+  float a_sad, b_sad;
   int n_table;
   const float* tab;      // the row's depth table
   const float4* lut;     // beam-model table
   float lut_scale, lut_last;
-  float c1q[3], c2h[3], c2hn[3];   // c1/4, c2/2, -c2/2
+  float c1q[3], c2h[3], c2hn[3];   // c1/4 SAD^2, c2/2, -c2/2
   float cutoff_k;
 };
 
-// D for candidate ix of a line; returns -1 outside the SIGMA cutoff
-template <int PROF>
-__device__ __forceinline__ float eval_pair(const RowConst& C, int ix, float4 sx, float zlo, long long sf, int mode) {
+// D for candidate ix of a line; returns -1 outside the SIGMA cutoff.  TS: the
+// row's depth table is staged in shared memory at stab
+template <int PROF, bool TS>
+__device__ __forceinline__ float eval_pair(const RowConst& C, int ix, float4 sx, float zlo, long long sf, int mode,
+                                           const float* stab) {
   // t, x', z' of voxel ix on the line (compensated FP32 for x', z')
   const float fi = (float)ix;
   const float t = fmaf(fi, C.tx, sx.x);
@@ -785,10 +789,11 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, int ix, float4 sx,
   const bool past = cell >= C.n_table - 1;
   const int k = neg ? 0 : (past ? C.n_table - 2 : cell);
   const float f = neg ? 0.0f : __uint_as_float(((unsigned)s >> 9) | 0x3f800000u) - 1.0f;   // low word / 2^32
-  const float d0 = __ldg(C.tab + k), d1 = __ldg(C.tab + k + 1);
+  const float d0 = TS ? stab[k] : __ldg(C.tab + k), d1 = TS ? stab[k + 1] : __ldg(C.tab + k + 1);
   const float d = past ? d1 : fmaf(f, d1 - d0, d0);
 
-  // beam-model table: T(d), c3_1..3(d); past the end, the last row
+  // beam-model table: T(d), c3_1..3(d) / K (K = Prof<PROF>::K, folded in
+  // when the table was built); past the end, the last row
   float g = fmaxf(d * C.lut_scale, 0.0f);   // also maps a NaN depth to 0
   float kl = fminf(floorf(g), C.lut_last - 1.0f);
   float w = fminf(g - kl, 1.0f);
@@ -799,26 +804,26 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, int ix, float4 sx,
 
   const float2 abt = __fmul2_rn(make_float2(C.a_sad, C.b_sad), f2(t));   // (a_t, b_t)
   const float2 axz = make_float2(fabsf(xp), fabsf(zp));
+  constexpr float kK = Prof<PROF>::K;
   if (mode == 1) {
-    float lim = C.cutoff_k * Pxy.y;
+    float lim = (C.cutoff_k * kK) * Pxy.y;   // cutoff_k c3_1
     if (axz.x > fmaf(0.5f, abt.x, lim) || axz.y > fmaf(0.5f, abt.y, lim)) return -1.0f;
   }
   // Eq. 3 (or another profile): three pair products, arguments scaled by
-  // Prof<PROF>::K / c3 (for Eq. 3: 1/(sqrt(2) c3) * sqrt(log2 e))
-  constexpr float kSqrtHalfL = Prof<PROF>::K;
-  const float c3[3] = {Pxy.y, Pzw.x, Pzw.y};
+  // K / c3 (for Eq. 3: 1/(sqrt(2) c3) * sqrt(log2 e)), the reciprocal of the
+  // table's c3 / K
+  const float c3k[3] = {Pxy.y, Pzw.x, Pzw.y};
   float F = 0.0f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const float inv_s = kSqrtHalfL * rcp_approx(c3[i]);
+    const float inv_s = rcp_approx(c3k[i]);
     const float2 XZ = erf_pair2<PROF>(C.c2h[i], C.c2hn[i], abt, axz, inv_s);
     F = fmaf(C.c1q[i] * XZ.x, XZ.y, F);
   }
-  // Eq. 2 with A = T(d) (SAD/t)^2; 1/t with one Newton step
-  float it = rcp_approx(t);
-  it = fmaf(it, fmaf(-t, it, 1.0f), it);
-  float q = C.sad * it;
-  return Pxy.x * (q * q) * F;
+  // Eq. 2 with A = T(d) (SAD/t)^2, SAD^2 carried in c1q; rcp.approx is
+  // within an ulp of 1/t
+  const float it = rcp_approx(t);
+  return Pxy.x * (it * it) * F;
 }
 
 __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const DInst& G, const float* tab) {
@@ -826,7 +831,6 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
   C.tx = R.Ss[0].hi;
   C.Xxh = R.Xs[0].hi; C.Xxl = R.Xs[0].lo;
   C.Zxh = R.Zs[0].hi; C.Zxl = R.Zs[0].lo;
-  C.sad = R.sad;
   C.a_sad = R.a_sad;
   C.b_sad = R.b_sad;
   C.n_table = R.n_table;
@@ -834,12 +838,14 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
   C.lut = G.lut;
   C.lut_scale = G.lut_scale;
   C.lut_last = (float)(G.n_lut - 1);
-  for (int i = 0; i < 3; ++i) { C.c1q[i] = G.c1q[i]; C.c2h[i] = G.c2h[i]; C.c2hn[i] = -G.c2h[i]; }
+  const float sad2 = R.sad * R.sad;
+  for (int i = 0; i < 3; ++i) { C.c1q[i] = G.c1q[i] * sad2; C.c2h[i] = G.c2h[i]; C.c2hn[i] = -G.c2h[i]; }
   C.cutoff_k = G.cutoff_k;
 }
 
-// the candidates [w0, w0 + wl) of an item's window, profile PROF (block-uniform)
-template <int PROF>
+// the candidates [w0, w0 + wl) of an item's window, profile PROF (block-uniform);
+// TS: the depth table is in sm.tab
+template <int PROF, bool TS>
 __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm, int w0, int wl, float* out,
                                             int* outc, int mode, float& vmax, int& valid) {
   // two candidates per thread per pass: independent chains to interleave
@@ -853,8 +859,8 @@ __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm,
     float4 zc = sm.zc[li], zcb = sm.zc[lb];
     int ix = __float_as_int(zc.y) + (w0 + j - sm.off[li]);
     int ixb = __float_as_int(zcb.y) + (w0 + jb - sm.off[lb]);
-    float D = eval_pair<PROF>(C, ix, sx, zc.x, sm.sf[li], mode);
-    float Db = eval_pair<PROF>(C, ixb, sxb, zcb.x, sm.sf[lb], mode);
+    float D = eval_pair<PROF, TS>(C, ix, sx, zc.x, sm.sf[li], mode, sm.tab);
+    float Db = eval_pair<PROF, TS>(C, ixb, sxb, zcb.x, sm.sf[lb], mode, sm.tab);
     out[w0 + j] = D;
     outc[w0 + j] = __float_as_int(zc.z) + ix;
     vmax = fmaxf(vmax, D);
@@ -892,6 +898,12 @@ __global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
                           (int)(p.item_off[item + 1] - a_off));   // never past the counted range
     RowConst C;
     load_row_const(C, R, G, p.tables + (size_t)row * p.table_stride);
+    // the row's depth table into shared memory when it fits (block-uniform);
+    // the previous item's readers finished at its closing barrier, and this
+    // item's first reader comes after the barrier in item_map
+    const bool ts = R.n_table <= kTabSmem;
+    if (ts)
+      for (int k = threadIdx.x; k < R.n_table; k += kEvalThreads) sm.tab[k] = C.tab[k];
     float* out = p.vals + a_off;
     int* outc = p.cols + a_off;
     float vmax = 0.0f;
@@ -899,10 +911,18 @@ __global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
     for (int w0 = 0; w0 < total; w0 += kWindow) {
       int wl = min(kWindow, total - w0);
       item_map(sm, w0, wl);
-      switch (G.profile) {
-        case 1: eval_window<1>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
-        case 2: eval_window<2>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
-        default: eval_window<0>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+      if (ts) {
+        switch (G.profile) {
+          case 1: eval_window<1, true>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+          case 2: eval_window<2, true>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+          default: eval_window<0, true>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+        }
+      } else {
+        switch (G.profile) {
+          case 1: eval_window<1, false>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+          case 2: eval_window<2, false>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+          default: eval_window<0, false>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+        }
       }
       __syncthreads();
     }
@@ -923,13 +943,18 @@ __global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
 // ---------------------------------------------------------------------------
 // beam-model table as the evaluation reads it: entry k = {row k, row k+1 -
 // row k} (the FP32 difference the linear interpolation forms; zero for the
-// last row), so one interpolation is one FMA per column
+// last row), so one interpolation is one FMA per column.  The three c3
+// columns are divided by the profile's argument scale K first (one rounding),
+// so the evaluation's 1/s is one reciprocal.
 // ---------------------------------------------------------------------------
-__global__ void k_lut_pairs(const float4* __restrict__ rows, int n, float4* __restrict__ pairs) {
+__global__ void k_lut_pairs(const float4* __restrict__ rows, int n, int profile, float4* __restrict__ pairs) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const float4 a = rows[k];
-  const float4 b = k + 1 < n ? rows[k + 1] : a;
+  const float ik = profile == 1 ? 1.0f / Prof<1>::K : (profile == 2 ? 1.0f / Prof<2>::K : 1.0f / Prof<0>::K);
+  float4 a = rows[k];
+  float4 b = k + 1 < n ? rows[k + 1] : a;
+  a = make_float4(a.x, a.y * ik, a.z * ik, a.w * ik);
+  b = make_float4(b.x, b.y * ik, b.z * ik, b.w * ik);
   pairs[2 * k] = a;
   pairs[2 * k + 1] = make_float4(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y), __fsub_rn(b.z, a.z), __fsub_rn(b.w, a.w));
 }

@@ -33,7 +33,7 @@ __global__ void k_tile_map(const long long*, const long long*, long long, long l
 __global__ void k_eval(EvalParams);
 __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_tile_prep(CompactParams);
-__global__ void k_lut_pairs(const float4*, int, float4*);
+__global__ void k_lut_pairs(const float4*, int, int, float4*);
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
@@ -225,7 +225,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
                    kNoAllocBytes, nrows);
 
   NA_CU(cudaMemcpyAsync(d_lut_rows, model->table4, sizeof(float4) * model->n, cudaMemcpyHostToDevice, s));
-  k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(d_lut_rows, model->n, d_lut);
+  k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(d_lut_rows, model->n, model->profile, d_lut);
   NA_LAUNCH();
   I.lut = d_lut;
   NA_CU(cudaMemcpyAsync(d_inst, &I, sizeof(DInst), cudaMemcpyHostToDevice, s));
