@@ -31,10 +31,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP32 operations of one voxel-beamlet pair as the model defines it (FMA = 2):
-# geometry 20, depth 7, beam-model table 15, three erf-pair terms 51 + 12 erf
-# evaluations x 18 (degree-7 erfc), inverse square and product 4.
-F_PAIR = 313
+# FP32 operations of one voxel-beamlet pair as the evaluation kernel forms it
+# (FMA = 2): geometry 20, depth 7, beam-model table 15, three erf-pair terms
+# 48 + 12 erf evaluations x 18 (degree-7 erfc), inverse square and product 3.
+F_PAIR = 309
 FP32_LANES_PER_SM = 128
 # MUFU operations (rcp.approx, ex2.approx) of one pair in the evaluation
 # kernel's formulation, by lateral profile.  Per profile term one reciprocal
@@ -46,8 +46,8 @@ MUFU_PAIR = {0: {"rcp": 16, "ex2": 12}, 1: {"rcp": 4, "ex2": 12}, 2: {"rcp": 16,
 HBM_NOMINAL_GBS = 7900.0
 # DRAM bytes (read + write) of the evaluation kernel per candidate pair, from
 # one Nsight Compute capture of the current kernel on the 2-field prostate
-# (27.85 M pairs, 163.7 MB); the full workload's traffic is this times its pairs
-KEVAL_DRAM_BYTES_PER_PAIR = 5.877
+# (27.85 M pairs, 164.0 MB); the full workload's traffic is this times its pairs
+KEVAL_DRAM_BYTES_PER_PAIR = 5.887
 
 
 def parse():
