@@ -254,6 +254,16 @@ dsc_status dsc_beamlet_dot(dsc_result* res, const float* g_dev, float* out_dev, 
 dsc_status dsc_measure_alu_peaks(double ms_per_loop, double* out, int32_t n, void* stream);
 
 /* --- stage inspection (per-step parity and timing) ---------------------- */
+/* The lateral-profile tail T(y) = 2 G(y) of Eq. 3 (profile DSC_PROFILE_ERF:
+ * erfc(y / sqrt 2)) or of the other profiles (DSC_PROFILE_LAPLACE:
+ * exp(-sqrt 2 y); DSC_PROFILE_LOGISTIC: 2 q / (1 + q), q = exp(-pi y / sqrt 3)),
+ * y >= 0 in units of the spread c3, computed with the evaluation kernel's own
+ * primitives and constants, and the same tail from CUDA's erfcf / expf for
+ * comparison.  y_dev, ours_dev, cuda_dev: n floats each, device pointers;
+ * queued on `stream`.  DSC_E_INVAL for an unknown profile or a null pointer
+ * with n > 0. */
+dsc_status dsc_probe_tail(int32_t profile, const float* y_dev, int64_t n, float* ours_dev, float* cuda_dev,
+                          void* stream);
 /* Per row 16 doubles: S[3] e[3] x'[3] z'[3] tA tB hit n_table. */
 dsc_status dsc_get_beamlets(dsc_result* res, double* out, int64_t cap_rows);
 /* Depth tables, row-major [nrows][n_max] floats (entries past a row's n_table are 0). */

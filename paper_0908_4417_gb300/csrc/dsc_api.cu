@@ -57,7 +57,7 @@ __global__ void k_scan_partial(const int*, const long long*, long long, long lon
 __global__ void k_scan_blocks(long long*);
 __global__ void k_scan_final(const int*, const long long*, long long, const long long*, long long*);
 __global__ void k_scan_small(const int*, const long long*, long long, long long*);
-__global__ void k_scan_small(const int*, const long long*, long long, long long*);
+__global__ void k_tail_probe(int, const float*, long long, float*, float*);
 }  // namespace dsc
 
 using namespace dsc;
@@ -1109,6 +1109,18 @@ extern "C" dsc_status dsc_beamlet_dot(dsc_result* r, const float* g_dev, float* 
   k_beamlet_dot<<<row_blocks_grid(r->nrows), 256, 0, s>>>(q.row_ptr + r->rp_off, q.inst_begin + r->inst, q.col, q.val,
                                                          r->value_dtype, r->plan->d_rows, r->row_base, q.beam_scale,
                                                          g_dev, r->nrows, out_dev);
+  CHECK_LAUNCH();
+  return DSC_OK;
+}
+
+extern "C" dsc_status dsc_probe_tail(int32_t profile, const float* y_dev, int64_t n, float* ours_dev, float* cuda_dev,
+                                     void* stream) {
+  if (profile < 0 || profile > 2) return fail(DSC_E_INVAL, "profile: DSC_PROFILE_ERF, _LAPLACE or _LOGISTIC");
+  if (n < 0 || (n > 0 && (!y_dev || !ours_dev || !cuda_dev))) return fail(DSC_E_INVAL, "null argument or n < 0");
+  if (n == 0) return DSC_OK;
+  const long long threads = (n + 1) / 2;
+  k_tail_probe<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(profile, y_dev, n, ours_dev,
+                                                                                    cuda_dev);
   CHECK_LAUNCH();
   return DSC_OK;
 }

@@ -941,6 +941,45 @@ __global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// the lateral-profile tail T(y), y >= 0 in units of the spread, with the
+// evaluation's own primitives and constants (argument scale K, the fitted
+// erfc, rcp.approx, ex2.approx), two values per thread in packed FP32x2 as
+// erf_pair2 forms them, beside CUDA's own function of the same tail
+// ---------------------------------------------------------------------------
+template <int PROF>
+__device__ __forceinline__ float2 tail2(float2 y) {
+  const float2 v = __fmul2_rn(y, f2(Prof<PROF>::K));
+  float2 tp, e;
+  if (PROF == 0) {
+    constexpr float kPs = kErfcP * kInvSqrtL;
+    erfc_parts(rcp2(__ffma2_rn(f2(kPs), v, f2(1.0f))), v, kErfcC2, tp, e);
+  } else {
+    e = make_float2(ex2_approx(-v.x), ex2_approx(-v.y));
+    tp = PROF == 1 ? f2(1.0f) : rcp2(__ffma2_rn(e, f2(0.5f), f2(0.5f)));
+  }
+  return __fmul2_rn(tp, e);
+}
+
+__global__ void k_tail_probe(int profile, const float* __restrict__ y, long long n, float* __restrict__ ours,
+                             float* __restrict__ cuda_ref) {
+  const long long i = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const float2 yy = make_float2(y[i], i + 1 < n ? y[i + 1] : 0.0f);
+  const float2 r = profile == 1 ? tail2<1>(yy) : (profile == 2 ? tail2<2>(yy) : tail2<0>(yy));
+  for (int h = 0; h < 2 && i + h < n; ++h) {
+    const float a = h ? yy.y : yy.x;
+    ours[i + h] = h ? r.y : r.x;
+    float c;
+    if (profile == 1) c = expf(-1.41421356237309504880f * a);                     // exp(-sqrt 2 y)
+    else if (profile == 2) {
+      const float q = expf(-1.81379936423421785059f * a);                          // exp(-pi y / sqrt 3)
+      c = 2.0f * q / (1.0f + q);
+    } else c = erfcf(0.70710678118654752440f * a);                                 // erfc(y / sqrt 2)
+    cuda_ref[i + h] = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // beam-model table as the evaluation reads it: entry k = {row k, row k+1 -
 // row k} (the FP32 difference the linear interpolation forms; zero for the
 // last row), so one interpolation is one FMA per column.  The three c3

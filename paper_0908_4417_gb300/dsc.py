@@ -34,7 +34,7 @@ EXPORTS = [
     "dsc_release_result", "dsc_get_beamlets", "dsc_get_depth_tables", "dsc_get_row_stats", "dsc_get_stage_times",
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
     "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune", "dsc_dose", "dsc_beamlet_dot",
-    "dsc_measure_alu_peaks",
+    "dsc_measure_alu_peaks", "dsc_probe_tail",
 ]
 
 
@@ -122,6 +122,7 @@ def lib():
             "dsc_autotune": (C.c_int, [C.POINTER(P), I32, C.POINTER(ComputeOpts), P, I32, C.POINTER(Tuning),
                                        C.POINTER(C.c_float)]),
             "dsc_measure_alu_peaks": (C.c_int, [C.c_double, C.POINTER(C.c_double), I32, P]),
+            "dsc_probe_tail": (C.c_int, [I32, P, I64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -262,6 +263,12 @@ def dsc_measure_alu_peaks(ms_per_loop: float = 200.0, stream=0) -> dict:
     _check(lib().dsc_measure_alu_peaks(float(ms_per_loop), out, 6, stream))
     return {"fp32_tflops": out[0], "ex2_tops": out[1], "rcp_tops": out[2],
             "ms": {"fma": out[3], "ex2": out[4], "rcp": out[5]}}
+
+
+def dsc_probe_tail(profile: int, y_ptr: int, n: int, ours_ptr: int, cuda_ptr: int, stream=0):
+    """T(y) as the evaluation computes it, and CUDA's erfcf / expf of the same
+    tail; device pointers to n floats each."""
+    _check(lib().dsc_probe_tail(int(profile), y_ptr, int(n), ours_ptr, cuda_ptr, stream))
 
 
 def dsc_result_wait(res):

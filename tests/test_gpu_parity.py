@@ -547,3 +547,36 @@ def test_alu_peaks_are_plausible(dsc):
         assert 0.2 * mufu_nominal < r[k] < 1.1 * 2 * mufu_nominal, r
     for ms in r["ms"].values():
         assert 5.0 < ms < 200.0, r
+
+
+@pytest.mark.parametrize("profile", [P.PROFILE_ERF, P.PROFILE_LAPLACE, P.PROFILE_LOGISTIC])
+def test_profile_tails_against_fp64_and_cuda(dsc, profile):
+    """The evaluation's lateral-profile tail T(y) (for Eq. 3 the fitted erfc,
+    erfc(y / sqrt 2)) on 600 001 arguments against the FP64 function, next to
+    CUDA's own erfcf / expf of the same argument.  Where T > 1e-30 both stay
+    within 1e-6 + 2e-7 |ln T| relative (the second part: FP32 rounding of the
+    argument, amplified by the exponent), and ours within 1e-6 where T > 0.1."""
+    special = pytest.importorskip("scipy.special")
+    y = np.linspace(0.0, 60.0, 600001).astype(np.float32)
+    yt = torch.from_numpy(y).cuda()
+    ours, cuda = torch.empty_like(yt), torch.empty_like(yt)
+    dsc.dsc_probe_tail(profile, yt.data_ptr(), y.size, ours.data_ptr(), cuda.data_ptr(),
+                       torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    yd = y.astype(np.float64)
+    if profile == P.PROFILE_ERF:
+        truth = special.erfc(yd / math.sqrt(2.0))
+    elif profile == P.PROFILE_LAPLACE:
+        truth = np.exp(-math.sqrt(2.0) * yd)
+    else:
+        q = np.exp(-math.pi / math.sqrt(3.0) * yd)
+        truth = 2.0 * q / (1.0 + q)
+    m = truth > 1e-30
+    bound = 1e-6 + 2e-7 * np.abs(np.log(truth[m]))
+    rel_ours = np.abs(ours.cpu().numpy().astype(np.float64)[m] - truth[m]) / truth[m]
+    rel_cuda = np.abs(cuda.cpu().numpy().astype(np.float64)[m] - truth[m]) / truth[m]
+    assert np.all(rel_cuda <= bound), rel_cuda.max()
+    assert np.all(rel_ours <= bound), (rel_ours.max(), y[m][np.argmax(rel_ours / bound)])
+    near = truth[m] > 0.1
+    assert rel_ours[near].max() < 1e-6
+    print("tail", profile, "ours", rel_ours.max(), rel_ours[near].max(), "cuda", rel_cuda.max(), rel_cuda[near].max())
