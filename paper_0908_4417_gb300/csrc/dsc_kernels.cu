@@ -466,8 +466,8 @@ struct LineSm {
   int total;
 };
 
-// the candidate interval [lo, hi] of one x-line (iy, iz) of row R and its
-// float-float s, x', z' at ix = 0
+// float-float s, x', z' of x-line (iy, iz) of row R at ix = 0 (the
+// evaluation's per-candidate values start from these)
 __device__ __forceinline__ void line_base(const DRow& R, int iy, int iz, ff& s0, ff& x0, ff& z0) {
   float fy = (float)iy, fz = (float)iz;
   s0 = ff_add(ff_add(R.S0, ff_mul_i(R.Ss[1], fy)), ff_mul_i(R.Ss[2], fz));
@@ -475,12 +475,23 @@ __device__ __forceinline__ void line_base(const DRow& R, int iy, int iz, ff& s0,
   z0 = ff_add(ff_add(R.Z0, ff_mul_i(R.Zs[1], fy)), ff_mul_i(R.Zs[2], fz));
 }
 
-// candidate interval [lo, lo + len) of the x-line whose s, x', z' at ix = 0 are given
-__device__ __forceinline__ int line_interval(const DRow& R, int mode, int nx, const ff& s0, const ff& x0, const ff& z0,
-                                             int& lo_out) {
+// t, x', z' of x-line (iy, iz) at ix = 0 in plain FP32: the inputs of its
+// candidate interval.  Their error (about 1e-4 mm) is far inside the 1e-3 mm
+// band around the cutoff that parity leaves open, and the enumeration count
+// and the evaluation both take the interval from these, so they agree exactly.
+__device__ __forceinline__ void line_base32(const DRow& R, int iy, int iz, float& T0, float& X0, float& Z0) {
+  const float fy = (float)iy, fz = (float)iz;
+  T0 = R.tA_f + fmaf(R.Ss[2].hi, fz, fmaf(R.Ss[1].hi, fy, R.S0.hi));
+  X0 = fmaf(R.Xs[2].hi, fz, fmaf(R.Xs[1].hi, fy, R.X0.hi));
+  Z0 = fmaf(R.Zs[2].hi, fz, fmaf(R.Zs[1].hi, fy, R.Z0.hi));
+}
+
+// candidate interval [lo, lo + len) of x-line (iy, iz)
+__device__ __forceinline__ int line_interval(const DRow& R, int mode, int nx, int iy, int iz, int& lo_out) {
   // t(i) = T0 + i tx, x'(i) = X0 + i xx, z'(i) = Z0 + i zx; constraints c i <= r
-  float T0 = R.tA_f + s0.hi, tx = R.Ss[0].hi;
-  float X0 = x0.hi, xx = R.Xs[0].hi, Z0 = z0.hi, zx = R.Zs[0].hi;
+  float T0, X0, Z0;
+  line_base32(R, iy, iz, T0, X0, Z0);
+  const float tx = R.Ss[0].hi, xx = R.Xs[0].hi, zx = R.Zs[0].hi;
   float lo = 0.0f, hi = (float)(nx - 1);
   bool empty = false;
   auto constrain = [&](float c, float r) {
@@ -506,13 +517,6 @@ __device__ __forceinline__ int line_interval(const DRow& R, int mode, int nx, co
   return ihi - ilo + 1;
 }
 
-// the candidate interval of x-line (iy, iz) and its s, x', z' at ix = 0; the
-// enumeration count and the evaluation both call this, so they agree exactly
-__device__ __forceinline__ int line_setup(const DRow& R, int mode, int nx, int iy, int iz, ff& s0, ff& x0, ff& z0,
-                                          int& lo_out) {
-  line_base(R, iy, iz, s0, x0, z0);
-  return line_interval(R, mode, nx, s0, x0, z0, lo_out);
-}
 
 
 // block-wide exclusive scan of one int per thread (kEvalThreads threads); returns the total
@@ -538,13 +542,25 @@ __device__ __forceinline__ int block_excl_scan(int v, int& excl, int* wscan) {
   return tot;
 }
 
-// line (iy, iz) of line index l of row R (a row's VOI box has fewer than
-// 2^31 lines: the grid has fewer than 2^31 voxels)
-__device__ __forceinline__ void line_yz(const DRow& R, int l, int& iy, int& iz) {
-  const unsigned nyb = (unsigned)(R.iy1 - R.iy0 + 1);
-  const unsigned q = (unsigned)l / nyb;
-  iz = R.iz0 + (int)q;
-  iy = R.iy0 + (int)((unsigned)l - q * nyb);
+// line (iy, iz) of line index l >= 0 of row R (a row's VOI box has fewer than
+// 2^31 lines: the grid has fewer than 2^31 voxels).  inv_nyb = 1 / (lines per
+// iz), correctly rounded.  Below 2^22 the FP32 quotient is within 1/2 of l /
+// nyb, so its truncation is off by at most one, which the remainder corrects.
+__device__ __forceinline__ float line_inv(const DRow& R) { return __frcp_rn((float)(R.iy1 - R.iy0 + 1)); }
+__device__ __forceinline__ void line_yz(const DRow& R, int l, float inv_nyb, int& iy, int& iz) {
+  const int nyb = R.iy1 - R.iy0 + 1;
+  int q, r;
+  if (l < (1 << 22)) {
+    q = (int)((float)l * inv_nyb);
+    r = l - q * nyb;
+    if (r < 0) { --q; r += nyb; }
+    else if (r >= nyb) { ++q; r -= nyb; }
+  } else {
+    q = (int)((unsigned)l / (unsigned)nyb);
+    r = l - q * nyb;
+  }
+  iz = R.iz0 + q;
+  iy = R.iy0 + r;
 }
 
 // lines of a work item: [chunk * lpc, min(+lpc, lines of the row))
@@ -563,16 +579,18 @@ __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, l
   int t = threadIdx.x;
   int len[per];
   int mine = 0;
+  const float inv_nyb = line_inv(R);
 #pragma unroll
   for (int q = 0; q < per; ++q) {
     int li = t * per + q;             // consecutive lines per thread keep the scan order
     len[q] = 0;
     if (li < nl) {
       int iy, iz;
-      line_yz(R, l0 + li, iy, iz);
+      line_yz(R, l0 + li, inv_nyb, iy, iz);
       ff s0, x0, z0;
+      line_base(R, iy, iz, s0, x0, z0);
       int lo;
-      len[q] = line_setup(R, mode, nx, iy, iz, s0, x0, z0, lo);
+      len[q] = line_interval(R, mode, nx, iy, iz, lo);
       sm.sx[li] = make_float4(R.tA_f + s0.hi, x0.hi, x0.lo, z0.hi);
       sm.zc[li] = make_float4(z0.lo, __int_as_float(lo), __int_as_float(nx * (iy + ny * iz)), 0.0f);
       sm.sf[li] = R.sfx0 + (long long)iy * R.sfx_s[1] + (long long)iz * R.sfx_s[2];
@@ -670,12 +688,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
     int l0;
     int nl = item_nlines(R, item - row_item_base[row], l0);
     int cnt = 0;
+    const float inv_nyb = line_inv(R);
     for (int li = lane; li < nl; li += 32) {
       int iy, iz;
-      line_yz(R, l0 + li, iy, iz);
-      ff s0, x0, z0;
+      line_yz(R, l0 + li, inv_nyb, iy, iz);
       int lo;
-      cnt += line_setup(R, G.cutoff_mode, G.nx, iy, iz, s0, x0, z0, lo);
+      cnt += line_interval(R, G.cutoff_mode, G.nx, iy, iz, lo);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
