@@ -25,6 +25,7 @@
 #include <deque>
 #include <map>
 #include <memory>
+#include <limits>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -52,12 +53,14 @@ __global__ void k_beamlet_dot(const long long*, const long long*, const int*, co
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
-__global__ void k_copy_stats(const unsigned*, const long long*, int, const OutSlot*);
+__global__ void k_copy_stats(const unsigned*, const long long*, int, const unsigned long long*, const OutSlot*);
 __global__ void k_scan_partial(const int*, const long long*, long long, long long*);
 __global__ void k_scan_blocks(long long*);
 __global__ void k_scan_final(const int*, const long long*, long long, const long long*, long long*);
 __global__ void k_scan_small(const int*, const long long*, long long, long long*);
 __global__ void k_tail_probe(int, const float*, long long, float*, float*);
+__global__ void k_refine_max(RefineParams);
+__global__ void k_refine(RefineParams);
 }  // namespace dsc
 
 using namespace dsc;
@@ -150,7 +153,8 @@ struct dsc_geometry {
   int profile = 0;                   // DSC_PROFILE_*
   float c3max;
   float* d_rho = nullptr;
-  float4* d_lut = nullptr;
+  float4* d_lut = nullptr;            // evaluation table: (row, difference) pairs, c3 / K
+  float4* d_lut_rows = nullptr;       // the model's rows as given (FP64 re-evaluation)
   std::vector<dsc_beam_desc> beams;
 };
 
@@ -161,8 +165,8 @@ struct OutBufs {
   OutSlot slot{};                    // row_ptr, col, val, beam_scale, row_max, row_cand, inst_begin, status
   ~OutBufs() {
     void* ps[] = {slot.row_ptr, slot.col, slot.val, slot.beam_scale, slot.row_max, slot.row_cand, slot.inst_begin,
-                  slot.status};
-    release_after(done, device, ps, 8);
+                  slot.status, slot.refine};
+    release_after(done, device, ps, 9);
     if (done) cudaEventDestroy(done);
   }
 };
@@ -236,6 +240,13 @@ struct Plan {
   long long* d_row_cand = nullptr;
   long long* d_scan = nullptr;       // kScanBlocks + 1
   int* d_counter = nullptr;
+  // decisions the FP32 values cannot settle (the count pass lists them)
+  unsigned long long* d_rlist_u = nullptr;   // near a threshold: cap_u entries
+  unsigned long long* d_rlist_m = nullptr;   // near a row maximum: cap_m entries
+  unsigned long long* d_rcount = nullptr;   // [2] list lengths
+  unsigned long long* d_mref = nullptr;     // per row: FP64 maximum (double bits)
+  int* d_need_m = nullptr;                  // per row: the FP64 maximum is needed
+  int cap_u = 0, cap_m = 0;
   OutSlot* d_slot = nullptr;         // output pointers of the computation in flight
   cudaGraphExec_t graph = nullptr;   // the captured launch sequence
   cudaStream_t cap_stream = nullptr; // private stream the sequence is captured on
@@ -248,18 +259,18 @@ struct Plan {
   std::mutex mu;                     // one computation at a time per plan
   void free_scratch() {
     void* ps[] = {d_item_cand, d_item_off, d_tile_cnt, d_tile_off, d_item_out, d_vals, d_cols, d_item_row,
-                  d_tile_item0, d_tile_first, d_tile_thr, d_tile_scale, d_tile_next, d_tile_starts};
-    release_after(last_done, device, ps, 14);
+                  d_tile_item0, d_tile_first, d_tile_thr, d_tile_scale, d_tile_next, d_tile_starts, d_rlist_u};
+    release_after(last_done, device, ps, 15);
     d_item_cand = nullptr; d_item_off = nullptr; d_tile_cnt = nullptr; d_tile_off = nullptr; d_item_out = nullptr;
     d_vals = nullptr; d_cols = nullptr; d_item_row = nullptr; d_tile_item0 = nullptr; d_tile_first = nullptr;
-    d_tile_thr = nullptr; d_tile_scale = nullptr; d_tile_next = nullptr; d_tile_starts = nullptr;
+    d_tile_thr = nullptr; d_tile_scale = nullptr; d_tile_next = nullptr; d_tile_starts = nullptr; d_rlist_u = nullptr;
     if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
   }
   ~Plan() {
     free_scratch();
     void* ps[] = {d_inst, d_beams, d_rows, d_row_items, d_row_item_base, d_tables, d_row_max, d_row_cand, d_scan,
-                  d_counter, d_slot};
-    release_after(last_done, device, ps, 11);
+                  d_counter, d_slot, d_rlist_m, d_rcount, d_mref, d_need_m};
+    release_after(last_done, device, ps, 15);
     if (last_done) cudaEventDestroy(last_done);
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
@@ -400,17 +411,14 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
   g->c3max = c3max;
   size_t nvox = (size_t)grid->nx * grid->ny * grid->nz;
   dsc_status st = dalloc(&g->d_rho, nvox, s);
-  float4* rows = nullptr;
   if (st == DSC_OK) st = dalloc(&g->d_lut, 2 * (size_t)model->n, s);
-  if (st == DSC_OK) st = dalloc(&rows, (size_t)model->n, s);
+  if (st == DSC_OK) st = dalloc(&g->d_lut_rows, (size_t)model->n, s);
   if (st != DSC_OK) { dsc_destroy_geometry(g); return st; }
-  cudaError_t e = cudaMemcpyAsync(rows, model->table4, sizeof(float4) * model->n, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(g->d_lut_rows, model->table4, sizeof(float4) * model->n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(rows, model->n, model->profile, g->d_lut);
+    k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(g->d_lut_rows, model->n, model->profile, g->d_lut);
     e = cudaGetLastError();
   }
-  cudaError_t ef = cudaFreeAsync(rows, s);
-  if (e == cudaSuccess) e = ef;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->d_rho, density, nvox * sizeof(float),
                         density_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
@@ -466,6 +474,7 @@ extern "C" void dsc_destroy_geometry(dsc_geometry* g) {
   cudaDeviceSynchronize();
   if (g->d_rho) cudaFree(g->d_rho);
   if (g->d_lut) cudaFree(g->d_lut);
+  if (g->d_lut_rows) cudaFree(g->d_lut_rows);
   delete g;
 }
 
@@ -506,8 +515,12 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
     P->geoms.push_back(g);
     P->geom_ids.push_back(g->id);
     DInst I{};
+    if (!g->d_rho || !g->d_lut || !g->d_lut_rows) return fail(DSC_E_STATE, "geometry %d has no device tables", k);
     I.rho = g->d_rho;
     I.lut = g->d_lut;
+    I.lut_rows = g->d_lut_rows;
+    I.d_max = g->d_max;
+    for (int i = 0; i < 3; ++i) { I.c1d[i] = g->c1[i]; I.c2d[i] = g->c2[i]; }
     I.nx = g->grid.nx; I.ny = g->grid.ny; I.nz = g->grid.nz;
     I.n_lut = g->n_lut;
     I.dx = g->grid.dx; I.dy = g->grid.dy; I.dz = g->grid.dz;
@@ -561,6 +574,12 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_row_cand, P->nrows, s));
   TRY(dalloc(&P->d_scan, kScanBlocks + 1, s));
   TRY(dalloc(&P->d_counter, 4, s));
+  if (P->nrows >= (1 << 24)) return fail(DSC_E_INVAL, "too many beamlets in one launch (%d)", P->nrows);
+  P->cap_m = 4 * P->nrows + 1024;    // a row maximum and its near ties
+  TRY(dalloc(&P->d_rlist_m, P->cap_m, s));
+  TRY(dalloc(&P->d_rcount, 2, s));
+  TRY(dalloc(&P->d_mref, P->nrows, s));
+  TRY(dalloc(&P->d_need_m, P->nrows, s));
   TRY(dalloc(&P->d_slot, 1, s));
   CU(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   CU(cudaEventCreateWithFlags(&P->last_done, cudaEventDisableTiming));
@@ -605,6 +624,9 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_tile_scale, P->n_tiles, s));
   TRY(dalloc(&P->d_tile_next, P->n_tiles, s));
   TRY(dalloc(&P->d_tile_starts, P->n_tiles, s));
+  // about 1e-5 of the candidates fall within kRefineDelta of their threshold
+  P->cap_u = (int)std::min<long long>(std::max<long long>(1 << 16, P->n_cand >> 10), 1 << 28);
+  TRY(dalloc(&P->d_rlist_u, P->cap_u, s));
   out = P;
   return DSC_OK;
 }
@@ -640,6 +662,37 @@ static dsc_status record(EventSet* ev, int i, cudaStream_t s) {
   return DSC_OK;
 }
 
+// the FP64 re-evaluation of the listed pairs: row maxima, then keep decisions
+static dsc_status refine_launch(Plan* P, const CompactParams& cp, cudaStream_t s) {
+  RefineParams rp{};
+  rp.inst = P->d_inst;
+  rp.rows = P->d_rows;
+  rp.beams = P->d_beams;
+  rp.tables = P->d_tables;
+  rp.table_stride = P->stride;
+  rp.item_off = P->d_item_off;
+  rp.item_row = P->d_item_row;
+  rp.n_items = cp.n_items;
+  rp.vals = P->d_vals;
+  rp.cols = P->d_cols;
+  rp.row_max = P->d_row_max;
+  rp.tau = cp.tau;
+  rp.tau_d = P->opts.rel_threshold;
+  rp.rlist_u = P->d_rlist_u;
+  rp.rlist_m = P->d_rlist_m;
+  rp.rcount = P->d_rcount;
+  rp.cap_u = P->cap_u;
+  rp.cap_m = P->cap_m;
+  rp.mref = P->d_mref;
+  rp.need_m = P->d_need_m;
+  rp.tile_cnt = P->d_tile_cnt;
+  k_refine_max<<<refine_blocks(P->cap_m), kRefineThreads, 0, s>>>(rp);
+  CHECK_LAUNCH();
+  k_refine<<<refine_blocks(P->cap_u), kRefineThreads, 0, s>>>(rp);
+  CHECK_LAUNCH();
+  return DSC_OK;
+}
+
 static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   int k0 = (int)g_launches.load();
   const long long* n_items = P->d_row_item_base + P->nrows;
@@ -647,6 +700,9 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   CU(cudaMemsetAsync(P->d_row_max, 0, sizeof(unsigned) * P->nrows, s));
   CU(cudaMemsetAsync(P->d_row_cand, 0, sizeof(long long) * P->nrows, s));
   CU(cudaMemsetAsync(P->d_counter, 0, sizeof(int) * 4, s));
+  CU(cudaMemsetAsync(P->d_rcount, 0, sizeof(unsigned long long) * 2, s));
+  CU(cudaMemsetAsync(P->d_mref, 0, sizeof(unsigned long long) * P->nrows, s));
+  CU(cudaMemsetAsync(P->d_need_m, 0, sizeof(int) * P->nrows, s));
   // a1: beamlet frames, entry/exit, VOI box, work items
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
                                                  P->d_row_items, P->target_cand);
@@ -715,11 +771,19 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.tile_starts = P->d_tile_starts;
   cp.value_dtype = P->opts.value_dtype;
   cp.slot = P->d_slot;
+  cp.rlist_u = P->d_rlist_u;
+  cp.rlist_m = P->d_rlist_m;
+  cp.rcount = P->d_rcount;
+  cp.need_m = P->d_need_m;
+  cp.cap_u = P->cap_u;
+  cp.cap_m = P->cap_m;
+  cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
   k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((P->n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
   CHECK_LAUNCH();
   const unsigned tiles = (unsigned)std::max<long long>(1, (P->n_tiles + kEvalThreads / 32 - 1) / (kEvalThreads / 32));
   k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_cnt);
   CHECK_LAUNCH();
+  TRY(refine_launch(P, cp, s));
   TRY(scan_launch(P->d_tile_cnt, nullptr, P->n_tiles, P->d_scan, P->d_tile_off, s, P->n_tiles));
   k_tile_write<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_off);
   CHECK_LAUNCH();
@@ -731,7 +795,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
                                                         P->rp_off[k], k, k == P->ninst - 1, P->d_slot);
     CHECK_LAUNCH();
   }
-  k_copy_stats<<<(P->nrows + 255) / 256, 256, 0, s>>>(P->d_row_max, P->d_row_cand, P->nrows, P->d_slot);
+  k_copy_stats<<<(P->nrows + 255) / 256, 256, 0, s>>>(P->d_row_max, P->d_row_cand, P->nrows, P->d_rcount, P->d_slot);
   CHECK_LAUNCH();
   TRY(record(ev, 7, s));
   if (nk) *nk = (int)(g_launches.load() - k0);
@@ -758,6 +822,7 @@ static dsc_status alloc_outputs(Plan* P, cudaStream_t s, std::shared_ptr<OutBufs
   TRY(dalloc(&q.row_max, P->nrows, s));
   TRY(dalloc(&q.row_cand, P->nrows, s));
   TRY(dalloc(&q.inst_begin, P->ninst + 1, s));
+  TRY(dalloc(&q.refine, 2, s));
   TRY(dalloc(&q.status, 1, s));
   CU(cudaMemsetAsync(q.status, 0, sizeof(int), s));
   if (P->opts.value_dtype != DSC_VALUE_BF16) {
@@ -1125,6 +1190,16 @@ extern "C" dsc_status dsc_probe_tail(int32_t profile, const float* y_dev, int64_
   return DSC_OK;
 }
 
+extern "C" dsc_status dsc_get_refine_counts(dsc_result* r, int64_t* near_threshold, int64_t* near_max) {
+  if (!r || !near_threshold || !near_max) return fail(DSC_E_INVAL, "null argument");
+  CU(cudaEventSynchronize(r->done));
+  unsigned long long c[2] = {0, 0};
+  CU(cudaMemcpy(c, r->out->slot.refine, sizeof c, cudaMemcpyDeviceToHost));
+  *near_threshold = (int64_t)c[0];
+  *near_max = (int64_t)c[1];
+  return DSC_OK;
+}
+
 extern "C" dsc_status dsc_get_row_stats(dsc_result* r, float* row_max, int64_t* row_cand) {
   if (!r) return fail(DSC_E_INVAL, "null argument");
   CU(cudaEventSynchronize(r->done));
@@ -1372,6 +1447,7 @@ extern "C" dsc_status dsc_server_submit(dsc_server* S, dsc_geometry* geom, const
   q->view.c3max = geom->c3max;
   q->view.d_rho = geom->d_rho;
   q->view.d_lut = geom->d_lut;
+  q->view.d_lut_rows = geom->d_lut_rows;
   for (int i = 0; i < nbeams; ++i) {
     TRY(check_beam(geom, &beams[i]));
     q->view.beams.push_back(beams[i]);

@@ -37,6 +37,10 @@ struct DInst {
   int cutoff_mode;
   float cutoff_k;
   int profile;             // lateral profile: 0 erf (Eq. 3), 1 Laplace, 2 logistic
+  // the model as given, for the FP64 re-evaluation of decisive pairs
+  const float4* lut_rows;  // n_lut rows {T, c3_1, c3_2, c3_3}
+  double d_max;
+  double c1d[3], c2d[3];
   int row_base, nrows;     // rows of this instance in the flat row list
   int beam_base, nbeams;
   float h;                 // depth-table spacing
@@ -111,6 +115,7 @@ struct OutSlot {
   long long* row_cand;     // per row
   long long* inst_begin;   // per instance: first output slot; [ninst] = total
   int* status;             // nonzero when a bounded device wait expired
+  unsigned long long* refine;  // [2] pairs listed for the FP64 re-evaluation: near a threshold, near a row maximum
 };
 
 constexpr int kTilePer = 8;                       // candidates per thread of the compaction
@@ -135,6 +140,59 @@ struct CompactParams {
   int* tile_starts;               // per tile: an item starts inside the tile
   int value_dtype;
   const OutSlot* slot;
+  // decisions FP32 cannot settle: candidates within kRefineDelta (relative)
+  // of their threshold go to rlist_u and are left out of the tile counts;
+  // candidates within kRefineDelta of their row maximum go to rlist_m
+  unsigned long long* rlist_u;   // refine_entry(candidate, row)
+  unsigned long long* rlist_m;
+  unsigned long long* rcount;     // [0] entries of rlist_u, [1] of rlist_m (may exceed the capacities)
+  int* need_m;                    // per row: an rlist_u entry needs the row's FP64 maximum
+  int cap_u, cap_m;
+  float inv_tau_m;                // (1 - kRefineDelta) / tau (infinite for tau = 0)
+};
+
+// a refine-list entry: candidate index in the low 40 bits, row above (a
+// launch has fewer than 2^24 rows and 2^40 candidates)
+constexpr int kRefineRowShift = 40;
+__host__ __device__ __forceinline__ unsigned long long refine_entry(long long p, int row) {
+  return ((unsigned long long)row << kRefineRowShift) | (unsigned long long)p;
+}
+
+// relative window around a threshold (and below a row maximum) inside which
+// the FP32 value does not settle a decision: the evaluation's FP32 error is
+// below 3e-6 relative
+constexpr float kRefineDelta = 1e-5f;
+
+// the FP64 re-evaluation: one warp per listed pair, kRefineThreads per CTA,
+// enough CTAs for a warp per entry up to 4096 entries (grid-stride beyond)
+constexpr int kRefineThreads = 128;
+inline unsigned refine_blocks(int cap) {
+  const int warps = cap < 4096 ? cap : 4096;
+  return (unsigned)((warps + kRefineThreads / 32 - 1) / (kRefineThreads / 32));
+}
+
+// the FP64 re-evaluation of the pairs in the refine lists
+struct RefineParams {
+  const DInst* inst;
+  const DRow* rows;
+  const DBeam* beams;
+  const float* tables;
+  int table_stride;
+  const long long* item_off;
+  const int* item_row;
+  const long long* n_items;
+  float* vals;                    // refined values are written back
+  const int* cols;
+  const unsigned* row_max;        // FP32 row maxima (float bits), as the compaction reads them
+  float tau;                      // the compaction's FP32 threshold factor
+  double tau_d;                   // the threshold factor as given
+  const unsigned long long* rlist_u;
+  const unsigned long long* rlist_m;
+  const unsigned long long* rcount;
+  int cap_u, cap_m;
+  const int* need_m;              // rows whose FP64 maximum is needed
+  unsigned long long* mref;       // per row: FP64 maximum (double bits) of the rlist_m pairs
+  int* tile_cnt;                  // kept refined pairs are added to their tile's count
 };
 
 // process-wide work decomposition (dsc_set_tuning): candidates per work item

@@ -1096,8 +1096,13 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
   // boundary inside this lane's range (kTilePer: none)
   constexpr float kTiny = 1.40129846e-45f;
   float thr1 = fmaxf(thr, kTiny);
+  // count pass: the refinement windows of the current row (empty when thr1 is
+  // the smallest denormal: no value lies strictly between ulo and uhi)
+  constexpr float kLo = 1.0f - kRefineDelta, kHi = 1.0f + kRefineDelta;
+  float ulo = 0.0f, uhi = 0.0f, mlo = 0.0f;
+  if (!kCols) { ulo = thr1 * kLo; uhi = thr1 * kHi; mlo = thr1 * p.inv_tau_m; }
   int nx = next >= n ? kTilePer : (int)min(next - p0, (long long)kTilePer);
-  unsigned keep = 0;
+  unsigned keep = 0, special = 0;
 #pragma unroll
   for (int i = 0; i < kTilePer; ++i) {
     if (i >= nx) {                                     // crossing into the next item(s)
@@ -1109,11 +1114,49 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
       const int r = p.item_row[it];
       thr1 = fmaxf(p.tau * __uint_as_float(p.row_max[r]), kTiny);
       if (bf16) scale = p.slot->beam_scale[p.rows[r].beam];
+      if (!kCols) { ulo = thr1 * kLo; uhi = thr1 * kHi; mlo = thr1 * p.inv_tau_m; }
       nx = next >= n ? kTilePer : (int)min(next - p0, (long long)kTilePer);
     }
-    if (K.D[i] >= thr1) {
+    const float D = K.D[i];
+    if (D >= thr1) {
       keep |= 1u << i;
       if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
+    }
+    if (!kCols && ((D > ulo && D < uhi) || D >= mlo)) special |= 1u << i;
+  }
+  if (!kCols && special) {
+    // count pass, candidates near their threshold or their row maximum (rare).
+    // A value within kRefineDelta of its threshold does not settle the
+    // decision in FP32: it is listed for the FP64 re-evaluation, which adds
+    // it to the count if kept, its row is marked as needing an FP64 maximum,
+    // and it leaves this count.  A value within kRefineDelta of the row
+    // maximum is listed for that maximum.  A full list leaves the FP32
+    // decision in place.  The item of each position is found again from the
+    // tile's first item.
+    long long it2 = item0, next2 = p.tile_next[tile];
+#pragma unroll
+    for (int i = 0; i < kTilePer; ++i) {              // static positions: K stays in registers
+      if (!(special & (1u << i))) continue;
+      const long long pos = p0 + i;
+      while (next2 <= pos && it2 + 1 < ni) {
+        ++it2;
+        next2 = it2 + 1 < ni ? off[it2 + 1] : n;
+      }
+      const int r = p.item_row[it2];
+      const float t1 = fmaxf(p.tau * __uint_as_float(p.row_max[r]), kTiny);
+      const float D = K.D[i];
+      if (D > t1 * kLo && D < t1 * kHi) {
+        const unsigned long long e = atomicAdd(p.rcount, 1ull);
+        if (e < (unsigned long long)p.cap_u) {
+          p.rlist_u[e] = refine_entry(pos, r);
+          p.need_m[r] = 1;
+          keep &= ~(1u << i);
+        }
+      }
+      if (D >= t1 * p.inv_tau_m) {
+        const unsigned long long e = atomicAdd(p.rcount + 1, 1ull);
+        if (e < (unsigned long long)p.cap_m) p.rlist_m[e] = refine_entry(pos, r);
+      }
     }
   }
   K.keep = keep;
@@ -1158,7 +1201,7 @@ __global__ void k_tile_prep(CompactParams p) {
   }
 }
 
-__global__ void __launch_bounds__(kEvalThreads) k_tile_count(CompactParams p, int* tile_cnt) {
+__global__ void __launch_bounds__(kEvalThreads, 16) k_tile_count(CompactParams p, int* tile_cnt) {
   const int lane = threadIdx.x & 31;
   const long long tile = (long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5);
   const long long base = tile * kTile;
@@ -1253,12 +1296,13 @@ __global__ void k_row_ptr(const long long* __restrict__ row_item_base, const lon
 
 // per-row statistics into the result
 __global__ void k_copy_stats(const unsigned* __restrict__ row_max, const long long* __restrict__ row_cand, int nrows,
-                             const OutSlot* __restrict__ slot) {
+                             const unsigned long long* __restrict__ rcount, const OutSlot* __restrict__ slot) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < nrows) {
     slot->row_max[r] = row_max[r];
     slot->row_cand[r] = row_cand[r];
   }
+  if (r < 2 && slot->refine) slot->refine[r] = rcount[r];
 }
 
 // ---------------------------------------------------------------------------

@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <limits>
 #include <mutex>
 
 namespace dsc {
@@ -34,6 +35,8 @@ __global__ void k_eval(EvalParams);
 __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_tile_prep(CompactParams);
 __global__ void k_lut_pairs(const float4*, int, int, float4*);
+__global__ void k_refine_max(RefineParams);
+__global__ void k_refine(RefineParams);
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
@@ -220,7 +223,12 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   float* d_scale = cv.take<float>(1);
   int* d_status = cv.take<int>(1);
   long long* d_inst_begin = cv.take<long long>(2);
-  if (!d_inst_begin)
+  const int cap_m = 4 * nrows + 1024;
+  unsigned long long* d_rlist_m = cv.take<unsigned long long>(cap_m);
+  unsigned long long* d_rcount = cv.take<unsigned long long>(2);
+  unsigned long long* d_mref = cv.take<unsigned long long>(nrows);
+  int* d_need_m = cv.take<int>(nrows);
+  if (!d_need_m)
     return na_fail(DSC_E_INVAL, "needs more than %zu bytes of working memory (the fixed maximum) for %d beamlets",
                    kNoAllocBytes, nrows);
 
@@ -228,7 +236,13 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(d_lut_rows, model->n, model->profile, d_lut);
   NA_LAUNCH();
   I.lut = d_lut;
+  I.lut_rows = d_lut_rows;
+  I.d_max = model->d_max;
+  for (int i = 0; i < 3; ++i) { I.c1d[i] = model->c1[i]; I.c2d[i] = model->c2[i]; }
   NA_CU(cudaMemcpyAsync(d_inst, &I, sizeof(DInst), cudaMemcpyHostToDevice, s));
+  NA_CU(cudaMemsetAsync(d_rcount, 0, sizeof(unsigned long long) * 2, s));
+  NA_CU(cudaMemsetAsync(d_mref, 0, sizeof(unsigned long long) * nrows, s));
+  NA_CU(cudaMemsetAsync(d_need_m, 0, sizeof(int) * nrows, s));
   for (int b = 0, row = 0; b < nbeams; ++b) {
     DBeam D{};
     D.inst = 0;
@@ -297,7 +311,9 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   float* d_tile_scale = cv.take<float>(n_tiles);
   long long* d_tile_next = cv.take<long long>(n_tiles);
   int* d_tile_starts = cv.take<int>(n_tiles);
-  if (!d_tile_starts)
+  const int cap_u = (int)std::min<long long>(std::max<long long>(1 << 16, n_cand >> 10), 1 << 28);
+  unsigned long long* d_rlist_u = cv.take<unsigned long long>(cap_u);
+  if (!d_rlist_u)
     return na_fail(DSC_E_INVAL, "needs %zu bytes of working memory for %lld candidate pairs; the fixed maximum is %zu",
                    cv.need, n_cand, kNoAllocBytes);
 
@@ -348,6 +364,13 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.tile_starts = d_tile_starts;
   cp.value_dtype = DSC_VALUE_F32;
   cp.slot = d_slot;
+  cp.rlist_u = d_rlist_u;
+  cp.rlist_m = d_rlist_m;
+  cp.rcount = d_rcount;
+  cp.need_m = d_need_m;
+  cp.cap_u = cap_u;
+  cp.cap_m = cap_m;
+  cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
   k_tile_map<<<256, 256, 0, s>>>(d_item_off, n_items_dev, n_cand, d_tile_item0, d_tile_first);
   NA_LAUNCH();
   k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
@@ -355,6 +378,32 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   // kept count first, so the capacity is checked before any output is touched
   const unsigned tiles = (unsigned)(n_tiles > 0 ? (n_tiles + kEvalThreads / 32 - 1) / (kEvalThreads / 32) : 1);
   k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, d_tile_cnt);
+  NA_LAUNCH();
+  RefineParams rp{};
+  rp.inst = d_inst;
+  rp.rows = d_rows;
+  rp.beams = d_beams;
+  rp.tables = d_tables;
+  rp.table_stride = stride;
+  rp.item_off = d_item_off;
+  rp.item_row = d_item_row;
+  rp.n_items = n_items_dev;
+  rp.vals = d_vals;
+  rp.cols = d_cols;
+  rp.row_max = d_row_max;
+  rp.tau = cp.tau;
+  rp.tau_d = opts->rel_threshold;
+  rp.rlist_u = d_rlist_u;
+  rp.rlist_m = d_rlist_m;
+  rp.rcount = d_rcount;
+  rp.cap_u = cap_u;
+  rp.cap_m = cap_m;
+  rp.mref = d_mref;
+  rp.need_m = d_need_m;
+  rp.tile_cnt = d_tile_cnt;
+  k_refine_max<<<refine_blocks(cap_m), kRefineThreads, 0, s>>>(rp);
+  NA_LAUNCH();
+  k_refine<<<refine_blocks(cap_u), kRefineThreads, 0, s>>>(rp);
   NA_LAUNCH();
   st = na_scan(d_tile_cnt, nullptr, n_tiles, d_scan, d_tile_off, s, n_tiles);
   if (st != DSC_OK) return st;

@@ -1,0 +1,176 @@
+// dsc_refine.cu -- the decisions FP32 cannot settle, re-evaluated in FP64.
+//
+// The evaluation computes every D_ij in FP32 with a relative error below
+// about 3e-6 (the fitted erfc, FP32 arguments, erf pairs that partly cancel
+// in the lateral tails).  Two kinds of decision are closer than that:
+//   * keep or drop, for a value within kRefineDelta of tau * M_j;
+//   * which candidate is the row maximum M_j itself, for values within
+//     kRefineDelta of the FP32 maximum.
+// The count pass lists both kinds (a few thousand pairs per step).  Here each
+// listed pair is evaluated again in FP64 from the same inputs: the voxel
+// centre, the beamlet frame and entry point (FP64 from the set-up), the
+// row's depth table (Section 2.2) and the beam model as given, Eq. 2 with the
+// profile's erf pair (Eq. 3), a warp per pair with the twelve tails spread
+// over twelve lanes (the kernels are a single short wave: their time is one
+// pair's FP64 latency).  Row maxima come first (k_refine_max), then the
+// keep decisions against tau * M_j in FP64 (k_refine).  The refined value is
+// written back, and where its FP32 rounding falls on the other side of the
+// compaction's FP32 threshold it is set to that threshold (kept) or one ulp
+// below it (dropped), a change no larger than the gap between the FP32 and
+// FP64 thresholds (a few 1e-6 relative); kept pairs are added to their tile's
+// count.  The FP64 depth table is the FP32 one widened, which limits
+// the refined value to about 3e-7 relative: decisions farther than 1e-6 from
+// the threshold are exact.
+#include "dsc_internal.h"
+
+namespace dsc {
+namespace {
+
+constexpr double kSqrt2 = 1.41421356237309504880;
+constexpr double kSqrt3OverPi = 0.55132889542179204315;   // sqrt 3 / pi
+
+// 2 G(y) for y >= 0: the tail of the lateral kernel in units of its scale s
+__device__ double tail2(int profile, double y) {
+  if (profile == 1) return exp(-y);                      // Laplace
+  if (profile == 2) {                                    // logistic
+    const double e = exp(-y);
+    return 2.0 * e / (1.0 + e);
+  }
+  return erfc(y / kSqrt2);                               // Gaussian: s = c3
+}
+
+// D for the pair (row R, voxel col) in FP64, one warp per pair: every lane
+// forms the geometry, depth and beam model; lanes 0..11 take one tail each
+// (term i = lane / 4; lanes 4i, 4i+1: X at y1, y2; 4i+2, 4i+3: Z), and the
+// sum of Eq. 3 is formed from the shuffled tails.  The result is valid in
+// every lane.
+__device__ double eval_pair64_warp(const DRow& R, const DInst& G, const DBeam& B, const float* tab, int col,
+                                   int lane) {
+  const long long nxy = (long long)G.nx * G.ny;
+  const int iz = (int)(col / nxy);
+  const int rem = (int)(col - (long long)iz * nxy);
+  const int iy = rem / G.nx, ix = rem - iy * G.nx;
+  // voxel centre relative to the source; t, x', z' on the beamlet frame (Fig. 1)
+  const double w0 = G.ox + (ix + 0.5) * G.dx - R.S[0];
+  const double w1 = G.oy + (iy + 0.5) * G.dy - R.S[1];
+  const double w2 = G.oz + (iz + 0.5) * G.dz - R.S[2];
+  const double t = w0 * R.e[0] + w1 * R.e[1] + w2 * R.e[2];
+  const double xp = w0 * R.x[0] + w1 * R.x[1] + w2 * R.x[2];
+  const double zp = w0 * R.z[0] + w1 * R.z[1] + w2 * R.z[2];
+  // radiological depth at O' (Section 2.2): the table, linearly
+  double d = 0.0;
+  const double s = t - R.tA;
+  if (R.n_table > 0 && s > 0.0) {
+    const double f = s / G.hd, kf = floor(f);
+    if (kf >= R.n_table - 1) {
+      d = tab[R.n_table - 1];
+    } else {
+      const int k = (int)kf;
+      d = (double)tab[k] + (f - kf) * ((double)tab[k + 1] - (double)tab[k]);
+    }
+  }
+  // beam model at d: T and c3_1..3, linearly between rows, the last row beyond
+  double T, c3[3];
+  double g = d * (G.n_lut - 1) / G.d_max;
+  if (g < 0.0) g = 0.0;
+  if (g >= G.n_lut - 1) {
+    const float4 r = G.lut_rows[G.n_lut - 1];
+    T = r.x; c3[0] = r.y; c3[1] = r.z; c3[2] = r.w;
+  } else {
+    const int k = (int)floor(g);
+    const double wt = g - k;
+    const float4 a = G.lut_rows[k], b = G.lut_rows[k + 1];
+    T = a.x + wt * ((double)b.x - a.x);
+    c3[0] = a.y + wt * ((double)b.y - a.y);
+    c3[1] = a.z + wt * ((double)b.z - a.z);
+    c3[2] = a.w + wt * ((double)b.w - a.w);
+  }
+  // this lane's tail: 2 G(y) with y1 = (|x| - h) / s, y2 = (|x| + h) / s,
+  // 2 G(y) = 2 - 2 G(-y) for y < 0 (the tails never cancel)
+  double v = 0.0;
+  if (lane < 12) {
+    const int i = lane >> 2;
+    const bool zax = (lane & 2) != 0, second = (lane & 1) != 0;
+    const double side = zax ? B.b : B.a;
+    const double h = 0.5 * G.c2d[i] * side * t / B.sad;             // c2 a_t / 2 (b_t for Z)
+    const double sc = G.profile == 1 ? c3[i] / kSqrt2 : (G.profile == 2 ? c3[i] * kSqrt3OverPi : c3[i]);
+    const double ax = fabs(zax ? zp : xp);
+    const double y = second ? (ax + h) / sc : (ax - h) / sc;
+    v = y >= 0.0 ? tail2(G.profile, y) : 2.0 - tail2(G.profile, -y);
+  }
+  double F = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double X = __shfl_sync(0xffffffffu, v, 4 * i) - __shfl_sync(0xffffffffu, v, 4 * i + 1);
+    const double Z = __shfl_sync(0xffffffffu, v, 4 * i + 2) - __shfl_sync(0xffffffffu, v, 4 * i + 3);
+    F += 0.25 * G.c1d[i] * X * Z;
+  }
+  if (!(t > 0.0)) return 0.0;
+  // Eq. 2: A = T(d) (SAD / t)^2
+  const double q = B.sad / t;
+  return T * q * q * F;
+}
+
+__device__ double refined(const RefineParams& P, unsigned long long entry, long long* p_out, int* row_out,
+                          int lane) {
+  const long long p = (long long)(entry & ((1ull << kRefineRowShift) - 1ull));
+  const int r = (int)(entry >> kRefineRowShift);
+  const DRow& R = P.rows[r];
+  *p_out = p;
+  *row_out = r;
+  return eval_pair64_warp(R, P.inst[R.inst], P.beams[R.beam], P.tables + (size_t)r * P.table_stride, P.cols[p],
+                          lane);
+}
+
+}  // namespace
+
+// FP64 row maxima over the listed near-maximum pairs, a warp per pair
+// (atomicMax on the bits of a non-negative double orders like the value)
+__global__ void __launch_bounds__(kRefineThreads) k_refine_max(RefineParams P) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n = min(P.rcount[1], (unsigned long long)P.cap_m);
+  const unsigned long long warps = (unsigned long long)gridDim.x * (kRefineThreads / 32);
+  for (unsigned long long e = blockIdx.x * (unsigned long long)(kRefineThreads / 32) + (threadIdx.x >> 5); e < n;
+       e += warps) {
+    const unsigned long long entry = P.rlist_m[e];
+    if (!P.need_m[(int)(entry >> kRefineRowShift)]) continue;   // no keep decision of the row waits for it
+    long long p;
+    int r;
+    const double D = refined(P, entry, &p, &r, lane);
+    if (lane == 0) atomicMax(P.mref + r, (unsigned long long)__double_as_longlong(fmax(D, 0.0)));
+  }
+}
+
+// keep decisions of the listed pairs in FP64, a warp per pair; the value
+// written back makes the compaction's FP32 test agree, and kept pairs join
+// their tile's count
+__global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams P) {
+  constexpr float kTiny = 1.40129846e-45f;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n = min(P.rcount[0], (unsigned long long)P.cap_u);
+  const unsigned long long warps = (unsigned long long)gridDim.x * (kRefineThreads / 32);
+  for (unsigned long long e = blockIdx.x * (unsigned long long)(kRefineThreads / 32) + (threadIdx.x >> 5); e < n;
+       e += warps) {
+    long long p;
+    int r;
+    const double D = refined(P, P.rlist_u[e], &p, &r, lane);
+    if (lane != 0) continue;
+    const float thr1 = fmaxf(P.tau * __uint_as_float(P.row_max[r]), kTiny);   // the compaction's FP32 threshold
+    const double M = __longlong_as_double((long long)P.mref[r]);
+    float v;
+    bool keep;
+    if (M > 0.0) {
+      keep = D > 0.0 && D >= P.tau_d * M;
+      v = __double2float_rn(D);
+      if (keep && v < thr1) v = thr1;
+      if (!keep && v >= thr1) v = __uint_as_float(__float_as_uint(thr1) - 1u);   // thr1 > smallest denormal
+    } else {                                                            // no FP64 maximum: FP32 decides
+      v = P.vals[p];
+      keep = v >= thr1;
+    }
+    P.vals[p] = v;
+    if (keep) atomicAdd(P.tile_cnt + p / kTile, 1);
+  }
+}
+
+}  // namespace dsc

@@ -34,7 +34,7 @@ EXPORTS = [
     "dsc_release_result", "dsc_get_beamlets", "dsc_get_depth_tables", "dsc_get_row_stats", "dsc_get_stage_times",
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
     "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune", "dsc_dose", "dsc_beamlet_dot",
-    "dsc_measure_alu_peaks", "dsc_probe_tail",
+    "dsc_measure_alu_peaks", "dsc_probe_tail", "dsc_get_refine_counts",
 ]
 
 
@@ -123,6 +123,7 @@ def lib():
                                        C.POINTER(C.c_float)]),
             "dsc_measure_alu_peaks": (C.c_int, [C.c_double, C.POINTER(C.c_double), I32, P]),
             "dsc_probe_tail": (C.c_int, [I32, P, I64, P, P, P]),
+            "dsc_get_refine_counts": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -269,6 +270,13 @@ def dsc_probe_tail(profile: int, y_ptr: int, n: int, ours_ptr: int, cuda_ptr: in
     """T(y) as the evaluation computes it, and CUDA's erfcf / expf of the same
     tail; device pointers to n floats each."""
     _check(lib().dsc_probe_tail(int(profile), y_ptr, int(n), ours_ptr, cuda_ptr, stream))
+
+
+def dsc_get_refine_counts(res) -> tuple:
+    """(pairs re-evaluated in FP64 near a threshold, near a row maximum)."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().dsc_get_refine_counts(res, C.byref(a), C.byref(b)))
+    return int(a.value), int(b.value)
 
 
 def dsc_result_wait(res):

@@ -162,6 +162,10 @@ PROFILE_ERF, PROFILE_LAPLACE, PROFILE_LOGISTIC = 0, 1, 2
 # depth-table construction of a workload
 TABLE_EXACT, TABLE_TRILINEAR = 0, 1
 
+# relative threshold on the per-beamlet maximum (the library's decisions near
+# it are taken in FP64 with this exact value, as the oracle's)
+TAU = 1e-3
+
 @dataclasses.dataclass
 class Workload:
     name: str
@@ -169,7 +173,7 @@ class Workload:
     density: np.ndarray      # float32 [nz][ny][nx]
     model: Model
     beams: List[Beam]
-    tau: float = 1e-3        # relative threshold on the per-beamlet maximum
+    tau: float = TAU         # relative threshold on the per-beamlet maximum
     h_frac: float = 0.5      # depth-table spacing as a fraction of min voxel side
     value_dtype: int = VALUE_F32
     table_mode: int = 0      # TABLE_EXACT (Siddon integral) or TABLE_TRILINEAR (the paper's sampled table)
