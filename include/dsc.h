@@ -271,8 +271,9 @@ dsc_status dsc_get_depth_tables(dsc_result* res, float* out, int64_t cap, int32_
 /* Pairs of the computation (all instances of its launch) whose decision the
  * FP32 values could not settle and that were evaluated again in FP64: values
  * within 1e-5 (relative) of their row's threshold (the keep decision), and
- * within 1e-5 of their row's maximum (the maximum itself).  Counts above the
- * lists' capacities (about n_cand / 1024, and 4 per row) were decided in FP32. */
+ * within 1e-5 of their row's maximum (the maximum itself).  Pairs beyond the
+ * list's capacity (about n_cand / 1024), and rows with more than 4 pairs near
+ * their maximum, were decided in FP32. */
 dsc_status dsc_get_refine_counts(dsc_result* res, int64_t* near_threshold, int64_t* near_max);
 /* Per row: max D over the row's candidates and the candidate count. */
 dsc_status dsc_get_row_stats(dsc_result* res, float* row_max, int64_t* row_cand);

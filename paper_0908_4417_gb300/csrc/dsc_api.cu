@@ -59,7 +59,6 @@ __global__ void k_scan_blocks(long long*);
 __global__ void k_scan_final(const int*, const long long*, long long, const long long*, long long*);
 __global__ void k_scan_small(const int*, const long long*, long long, long long*);
 __global__ void k_tail_probe(int, const float*, long long, float*, float*);
-__global__ void k_refine_max(RefineParams);
 __global__ void k_refine(RefineParams);
 }  // namespace dsc
 
@@ -242,11 +241,10 @@ struct Plan {
   int* d_counter = nullptr;
   // decisions the FP32 values cannot settle (the count pass lists them)
   unsigned long long* d_rlist_u = nullptr;   // near a threshold: cap_u entries
-  unsigned long long* d_rlist_m = nullptr;   // near a row maximum: cap_m entries
-  unsigned long long* d_rcount = nullptr;   // [2] list lengths
-  unsigned long long* d_mref = nullptr;     // per row: FP64 maximum (double bits)
-  int* d_need_m = nullptr;                  // per row: the FP64 maximum is needed
-  int cap_u = 0, cap_m = 0;
+  unsigned long long* d_rcount = nullptr;    // [2] listed counts
+  int* d_mcount = nullptr;                   // per row: near-maximum candidates seen
+  long long* d_mslot = nullptr;              // per row: kMaxSlots near-maximum candidates
+  int cap_u = 0;
   OutSlot* d_slot = nullptr;         // output pointers of the computation in flight
   cudaGraphExec_t graph = nullptr;   // the captured launch sequence
   cudaStream_t cap_stream = nullptr; // private stream the sequence is captured on
@@ -269,8 +267,8 @@ struct Plan {
   ~Plan() {
     free_scratch();
     void* ps[] = {d_inst, d_beams, d_rows, d_row_items, d_row_item_base, d_tables, d_row_max, d_row_cand, d_scan,
-                  d_counter, d_slot, d_rlist_m, d_rcount, d_mref, d_need_m};
-    release_after(last_done, device, ps, 15);
+                  d_counter, d_slot, d_rcount, d_mcount, d_mslot};
+    release_after(last_done, device, ps, 14);
     if (last_done) cudaEventDestroy(last_done);
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
@@ -575,11 +573,9 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_scan, kScanBlocks + 1, s));
   TRY(dalloc(&P->d_counter, 4, s));
   if (P->nrows >= (1 << 24)) return fail(DSC_E_INVAL, "too many beamlets in one launch (%d)", P->nrows);
-  P->cap_m = 4 * P->nrows + 1024;    // a row maximum and its near ties
-  TRY(dalloc(&P->d_rlist_m, P->cap_m, s));
   TRY(dalloc(&P->d_rcount, 2, s));
-  TRY(dalloc(&P->d_mref, P->nrows, s));
-  TRY(dalloc(&P->d_need_m, P->nrows, s));
+  TRY(dalloc(&P->d_mcount, P->nrows, s));
+  TRY(dalloc(&P->d_mslot, (size_t)P->nrows * kMaxSlots, s));
   TRY(dalloc(&P->d_slot, 1, s));
   CU(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   CU(cudaEventCreateWithFlags(&P->last_done, cudaEventDisableTiming));
@@ -662,7 +658,7 @@ static dsc_status record(EventSet* ev, int i, cudaStream_t s) {
   return DSC_OK;
 }
 
-// the FP64 re-evaluation of the listed pairs: row maxima, then keep decisions
+// the FP64 re-evaluation of the listed pairs (their row maxima and keep decisions)
 static dsc_status refine_launch(Plan* P, const CompactParams& cp, cudaStream_t s) {
   RefineParams rp{};
   rp.inst = P->d_inst;
@@ -679,15 +675,11 @@ static dsc_status refine_launch(Plan* P, const CompactParams& cp, cudaStream_t s
   rp.tau = cp.tau;
   rp.tau_d = P->opts.rel_threshold;
   rp.rlist_u = P->d_rlist_u;
-  rp.rlist_m = P->d_rlist_m;
   rp.rcount = P->d_rcount;
   rp.cap_u = P->cap_u;
-  rp.cap_m = P->cap_m;
-  rp.mref = P->d_mref;
-  rp.need_m = P->d_need_m;
+  rp.mcount = P->d_mcount;
+  rp.mslot = P->d_mslot;
   rp.tile_cnt = P->d_tile_cnt;
-  k_refine_max<<<refine_blocks(P->cap_m), kRefineThreads, 0, s>>>(rp);
-  CHECK_LAUNCH();
   k_refine<<<refine_blocks(P->cap_u), kRefineThreads, 0, s>>>(rp);
   CHECK_LAUNCH();
   return DSC_OK;
@@ -701,8 +693,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   CU(cudaMemsetAsync(P->d_row_cand, 0, sizeof(long long) * P->nrows, s));
   CU(cudaMemsetAsync(P->d_counter, 0, sizeof(int) * 4, s));
   CU(cudaMemsetAsync(P->d_rcount, 0, sizeof(unsigned long long) * 2, s));
-  CU(cudaMemsetAsync(P->d_mref, 0, sizeof(unsigned long long) * P->nrows, s));
-  CU(cudaMemsetAsync(P->d_need_m, 0, sizeof(int) * P->nrows, s));
+  CU(cudaMemsetAsync(P->d_mcount, 0, sizeof(int) * P->nrows, s));
   // a1: beamlet frames, entry/exit, VOI box, work items
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
                                                  P->d_row_items, P->target_cand);
@@ -772,11 +763,10 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.value_dtype = P->opts.value_dtype;
   cp.slot = P->d_slot;
   cp.rlist_u = P->d_rlist_u;
-  cp.rlist_m = P->d_rlist_m;
   cp.rcount = P->d_rcount;
-  cp.need_m = P->d_need_m;
+  cp.mcount = P->d_mcount;
+  cp.mslot = P->d_mslot;
   cp.cap_u = P->cap_u;
-  cp.cap_m = P->cap_m;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
   k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((P->n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
   CHECK_LAUNCH();

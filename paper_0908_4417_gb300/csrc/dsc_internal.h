@@ -142,12 +142,13 @@ struct CompactParams {
   const OutSlot* slot;
   // decisions FP32 cannot settle: candidates within kRefineDelta (relative)
   // of their threshold go to rlist_u and are left out of the tile counts;
-  // candidates within kRefineDelta of their row maximum go to rlist_m
+  // candidates within kRefineDelta of their row maximum go to their row's
+  // slots (kMaxSlots per row)
   unsigned long long* rlist_u;   // refine_entry(candidate, row)
-  unsigned long long* rlist_m;
-  unsigned long long* rcount;     // [0] entries of rlist_u, [1] of rlist_m (may exceed the capacities)
-  int* need_m;                    // per row: an rlist_u entry needs the row's FP64 maximum
-  int cap_u, cap_m;
+  unsigned long long* rcount;     // [0] entries listed in rlist_u, [1] near-maximum candidates (may exceed capacities)
+  int* mcount;                    // per row: near-maximum candidates seen
+  long long* mslot;               // per row: kMaxSlots candidate indices
+  int cap_u;
   float inv_tau_m;                // (1 - kRefineDelta) / tau (infinite for tau = 0)
 };
 
@@ -158,13 +159,18 @@ __host__ __device__ __forceinline__ unsigned long long refine_entry(long long p,
   return ((unsigned long long)row << kRefineRowShift) | (unsigned long long)p;
 }
 
+// near-maximum candidates kept per row for its FP64 maximum (more: FP32 decides the row)
+constexpr int kMaxSlots = 4;
+
 // relative window around a threshold (and below a row maximum) inside which
 // the FP32 value does not settle a decision: the evaluation's FP32 error is
 // below 3e-6 relative
 constexpr float kRefineDelta = 1e-5f;
 
 // the FP64 re-evaluation: one warp per listed pair, kRefineThreads per CTA,
-// enough CTAs for a warp per entry up to 4096 entries (grid-stride beyond)
+// enough CTAs for a warp per entry up to 4096 entries (grid-stride beyond);
+// the warp evaluates its pair and its row's near-maximum candidates, two
+// pairs at a time in half-warps
 constexpr int kRefineThreads = 128;
 inline unsigned refine_blocks(int cap) {
   const int warps = cap < 4096 ? cap : 4096;
@@ -187,11 +193,10 @@ struct RefineParams {
   float tau;                      // the compaction's FP32 threshold factor
   double tau_d;                   // the threshold factor as given
   const unsigned long long* rlist_u;
-  const unsigned long long* rlist_m;
   const unsigned long long* rcount;
-  int cap_u, cap_m;
-  const int* need_m;              // rows whose FP64 maximum is needed
-  unsigned long long* mref;       // per row: FP64 maximum (double bits) of the rlist_m pairs
+  int cap_u;
+  const int* mcount;              // per row: near-maximum candidates seen
+  const long long* mslot;         // per row: kMaxSlots candidate indices
   int* tile_cnt;                  // kept refined pairs are added to their tile's count
 };
 

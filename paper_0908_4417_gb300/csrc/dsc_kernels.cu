@@ -1128,9 +1128,9 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
     // count pass, candidates near their threshold or their row maximum (rare).
     // A value within kRefineDelta of its threshold does not settle the
     // decision in FP32: it is listed for the FP64 re-evaluation, which adds
-    // it to the count if kept, its row is marked as needing an FP64 maximum,
-    // and it leaves this count.  A value within kRefineDelta of the row
-    // maximum is listed for that maximum.  A full list leaves the FP32
+    // it to the count if kept, and it leaves this count.  A value within
+    // kRefineDelta of the row maximum goes to the row's slots, from which the
+    // re-evaluation takes the FP64 maximum.  A full list leaves the FP32
     // decision in place.  The item of each position is found again from the
     // tile's first item.
     long long it2 = item0, next2 = p.tile_next[tile];
@@ -1149,13 +1149,13 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
         const unsigned long long e = atomicAdd(p.rcount, 1ull);
         if (e < (unsigned long long)p.cap_u) {
           p.rlist_u[e] = refine_entry(pos, r);
-          p.need_m[r] = 1;
           keep &= ~(1u << i);
         }
       }
       if (D >= t1 * p.inv_tau_m) {
-        const unsigned long long e = atomicAdd(p.rcount + 1, 1ull);
-        if (e < (unsigned long long)p.cap_m) p.rlist_m[e] = refine_entry(pos, r);
+        atomicAdd(p.rcount + 1, 1ull);
+        const int k = atomicAdd(p.mcount + r, 1);
+        if (k < kMaxSlots) p.mslot[(size_t)r * kMaxSlots + k] = pos;
       }
     }
   }
@@ -1201,7 +1201,7 @@ __global__ void k_tile_prep(CompactParams p) {
   }
 }
 
-__global__ void __launch_bounds__(kEvalThreads, 16) k_tile_count(CompactParams p, int* tile_cnt) {
+__global__ void __launch_bounds__(kEvalThreads, 12) k_tile_count(CompactParams p, int* tile_cnt) {
   const int lane = threadIdx.x & 31;
   const long long tile = (long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5);
   const long long base = tile * kTile;

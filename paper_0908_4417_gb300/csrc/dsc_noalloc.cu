@@ -35,7 +35,6 @@ __global__ void k_eval(EvalParams);
 __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_tile_prep(CompactParams);
 __global__ void k_lut_pairs(const float4*, int, int, float4*);
-__global__ void k_refine_max(RefineParams);
 __global__ void k_refine(RefineParams);
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
@@ -223,12 +222,10 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   float* d_scale = cv.take<float>(1);
   int* d_status = cv.take<int>(1);
   long long* d_inst_begin = cv.take<long long>(2);
-  const int cap_m = 4 * nrows + 1024;
-  unsigned long long* d_rlist_m = cv.take<unsigned long long>(cap_m);
   unsigned long long* d_rcount = cv.take<unsigned long long>(2);
-  unsigned long long* d_mref = cv.take<unsigned long long>(nrows);
-  int* d_need_m = cv.take<int>(nrows);
-  if (!d_need_m)
+  int* d_mcount = cv.take<int>(nrows);
+  long long* d_mslot = cv.take<long long>((size_t)nrows * kMaxSlots);
+  if (!d_mslot)
     return na_fail(DSC_E_INVAL, "needs more than %zu bytes of working memory (the fixed maximum) for %d beamlets",
                    kNoAllocBytes, nrows);
 
@@ -241,8 +238,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   for (int i = 0; i < 3; ++i) { I.c1d[i] = model->c1[i]; I.c2d[i] = model->c2[i]; }
   NA_CU(cudaMemcpyAsync(d_inst, &I, sizeof(DInst), cudaMemcpyHostToDevice, s));
   NA_CU(cudaMemsetAsync(d_rcount, 0, sizeof(unsigned long long) * 2, s));
-  NA_CU(cudaMemsetAsync(d_mref, 0, sizeof(unsigned long long) * nrows, s));
-  NA_CU(cudaMemsetAsync(d_need_m, 0, sizeof(int) * nrows, s));
+  NA_CU(cudaMemsetAsync(d_mcount, 0, sizeof(int) * nrows, s));
   for (int b = 0, row = 0; b < nbeams; ++b) {
     DBeam D{};
     D.inst = 0;
@@ -365,11 +361,10 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.value_dtype = DSC_VALUE_F32;
   cp.slot = d_slot;
   cp.rlist_u = d_rlist_u;
-  cp.rlist_m = d_rlist_m;
   cp.rcount = d_rcount;
-  cp.need_m = d_need_m;
+  cp.mcount = d_mcount;
+  cp.mslot = d_mslot;
   cp.cap_u = cap_u;
-  cp.cap_m = cap_m;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
   k_tile_map<<<256, 256, 0, s>>>(d_item_off, n_items_dev, n_cand, d_tile_item0, d_tile_first);
   NA_LAUNCH();
@@ -394,15 +389,11 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   rp.tau = cp.tau;
   rp.tau_d = opts->rel_threshold;
   rp.rlist_u = d_rlist_u;
-  rp.rlist_m = d_rlist_m;
   rp.rcount = d_rcount;
   rp.cap_u = cap_u;
-  rp.cap_m = cap_m;
-  rp.mref = d_mref;
-  rp.need_m = d_need_m;
+  rp.mcount = d_mcount;
+  rp.mslot = d_mslot;
   rp.tile_cnt = d_tile_cnt;
-  k_refine_max<<<refine_blocks(cap_m), kRefineThreads, 0, s>>>(rp);
-  NA_LAUNCH();
   k_refine<<<refine_blocks(cap_u), kRefineThreads, 0, s>>>(rp);
   NA_LAUNCH();
   st = na_scan(d_tile_cnt, nullptr, n_tiles, d_scan, d_tile_off, s, n_tiles);

@@ -10,10 +10,12 @@
 // listed pair is evaluated again in FP64 from the same inputs: the voxel
 // centre, the beamlet frame and entry point (FP64 from the set-up), the
 // row's depth table (Section 2.2) and the beam model as given, Eq. 2 with the
-// profile's erf pair (Eq. 3), a warp per pair with the twelve tails spread
-// over twelve lanes (the kernels are a single short wave: their time is one
-// pair's FP64 latency).  Row maxima come first (k_refine_max), then the
-// keep decisions against tau * M_j in FP64 (k_refine).  The refined value is
+// profile's erf pair (Eq. 3).  One kernel, a warp per listed pair: the warp
+// evaluates the pair and its row's near-maximum candidates (the row maximum
+// M_j in FP64), two pairs at a time in half-warps, the twelve tails of a pair
+// spread over twelve lanes, and decides against tau * M_j in FP64.  The
+// kernel is a single short wave: its time is a few pairs' FP64 latency.  The
+// refined value is
 // written back, and where its FP32 rounding falls on the other side of the
 // compaction's FP32 threshold it is set to that threshold (kept) or one ulp
 // below it (dropped), a change no larger than the gap between the FP32 and
@@ -39,13 +41,13 @@ __device__ double tail2(int profile, double y) {
   return erfc(y / kSqrt2);                               // Gaussian: s = c3
 }
 
-// D for the pair (row R, voxel col) in FP64, one warp per pair: every lane
-// forms the geometry, depth and beam model; lanes 0..11 take one tail each
-// (term i = lane / 4; lanes 4i, 4i+1: X at y1, y2; 4i+2, 4i+3: Z), and the
-// sum of Eq. 3 is formed from the shuffled tails.  The result is valid in
-// every lane.
-__device__ double eval_pair64_warp(const DRow& R, const DInst& G, const DBeam& B, const float* tab, int col,
-                                   int lane) {
+// D for the pair (row R, voxel col) in FP64, one half-warp per pair: every
+// lane forms the geometry, depth and beam model; sub-lanes 0..11 take one
+// tail each (term i = sub / 4; 4i, 4i+1: X at y1, y2; 4i+2, 4i+3: Z), and
+// the sum of Eq. 3 is formed from the tails shuffled within the half.  The
+// result is valid in every lane of the half; both halves must call together.
+__device__ double eval_pair64_half(const DRow& R, const DInst& G, const DBeam& B, const float* tab, int col,
+                                   int sub) {
   const long long nxy = (long long)G.nx * G.ny;
   const int iz = (int)(col / nxy);
   const int rem = (int)(col - (long long)iz * nxy);
@@ -88,9 +90,9 @@ __device__ double eval_pair64_warp(const DRow& R, const DInst& G, const DBeam& B
   // this lane's tail: 2 G(y) with y1 = (|x| - h) / s, y2 = (|x| + h) / s,
   // 2 G(y) = 2 - 2 G(-y) for y < 0 (the tails never cancel)
   double v = 0.0;
-  if (lane < 12) {
-    const int i = lane >> 2;
-    const bool zax = (lane & 2) != 0, second = (lane & 1) != 0;
+  if (sub < 12) {
+    const int i = sub >> 2;
+    const bool zax = (sub & 2) != 0, second = (sub & 1) != 0;
     const double side = zax ? B.b : B.a;
     const double h = 0.5 * G.c2d[i] * side * t / B.sad;             // c2 a_t / 2 (b_t for Z)
     const double sc = G.profile == 1 ? c3[i] / kSqrt2 : (G.profile == 2 ? c3[i] * kSqrt3OverPi : c3[i]);
@@ -101,8 +103,8 @@ __device__ double eval_pair64_warp(const DRow& R, const DInst& G, const DBeam& B
   double F = 0.0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const double X = __shfl_sync(0xffffffffu, v, 4 * i) - __shfl_sync(0xffffffffu, v, 4 * i + 1);
-    const double Z = __shfl_sync(0xffffffffu, v, 4 * i + 2) - __shfl_sync(0xffffffffu, v, 4 * i + 3);
+    const double X = __shfl_sync(0xffffffffu, v, 4 * i, 16) - __shfl_sync(0xffffffffu, v, 4 * i + 1, 16);
+    const double Z = __shfl_sync(0xffffffffu, v, 4 * i + 2, 16) - __shfl_sync(0xffffffffu, v, 4 * i + 3, 16);
     F += 0.25 * G.c1d[i] * X * Z;
   }
   if (!(t > 0.0)) return 0.0;
@@ -111,57 +113,46 @@ __device__ double eval_pair64_warp(const DRow& R, const DInst& G, const DBeam& B
   return T * q * q * F;
 }
 
-__device__ double refined(const RefineParams& P, unsigned long long entry, long long* p_out, int* row_out,
-                          int lane) {
-  const long long p = (long long)(entry & ((1ull << kRefineRowShift) - 1ull));
-  const int r = (int)(entry >> kRefineRowShift);
-  const DRow& R = P.rows[r];
-  *p_out = p;
-  *row_out = r;
-  return eval_pair64_warp(R, P.inst[R.inst], P.beams[R.beam], P.tables + (size_t)r * P.table_stride, P.cols[p],
-                          lane);
-}
-
 }  // namespace
 
-// FP64 row maxima over the listed near-maximum pairs, a warp per pair
-// (atomicMax on the bits of a non-negative double orders like the value)
-__global__ void __launch_bounds__(kRefineThreads) k_refine_max(RefineParams P) {
-  const int lane = threadIdx.x & 31;
-  const unsigned long long n = min(P.rcount[1], (unsigned long long)P.cap_m);
-  const unsigned long long warps = (unsigned long long)gridDim.x * (kRefineThreads / 32);
-  for (unsigned long long e = blockIdx.x * (unsigned long long)(kRefineThreads / 32) + (threadIdx.x >> 5); e < n;
-       e += warps) {
-    const unsigned long long entry = P.rlist_m[e];
-    if (!P.need_m[(int)(entry >> kRefineRowShift)]) continue;   // no keep decision of the row waits for it
-    long long p;
-    int r;
-    const double D = refined(P, entry, &p, &r, lane);
-    if (lane == 0) atomicMax(P.mref + r, (unsigned long long)__double_as_longlong(fmax(D, 0.0)));
-  }
-}
-
-// keep decisions of the listed pairs in FP64, a warp per pair; the value
-// written back makes the compaction's FP32 test agree, and kept pairs join
-// their tile's count
+// keep decisions of the listed pairs in FP64, a warp per pair.  The warp
+// evaluates the pair and its row's near-maximum candidates, takes M_j as the
+// largest of the latter, and decides D >= tau M_j; the value written back
+// makes the compaction's FP32 test agree, and kept pairs join their tile's
+// count.  A row whose near-maximum candidates overflowed its slots keeps the
+// FP32 decision.
 __global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams P) {
   constexpr float kTiny = 1.40129846e-45f;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, half = lane >> 4, sub = lane & 15;
   const unsigned long long n = min(P.rcount[0], (unsigned long long)P.cap_u);
   const unsigned long long warps = (unsigned long long)gridDim.x * (kRefineThreads / 32);
   for (unsigned long long e = blockIdx.x * (unsigned long long)(kRefineThreads / 32) + (threadIdx.x >> 5); e < n;
        e += warps) {
-    long long p;
-    int r;
-    const double D = refined(P, P.rlist_u[e], &p, &r, lane);
+    const unsigned long long entry = P.rlist_u[e];
+    const long long p = (long long)(entry & ((1ull << kRefineRowShift) - 1ull));
+    const int r = (int)(entry >> kRefineRowShift);
+    const DRow& R = P.rows[r];
+    const DInst& G = P.inst[R.inst];
+    const DBeam& B = P.beams[R.beam];
+    const float* tab = P.tables + (size_t)r * P.table_stride;
+    const int mc = P.mcount[r];
+    const int total = 1 + min(mc, kMaxSlots);         // the pair, then the row's near-maximum candidates
+    double own = 0.0, M = 0.0;
+    for (int j0 = 0; j0 < total; j0 += 2) {           // warp-uniform
+      const int j = j0 + half;
+      const long long q = (j == 0 || j >= total) ? p : P.mslot[(size_t)r * kMaxSlots + j - 1];
+      const double D = eval_pair64_half(R, G, B, tab, P.cols[q], sub);
+      const double d0 = __shfl_sync(0xffffffffu, D, 0), d1 = __shfl_sync(0xffffffffu, D, 16);
+      if (j0 == 0) own = d0; else M = fmax(M, d0);
+      if (j0 + 1 < total) M = fmax(M, d1);
+    }
     if (lane != 0) continue;
     const float thr1 = fmaxf(P.tau * __uint_as_float(P.row_max[r]), kTiny);   // the compaction's FP32 threshold
-    const double M = __longlong_as_double((long long)P.mref[r]);
     float v;
     bool keep;
-    if (M > 0.0) {
-      keep = D > 0.0 && D >= P.tau_d * M;
-      v = __double2float_rn(D);
+    if (mc >= 1 && mc <= kMaxSlots && M > 0.0) {
+      keep = own > 0.0 && own >= P.tau_d * M;
+      v = __double2float_rn(own);
       if (keep && v < thr1) v = thr1;
       if (!keep && v >= thr1) v = __uint_as_float(__float_as_uint(thr1) - 1u);   // thr1 > smallest denormal
     } else {                                                            // no FP64 maximum: FP32 decides
