@@ -680,6 +680,9 @@ static dsc_status refine_launch(Plan* P, const CompactParams& cp, cudaStream_t s
   rp.mcount = P->d_mcount;
   rp.mslot = P->d_mslot;
   rp.tile_cnt = P->d_tile_cnt;
+  rp.nrows = P->nrows;
+  rp.n_cand = P->n_cand;
+  rp.slot = P->d_slot;
   k_refine<<<refine_blocks(P->cap_u), kRefineThreads, 0, s>>>(rp);
   CHECK_LAUNCH();
   return DSC_OK;
@@ -767,6 +770,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.mcount = P->d_mcount;
   cp.mslot = P->d_mslot;
   cp.cap_u = P->cap_u;
+  cp.nrows = P->nrows;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
   k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((P->n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
   CHECK_LAUNCH();
@@ -1017,6 +1021,7 @@ static dsc_status check_status(dsc_result* r) {
   int st = 0;
   CU(cudaEventSynchronize(r->done));
   CU(cudaMemcpy(&st, r->out->slot.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & kStatusIndex) return fail(DSC_E_CUDA, "a kernel found an index out of range (status %d); the result is invalid", st);
   if (st) return fail(DSC_E_TIMEOUT, "a bounded device wait expired (status %d); the result is invalid", st);
   return DSC_OK;
 }

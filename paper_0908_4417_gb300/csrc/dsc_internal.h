@@ -114,7 +114,7 @@ struct OutSlot {
   unsigned* row_max;       // per row, float bits
   long long* row_cand;     // per row
   long long* inst_begin;   // per instance: first output slot; [ninst] = total
-  int* status;             // nonzero when a bounded device wait expired
+  int* status;             // nonzero: kStatusWait (a bounded device wait expired) or kStatusIndex
   unsigned long long* refine;  // [2] pairs listed for the FP64 re-evaluation: near a threshold, near a row maximum
 };
 
@@ -149,6 +149,7 @@ struct CompactParams {
   int* mcount;                    // per row: near-maximum candidates seen
   long long* mslot;               // per row: kMaxSlots candidate indices
   int cap_u;
+  int nrows;
   float inv_tau_m;                // (1 - kRefineDelta) / tau (infinite for tau = 0)
 };
 
@@ -158,6 +159,11 @@ constexpr int kRefineRowShift = 40;
 __host__ __device__ __forceinline__ unsigned long long refine_entry(long long p, int row) {
   return ((unsigned long long)row << kRefineRowShift) | (unsigned long long)p;
 }
+
+// result status bits: a bounded device wait expired; an index a kernel
+// checks was out of range (the access was skipped)
+constexpr int kStatusWait = 1;
+constexpr int kStatusIndex = 2;
 
 // near-maximum candidates kept per row for its FP64 maximum (more: FP32 decides the row)
 constexpr int kMaxSlots = 4;
@@ -198,6 +204,9 @@ struct RefineParams {
   const int* mcount;              // per row: near-maximum candidates seen
   const long long* mslot;         // per row: kMaxSlots candidate indices
   int* tile_cnt;                  // kept refined pairs are added to their tile's count
+  int nrows;
+  long long n_cand;
+  const OutSlot* slot;            // status of the computation (kStatusIndex)
 };
 
 // process-wide work decomposition (dsc_set_tuning): candidates per work item

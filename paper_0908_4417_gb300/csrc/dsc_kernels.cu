@@ -1143,6 +1143,10 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
         next2 = it2 + 1 < ni ? off[it2 + 1] : n;
       }
       const int r = p.item_row[it2];
+      if ((unsigned)r >= (unsigned)p.nrows) {         // checked: skip and flag
+        atomicOr(p.slot->status, kStatusIndex);
+        continue;
+      }
       const float t1 = fmaxf(p.tau * __uint_as_float(p.row_max[r]), kTiny);
       const float D = K.D[i];
       if (D > t1 * kLo && D < t1 * kHi) {

@@ -365,6 +365,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.mcount = d_mcount;
   cp.mslot = d_mslot;
   cp.cap_u = cap_u;
+  cp.nrows = nrows;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
   k_tile_map<<<256, 256, 0, s>>>(d_item_off, n_items_dev, n_cand, d_tile_item0, d_tile_first);
   NA_LAUNCH();
@@ -394,6 +395,9 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   rp.mcount = d_mcount;
   rp.mslot = d_mslot;
   rp.tile_cnt = d_tile_cnt;
+  rp.nrows = nrows;
+  rp.n_cand = n_cand;
+  rp.slot = d_slot;
   k_refine<<<refine_blocks(cap_u), kRefineThreads, 0, s>>>(rp);
   NA_LAUNCH();
   st = na_scan(d_tile_cnt, nullptr, n_tiles, d_scan, d_tile_off, s, n_tiles);
@@ -411,6 +415,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   NA_LAUNCH();
   NA_CU(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   NA_CU(cudaStreamSynchronize(s));   // the array is free for the next call once this returns
+  if (status & kStatusIndex) return na_fail(DSC_E_CUDA, "a kernel found an index out of range (status %d)", status);
   if (status) return na_fail(DSC_E_TIMEOUT, "a bounded device wait expired (status %d)", status);
   *nnz_out = nnz;
   return DSC_OK;

@@ -64,7 +64,7 @@ __device__ double eval_pair64_half(const DRow& R, const DInst& G, const DBeam& B
   const double s = t - R.tA;
   if (R.n_table > 0 && s > 0.0) {
     const double f = s / G.hd, kf = floor(f);
-    if (kf >= R.n_table - 1) {
+    if (!(kf < R.n_table - 1)) {                     // also a NaN s: the last entry
       d = tab[R.n_table - 1];
     } else {
       const int k = (int)kf;
@@ -74,7 +74,7 @@ __device__ double eval_pair64_half(const DRow& R, const DInst& G, const DBeam& B
   // beam model at d: T and c3_1..3, linearly between rows, the last row beyond
   double T, c3[3];
   double g = d * (G.n_lut - 1) / G.d_max;
-  if (g < 0.0) g = 0.0;
+  if (!(g > 0.0)) g = 0.0;                            // also a NaN depth: the first row
   if (g >= G.n_lut - 1) {
     const float4 r = G.lut_rows[G.n_lut - 1];
     T = r.x; c3[0] = r.y; c3[1] = r.z; c3[2] = r.w;
@@ -131,6 +131,10 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams P) {
     const unsigned long long entry = P.rlist_u[e];
     const long long p = (long long)(entry & ((1ull << kRefineRowShift) - 1ull));
     const int r = (int)(entry >> kRefineRowShift);
+    if (p >= P.n_cand || r >= P.nrows) {              // checked (warp-uniform): skip and flag
+      if (lane == 0) atomicOr(P.slot->status, kStatusIndex);
+      continue;
+    }
     const DRow& R = P.rows[r];
     const DInst& G = P.inst[R.inst];
     const DBeam& B = P.beams[R.beam];
@@ -140,8 +144,14 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams P) {
     double own = 0.0, M = 0.0;
     for (int j0 = 0; j0 < total; j0 += 2) {           // warp-uniform
       const int j = j0 + half;
-      const long long q = (j == 0 || j >= total) ? p : P.mslot[(size_t)r * kMaxSlots + j - 1];
-      const double D = eval_pair64_half(R, G, B, tab, P.cols[q], sub);
+      long long q = (j == 0 || j >= total) ? p : P.mslot[(size_t)r * kMaxSlots + j - 1];
+      int col = 0;
+      if (q >= 0 && q < P.n_cand) col = P.cols[q];
+      if (q < 0 || q >= P.n_cand || col < 0 || (long long)col >= (long long)G.nx * G.ny * G.nz) {
+        atomicOr(P.slot->status, kStatusIndex);     // checked: evaluate the pair itself instead
+        col = P.cols[p];
+      }
+      const double D = eval_pair64_half(R, G, B, tab, col, sub);
       const double d0 = __shfl_sync(0xffffffffu, D, 0), d1 = __shfl_sync(0xffffffffu, D, 16);
       if (j0 == 0) own = d0; else M = fmax(M, d0);
       if (j0 + 1 < total) M = fmax(M, d1);
