@@ -1118,11 +1118,18 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
       nx = next >= n ? kTilePer : (int)min(next - p0, (long long)kTilePer);
     }
     const float D = K.D[i];
-    if (D >= thr1) {
-      keep |= 1u << i;
-      if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
+    if (kCols) {
+      if (D >= thr1) {
+        keep |= 1u << i;
+        if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
+      }
+    } else {
+      // count pass: outside the window (ulo, uhi) the decision D >= thr1 is
+      // D >= uhi; a value inside it is decided after the loop
+      const bool above = D >= uhi;
+      if (above) keep |= 1u << i;
+      if ((D > ulo && !above) || D >= mlo) special |= 1u << i;
     }
-    if (!kCols && ((D > ulo && D < uhi) || D >= mlo)) special |= 1u << i;
   }
   if (!kCols && special) {
     // count pass, candidates near their threshold or their row maximum (rare).
@@ -1151,10 +1158,8 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
       const float D = K.D[i];
       if (D > t1 * kLo && D < t1 * kHi) {
         const unsigned long long e = atomicAdd(p.rcount, 1ull);
-        if (e < (unsigned long long)p.cap_u) {
-          p.rlist_u[e] = refine_entry(pos, r);
-          keep &= ~(1u << i);
-        }
+        if (e < (unsigned long long)p.cap_u) p.rlist_u[e] = refine_entry(pos, r);
+        else if (D >= t1) keep |= 1u << i;            // list full: the FP32 decision
       }
       if (D >= t1 * p.inv_tau_m) {
         atomicAdd(p.rcount + 1, 1ull);
