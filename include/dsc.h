@@ -128,7 +128,11 @@ enum {
 };
 
 typedef struct {
-    double rel_threshold;    /* keep D_ij > 0 with D_ij >= rel_threshold * max_j' D_ij' (row max); >= 0 */
+    double rel_threshold;    /* keep D_ij > 0 with D_ij >= rel_threshold * max_j' D_ij' (row max); >= 0.
+                              * Values are FP32; a value within 1e-5 (relative) of its threshold, and the
+                              * row maximum it is compared with, are evaluated again in FP64 and decided
+                              * there (dsc_get_refine_counts), so every decision farther than about 1e-6
+                              * from the threshold is the one exact arithmetic makes. */
     int32_t value_dtype;     /* DSC_VALUE_F32, or DSC_VALUE_BF16: value / beam_scale[beam] rounded to bf16 */
     double h_frac;           /* depth-table spacing / min voxel side, (0, 1]; the paper uses 1/2 */
     int32_t flags;           /* DSC_FLAG_* */
