@@ -753,7 +753,8 @@ __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, f
   if (PROF == 0) {
     constexpr float kPs = kErfcP * kInvSqrtL;   // p / sqrt(log2 e)
     erfc_parts(rcp2(make_float2(fmaf(kPs, fabsf(x.x), 1.0f), fmaf(kPs, fabsf(x.y), 1.0f))), x, kErfcC2, tp1, e1);
-    erfc_parts(rcp2(__ffma2_rn(f2(kPs), v2, f2(1.0f))), v2, kErfcC2n, tp2n, e2);
+    // scalar FMAs with immediate operands: no packed constant pairs to build
+    erfc_parts(rcp2(make_float2(fmaf(kPs, v2.x, 1.0f), fmaf(kPs, v2.y, 1.0f))), v2, kErfcC2n, tp2n, e2);
   } else {
     e1 = make_float2(ex2_approx(-fabsf(x.x)), ex2_approx(-fabsf(x.y)));
     e2 = make_float2(ex2_approx(-v2.x), ex2_approx(-v2.y));
@@ -768,7 +769,7 @@ __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, f
   // 2 G(y1) = (1 - s) + s tp e, s = +-1 the sign of y1 (its sign bit on 1.0f)
   const float2 sg = make_float2(__uint_as_float((__float_as_uint(x.x) & 0x80000000u) | 0x3f800000u),
                                 __uint_as_float((__float_as_uint(x.y) & 0x80000000u) | 0x3f800000u));
-  const float2 erfc_x = __ffma2_rn(__fmul2_rn(sg, tp1), e1, __ffma2_rn(sg, f2(-1.0f), f2(1.0f)));
+  const float2 erfc_x = __ffma2_rn(__fmul2_rn(sg, tp1), e1, make_float2(1.0f - sg.x, 1.0f - sg.y));   // 1 - s exact
   return __ffma2_rn(tp2n, e2, erfc_x);
 }
 
