@@ -49,6 +49,19 @@ def cleanup(dsc, res, g):
 # ---------------------------------------------------------------------------
 # whole workloads
 # ---------------------------------------------------------------------------
+def test_prostate_full_matrix(dsc):
+    """The benchmark workload in full: every one of the 2304 rows (122 M
+    candidate pairs) against the oracle, structure outside the bands and
+    values within the tolerance."""
+    w = P.prostate_256()
+    csr, res, g = run(dsc, w)
+    orc = O.compute_workload(w)
+    st = compare(gpu_rows(csr, range(w.nrows)), orc, TOL)
+    assert abs(csr.pairs - orc.pairs) <= len(orc.amb_row)
+    print("prostate full", st)
+    cleanup(dsc, res, g)
+
+
 def test_water_32_full(dsc):
     w = P.water_32()
     csr, res, g = run(dsc, w)
