@@ -1,6 +1,7 @@
 """Full-matrix structure survey of the CUDA path against the oracle (GPU).
 
-    python tests/survey_structure.py
+    python tests/survey_structure.py            # every workload below
+    python tests/survey_structure.py --quick    # the 9-field prostate only
 
 For every workload below, the whole CSR is computed through the C ABI and by
 the FP64 oracle, and every row is compared: a column present on one side
@@ -54,8 +55,10 @@ def main():
     O.build()
     torch.cuda.init()
     dsc.lib()
-    ws = [P.prostate_256()] + P.batched(32) + [P.table1_water(c) for c in (1, 4, 7)]
-    ws.append(P.slabs_128(value_dtype=P.VALUE_F32))
+    ws = [P.prostate_256()]
+    if "--quick" not in sys.argv:
+        ws += P.batched(32) + [P.table1_water(c) for c in (1, 4, 7)]
+        ws.append(P.slabs_128(value_dtype=P.VALUE_F32))
     total = sum(survey(dsc, O, w) for w in ws)
     print("bad pairs in total:", total)
     return min(total, 255)
