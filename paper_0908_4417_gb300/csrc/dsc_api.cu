@@ -6,8 +6,8 @@
 // are sized once (two stream-ordered reads of device counts) and cached by
 // the identity of their geometries, beam lists and options; every later
 // computation with the same key replays the whole launch sequence -- set-up,
-// Siddon, enumeration, evaluation, compaction -- as one CUDA graph with no
-// host round trip.  Results own their CSR buffers (stream-ordered pool
+// Siddon, enumeration, evaluation, compaction with its FP64 refinement -- as
+// one CUDA graph with no host round trip.  Results own their CSR buffers (stream-ordered pool
 // allocations) and stay valid after later computations.
 #include "dsc_internal.h"
 #include "../../include/dsc.h"

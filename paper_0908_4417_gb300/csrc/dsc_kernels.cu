@@ -5,17 +5,20 @@
 //   k_count          candidate pairs per work item                        (VOI, Section 2.1)
 //   k_eval           D_ij = T(d) (SAD/t)^2 F(x', d, z')  (persistent)     (Eq. 2-3)
 //   k_beam_scale     per-beam maximum for BF16 storage
-//   k_tile_count     kept entries (D >= tau * row max) per tile of candidates
+//   k_tile_count     kept entries (D >= tau * row max) per tile of candidates;
+//                    lists the values too close to their threshold or row
+//                    maximum for FP32 to decide (k_refine in dsc_refine.cu)
 //   k_tile_write     CSR columns/values of the kept entries, tile by tile
 //   k_row_ptr        CSR row pointers per instance
 //   k_scan_*         device-wide exclusive scans with device-side length
+//   k_tail_probe     a profile's tail as the evaluation computes it (tests)
 //
 // The evaluation is FP32 with compensated (float-float) voxel coordinates:
 // every x-line of voxels gets its s = t - t_A, x' and z' at ix = 0 in
 // float-float, and a candidate at ix adds ix times a float-float slope with
 // FMAs, so position errors stay near ulp(value) instead of ulp(SAD).  FP64 is
-// used only in the per-beamlet set-up and for Siddon's plane-crossing
-// parameters alpha.
+// used only in the per-beamlet set-up, for Siddon's plane-crossing parameters
+// alpha, and in the re-evaluation of the few pairs FP32 cannot decide.
 #include "dsc_internal.h"
 #include "dsc_erfc_coeffs.h"
 
