@@ -2,6 +2,7 @@
 
     python tests/survey_structure.py            # every workload below
     python tests/survey_structure.py --quick    # the 9-field prostate only
+    python tests/survey_structure.py --instances 8   # the first 8 batched instances only
 
 For every workload below, the whole CSR is computed through the C ABI and by
 the FP64 oracle, and every row is compared: a column present on one side
@@ -55,9 +56,10 @@ def main():
     O.build()
     torch.cuda.init()
     dsc.lib()
+    n_inst = int(sys.argv[sys.argv.index("--instances") + 1]) if "--instances" in sys.argv else 32
     ws = [P.prostate_256()]
     if "--quick" not in sys.argv:
-        ws += P.batched(32) + [P.table1_water(c) for c in (1, 4, 7)]
+        ws += P.batched(32)[:n_inst] + [P.table1_water(c) for c in (1, 4, 7)]
         ws.append(P.slabs_128(value_dtype=P.VALUE_F32))
     total = sum(survey(dsc, O, w) for w in ws)
     print("bad pairs in total:", total)
