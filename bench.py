@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--instances", type=int, default=32, help="batched: re-plan instances")
     p.add_argument("--requests", type=int, default=64, help="serving: requests")
     p.add_argument("--rate", type=float, default=4.0, help="serving: mean Poisson arrival rate (1/s)")
+    p.add_argument("--stages", action="store_true",
+                   help="per-stage device times of W + K whole computations of the workload, one JSON line "
+                        "(no tuning, oracle or end-to-end legs: a short program for kernel profilers)")
     return p.parse_args()
 
 
@@ -769,6 +772,38 @@ def run_superposition(args):
     print(json.dumps(line), flush=True)
 
 
+def run_stages(args):
+    """W + K whole computations of the named workload through the C ABI, each
+    with the library's per-stage CUDA events; prints the median stage times.
+    Short and deterministic in its launches, so it serves as the program a
+    kernel profiler captures."""
+    import torch
+    from paper_0908_4417_gb300 import build as B
+    B.build()
+    from paper_0908_4417_gb300 import dsc, phantoms as P
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    sp = stream.cuda_stream
+    w = P.get(args.workload)
+    g = dsc.geometry_from_workload(w, sp)
+    opts = dsc.compute_opts(w.tau, w.value_dtype, w.h_frac, dsc.DSC_FLAG_TIMING)
+    times = []
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup + args.steps):
+            r = dsc.dsc_compute_dij(g, opts, sp)
+            dsc.dsc_result_wait(r)
+            if k >= args.warmup:
+                times.append(dsc.dsc_get_stage_times(r))
+            v = dsc.dsc_get_csr(r, False)
+            pairs, nnz = int(v.pairs), int(v.nnz)
+            dsc.dsc_release_result(r)
+    dsc.dsc_destroy_geometry(g)
+    med = {k: round(statistics.median(t[k] for t in times), 4) for k in times[0]} if times else {}
+    print(json.dumps({"workload": w.name, "pairs": pairs, "nnz": nnz, "steps": args.steps, "stage_ms": med}),
+          flush=True)
+
+
 def run_table1(args):
     """The paper's Table 1 water sweep (Section 3.1) as a second workload:
     five coplanar 10 x 10 cm beams on a 30 cm water cube, voxels 0.50-0.25 cm,
@@ -830,6 +865,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.stages:
+        run_stages(args)
     elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "serving":

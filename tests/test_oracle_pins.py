@@ -301,6 +301,181 @@ def test_inverse_square_and_voi_in_vacuum():
     assert 1.2 < expect[cols].max() / expect[cols].min()        # the factor really varies
 
 
+# ---------------------------------------------------------------------------
+# the sigma cutoff (the 32^3 water workload's "lateral cutoff 3 sigma"):
+# half-width a_t/2 + k c3^(1)(d) on each lateral axis, inclusive
+# ---------------------------------------------------------------------------
+_C3_FLAT = (1.7, 4.1, 9.3)       # three distinct widths, so a term mix-up moves the edge
+
+
+def _flat_model(c3=_C3_FLAT, T=0.8, cutoff_mode=P.CUTOFF_SIGMA, k=2.5):
+    """A beam model whose table is the same at every depth: T and c3 do not
+    depend on d, so the cutoff's half-width is a closed form of t alone."""
+    lut = np.empty((256, 4), np.float32)
+    lut[:, 0] = T
+    lut[:, 1:] = c3
+    return P.Model(lut=lut, d_max=300.0, c1=(0.6, 0.3, 0.1), c2=(1, 1, 1), cutoff_mode=cutoff_mode, cutoff_k=k)
+
+
+def _central_beamlet_frame(g, gantry, sad):
+    """t, x', z' of every voxel centre for the single beamlet through the
+    isocentre (0, 0, 0), written out for gantry 0 (source at -y, x' = x,
+    z' = z) and gantry 90 (source at +x, x' = y, z' = z)."""
+    x, y, z = g.voxel_centres()
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    if gantry == 0.0:
+        return Y + sad, X, Z
+    assert gantry == 90.0
+    return sad - X, Y, Z
+
+
+def _sigma_margin(t, xp, zp, a, b, sad, k, c3_1):
+    return np.minimum(a * t / (2 * sad) + k * c3_1 - np.abs(xp), b * t / (2 * sad) + k * c3_1 - np.abs(zp))
+
+
+@pytest.mark.parametrize("gantry", [0.0, 90.0])
+def test_sigma_cutoff_candidate_set_closed_form(gantry):
+    """Candidates are exactly the voxel centres with |x'| <= a_t/2 + k c3_1 and
+    |z'| <= b_t/2 + k c3_1 (a_t = a t/SAD), whatever the density: the table is
+    flat, so the half-width depends on t alone.  The test also checks that it
+    would see the plausible slips: c3 of term 2 or 3 in place of term 1, a
+    dropped a_t/2, k applied to a_t/2 too, and a and b exchanged."""
+    sad, a, b, k = 100.0, 6.0, 3.5, 2.5
+    m = _flat_model(k=k)
+    if gantry == 0.0:
+        g = P.centred_grid(20, 30, 16, 1.3, 1.3, 1.3, centre=(0.37, 0.0, 0.21))
+    else:
+        g = P.centred_grid(30, 20, 16, 1.3, 1.3, 1.3, centre=(0.0, 0.37, 0.21))
+    rho = P.random_grid_density(17, g.shape, 0.2, 1.8)
+    beam = P.Beam(gantry, sad, (0.0, 0.0, 0.0), a, b, 1, 1)
+    r = O.compute(g, rho, m, [beam], tau=0.0)
+    t, xp, zp = _central_beamlet_frame(g, gantry, sad)
+    margin = _sigma_margin(t, xp, zp, a, b, sad, k, _C3_FLAT[0])
+    assert np.abs(margin).min() > 1e-4                      # no centre near the edge
+    expect = np.flatnonzero((margin >= 0).ravel())
+    assert r.pairs == expect.size > 0
+    cols, vals = r.row(0)
+    assert np.array_equal(cols, expect)                     # tau = 0: every candidate has D > 0
+    assert r.amb_col.size == 0                                    # nothing within 1e-3 mm of the edge
+    slips = {
+        "c3 of term 2": _sigma_margin(t, xp, zp, a, b, sad, k, _C3_FLAT[1]),
+        "c3 of term 3": _sigma_margin(t, xp, zp, a, b, sad, k, _C3_FLAT[2]),
+        "no a_t/2": np.minimum(k * _C3_FLAT[0] - np.abs(xp), k * _C3_FLAT[0] - np.abs(zp)),
+        "k on a_t/2": _sigma_margin(t, xp, zp, k * a, k * b, sad, k, _C3_FLAT[0]),
+        "a and b exchanged": _sigma_margin(t, xp, zp, b, a, sad, k, _C3_FLAT[0]),
+    }
+    for name, s in slips.items():
+        assert np.count_nonzero((s >= 0) != (margin >= 0)) > 20, name
+
+
+def test_sigma_cutoff_depends_on_depth_through_c3():
+    """With c3_1 growing with depth the half-width follows c3_1(d): in vacuum
+    d = 0, so the edge is a_t/2 + k c3_1(0); in uniform density 0.5 the depth
+    at O' is 0.5 (t - t_A) and the edge is a_t/2 + k c3_1(d) with c3_1 read
+    off the table by linear interpolation (written out here)."""
+    sad, a, b, k = 100.0, 4.0, 4.0, 2.0
+    lut = np.empty((256, 4), np.float32)
+    dd = np.linspace(0.0, 300.0, 256)
+    lut[:, 0] = 1.0
+    lut[:, 1] = 1.0 + 0.05 * dd          # c3_1 grows 0.05 mm per mm of depth
+    lut[:, 2] = 3.0
+    lut[:, 3] = 8.0
+    m = P.Model(lut=lut, d_max=300.0, c1=(0.9, 0.08, 0.02), c2=(1, 1, 1), cutoff_mode=P.CUTOFF_SIGMA,
+                cutoff_k=k)
+    g = P.centred_grid(24, 40, 6, 1.1, 1.1, 1.1, centre=(0.23, 0.0, 0.17))
+    beam = P.Beam(0.0, sad, (0.0, 0.0, 0.0), a, b, 1, 1)
+    t, xp, zp = _central_beamlet_frame(g, 0.0, sad)
+    tA = g.origin[1] + sad
+    for rho0 in (0.0, 0.5):
+        rho = np.full(g.shape, rho0, np.float32)
+        d = float(np.float32(rho0)) * np.clip(t - tA, 0.0, None)
+        gi = d * 255 / 300.0
+        kk = np.floor(gi).astype(int)
+        c3_1 = lut[kk, 1].astype(np.float64) + (gi - kk) * (lut[kk + 1, 1].astype(np.float64) - lut[kk, 1])
+        margin = np.minimum(a * t / (2 * sad) + k * c3_1 - np.abs(xp), b * t / (2 * sad) + k * c3_1 - np.abs(zp))
+        band = np.abs(margin) <= 1e-3
+        r = O.compute(g, rho, m, [beam], tau=0.0)
+        keep = (margin >= 0).ravel()
+        amb = r.ambiguous(0)
+        assert amb == set(np.flatnonzero(band.ravel()).tolist())
+        cols, _ = r.row(0)
+        got = np.zeros(g.nvox, bool)
+        got[cols] = True
+        assert np.array_equal(got[~band.ravel()], keep[~band.ravel()])
+    # the two densities give different candidate sets (the depth matters)
+    assert r.pairs != O.compute(g, np.zeros(g.shape, np.float32), m, [beam], tau=0.0).pairs
+
+
+def test_cutoff_band_is_classified_kind_2():
+    """A voxel centre placed 4e-4 mm inside the x edge and another 4e-4 mm
+    outside the z edge are both in the cutoff band (kind 2); the band is
+    exactly the set of centres whose closed-form margin is within 1e-3 mm."""
+    sad, a, k = 100.0, 6.0, 2.5
+    g = P.centred_grid(20, 30, 16, 1.3, 1.3, 1.3, centre=(0.37, 0.0, 0.21))
+    t, xp, zp = _central_beamlet_frame(g, 0.0, sad)
+    # choose c3_1 so the x edge passes 4e-4 mm beyond centre (ix=15, iy=10,
+    # iz=8), then b so the z edge stops 4e-4 mm short of centre (iz=12,
+    # iy=20, ix=10); the other lateral coordinate is well inside at both
+    X1, T1 = xp[8, 10, 15], t[8, 10, 15]
+    c3_1 = (abs(X1) + 4e-4 - a * T1 / (2 * sad)) / k
+    Z2, T2 = zp[12, 20, 10], t[12, 20, 10]
+    b = (abs(Z2) - 4e-4 - k * c3_1) * 2 * sad / T2
+    assert c3_1 > 0 and b > 0
+    c3 = (c3_1, 2.0 * c3_1 + 1.0, 4.0 * c3_1 + 3.0)
+    m = _flat_model(c3=c3, k=k)
+    c3_1 = float(np.float32(c3_1))                       # the table stores FP32
+    beam = P.Beam(0.0, sad, (0.0, 0.0, 0.0), a, b, 1, 1)
+    rho = np.ones(g.shape, np.float32)
+    r = O.compute(g, rho, m, [beam], tau=0.0)
+    margin = _sigma_margin(t, xp, zp, a, b, sad, k, c3_1)
+    assert np.all(np.abs(np.abs(margin) - 1e-3) > 1e-6)    # the band's own edge is clear
+    band = np.flatnonzero((np.abs(margin) <= 1e-3).ravel())
+    c_in = (8 * g.ny + 10) * g.nx + 15
+    c_out = (12 * g.ny + 20) * g.nx + 10
+    assert margin.ravel()[c_in] == pytest.approx(4e-4, abs=1e-6)
+    assert margin.ravel()[c_out] == pytest.approx(-4e-4, abs=1e-6)
+    kinds = dict(zip(r.amb_col.tolist(), r.amb_kind.tolist()))
+    assert set(kinds) == set(band.tolist()) and {c_in, c_out} <= set(kinds)
+    assert set(kinds.values()) == {2}
+    cols, _ = r.row(0)
+    assert c_in in cols and c_out not in cols
+
+
+@pytest.mark.parametrize("side", [+1, -1])
+def test_threshold_band_is_classified_kind_1(side):
+    """Vacuum and widths -> 0: inside the beamlet D = T(0) (SAD/t)^2 sum(c1),
+    so the row maximum sits at the smallest t and D/M = (t_min/t)^2.  With
+    tau = (t_min/t_k)^2 (1 + side 5e-7) the voxels inside the beamlet at
+    depth row k are within 1e-6 of the threshold (kind 1): dropped for side
+    +1, kept for side -1; no other pair is in a band."""
+    lut = P.synthetic_model().lut.copy()
+    lut[:, 1:] = 1e-6
+    m = P.Model(lut=lut, d_max=300.0, c1=(0.6, 0.3, 0.05), c2=(1, 1, 1), cutoff_mode=P.CUTOFF_VOI6)
+    sad, a, b = 100.0, 8.0, 5.0
+    g = P.centred_grid(16, 24, 12, 1.3, 1.3, 1.3, centre=(0.37, 0.0, 0.21))
+    rho = np.zeros(g.shape, np.float32)
+    beam = P.Beam(0.0, sad, (0.0, 0.0, 0.0), a, b, 1, 1)
+    t, xp, zp = _central_beamlet_frame(g, 0.0, sad)
+    inside = (np.abs(xp) < a * t / (2 * sad)) & (np.abs(zp) < b * t / (2 * sad))
+    cand = (np.abs(xp) <= 3 * a * t / sad) & (np.abs(zp) <= 3 * b * t / sad)
+    ty = t[0, :, 0]
+    t_min, kk = ty[0], 13
+    assert inside[:, 0, :].any() and inside[:, kk, :].any()
+    tau = (t_min / ty[kk]) ** 2 * (1 + side * 5e-7)
+    r = O.compute(g, rho, m, [beam], tau=tau)
+    M = float(lut[0, 0]) * (sad / t_min) ** 2 * sum(m.c1)
+    assert r.row_max[0] == pytest.approx(M, rel=1e-12)
+    assert r.pairs == int(cand.sum())
+    row_k = np.zeros(g.shape, bool)
+    row_k[:, kk, :] = True
+    band = np.flatnonzero((inside & row_k).ravel())
+    kinds = dict(zip(r.amb_col.tolist(), r.amb_kind.tolist()))
+    assert set(kinds) == set(band.tolist()) and set(kinds.values()) == {1}
+    kept = inside & ((t < ty[kk]) | ((t == ty[kk]) & (side < 0)))
+    cols, _ = r.row(0)
+    assert np.array_equal(cols, np.flatnonzero(kept.ravel()))
+
+
 def test_water_depth_at_projection_point():
     """Water, widths c3 -> 0: inside the divergent beamlet D (t/SAD)^2 / sum(c1) equals
     T at the geometric depth of O' (the projection of P on the axis), t - t_A, for every
