@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define DSC_ABI_VERSION 2
+#define DSC_ABI_VERSION 3
 
 typedef enum {
     DSC_OK = 0,
@@ -58,7 +58,10 @@ typedef enum {
     DSC_E_TIMEOUT = 5,       /* a bounded device-side wait expired (status word set by a kernel) */
     DSC_E_STATE = 6,         /* call not valid in the handle's current state */
     DSC_E_NOTFOUND = 7,      /* unknown request id */
-    DSC_E_BUSY = 8           /* result not ready (non-blocking poll) */
+    DSC_E_BUSY = 8,          /* result not ready (non-blocking poll) */
+    DSC_W_INEXACT = 9        /* completed, outputs valid, but some keep decisions within 1e-5 of the
+                              * threshold were taken in FP32 (more such pairs than the FP64 list holds);
+                              * only dsc_compute_dij_noalloc returns it */
 } dsc_status;
 
 typedef struct dsc_geometry dsc_geometry;   /* device-resident density + beam model + beam list */
@@ -275,10 +278,14 @@ dsc_status dsc_get_depth_tables(dsc_result* res, float* out, int64_t cap, int32_
 /* Pairs of the computation (all instances of its launch) whose decision the
  * FP32 values could not settle and that were evaluated again in FP64: values
  * within 1e-5 (relative) of their row's threshold (the keep decision), and
- * within 1e-5 of their row's maximum (the maximum itself).  Pairs beyond the
- * list's capacity (about n_cand / 1024), and rows with more than 4 pairs near
- * their maximum, were decided in FP32. */
-dsc_status dsc_get_refine_counts(dsc_result* res, int64_t* near_threshold, int64_t* near_max);
+ * within 1e-5 of their row's maximum (the maximum itself; a row with more
+ * than 4 of them is scanned in full for its FP64 maximum).  fp32_decided
+ * (may be NULL): pairs within 1e-5 of their threshold beyond the FP64 list's
+ * capacity (at least 65536 and n_cand / 1024), whose decision stayed FP32;
+ * 0 means every decision farther than about 1e-6 from the threshold is the
+ * one exact arithmetic makes. */
+dsc_status dsc_get_refine_counts(dsc_result* res, int64_t* near_threshold, int64_t* near_max,
+                                 int64_t* fp32_decided);
 /* Per row: max D over the row's candidates and the candidate count. */
 dsc_status dsc_get_row_stats(dsc_result* res, float* row_max, int64_t* row_cand);
 /* Milliseconds per stage (needs DSC_FLAG_TIMING): [set-up + item scan, Siddon
@@ -326,11 +333,17 @@ void dsc_server_destroy(dsc_server* srv);
  * 8 bytes per candidate pair) exceeds it fails with DSC_E_INVAL and says so
  * in dsc_last_error(); so does an output capacity below the kept count
  * (nothing is written to the outputs then).  The first call on a device
- * looks up the array's device address; make that first call before any
- * stream capture.  Every call reuses the array from the start: calls whose
- * device work overlaps race and must not be issued (keep them on one stream,
- * one host thread at a time).  The call allocates no device or host memory
- * on its success path. */
+ * looks up the array's device address (kept for the life of the process: do
+ * not use the library across a reset of the device's primary context); make
+ * that first call before any stream capture.  The call waits for its own
+ * work: it synchronises `stream` several times, and on every return, error
+ * or not, no work of its own is left on the GPU.  Every call reuses the
+ * array from the start: calls whose device work overlapped would race, so
+ * the library runs one call at a time per process (a second host thread
+ * waits for the first call to return).  The call allocates no
+ * device or host memory.  DSC_W_INEXACT: the CSR is complete and valid, but
+ * some keep decisions within 1e-5 of the threshold stayed FP32 (how many is
+ * in dsc_last_error()). */
 dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const float* density_dev, const dsc_fspb_model* model,
                                    const dsc_beam_desc* beams, int32_t nbeams, const dsc_compute_opts* opts,
                                    int64_t* row_ptr_dev, int32_t* col_dev, float* val_dev, int64_t capacity,

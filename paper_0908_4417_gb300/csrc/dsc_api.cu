@@ -53,13 +53,14 @@ __global__ void k_beamlet_dot(const long long*, const long long*, const int*, co
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
-__global__ void k_copy_stats(const unsigned*, const long long*, int, const unsigned long long*, const OutSlot*);
+__global__ void k_copy_stats(const unsigned*, const long long*, int, const unsigned long long*, int, const OutSlot*);
 __global__ void k_scan_partial(const int*, const long long*, long long, long long*);
 __global__ void k_scan_blocks(long long*);
 __global__ void k_scan_final(const int*, const long long*, long long, const long long*, long long*);
 __global__ void k_scan_small(const int*, const long long*, long long, long long*);
 __global__ void k_tail_probe(int, const float*, long long, float*, float*);
 __global__ void k_refine(RefineParams);
+__global__ void k_refine_rowmax(RefineParams);
 }  // namespace dsc
 
 using namespace dsc;
@@ -241,9 +242,11 @@ struct Plan {
   int* d_counter = nullptr;
   // decisions the FP32 values cannot settle (the count pass lists them)
   unsigned long long* d_rlist_u = nullptr;   // near a threshold: cap_u entries
-  unsigned long long* d_rcount = nullptr;    // [2] listed counts
+  unsigned long long* d_rcount = nullptr;    // [3] listed counts
   int* d_mcount = nullptr;                   // per row: near-maximum candidates seen
   long long* d_mslot = nullptr;              // per row: kMaxSlots near-maximum candidates
+  int* d_ovf_rows = nullptr;                 // rows that overflowed their near-maximum slots
+  double* d_row_max64 = nullptr;             // per row: FP64 maximum of an overflowing row
   int cap_u = 0;
   OutSlot* d_slot = nullptr;         // output pointers of the computation in flight
   cudaGraphExec_t graph = nullptr;   // the captured launch sequence
@@ -267,8 +270,8 @@ struct Plan {
   ~Plan() {
     free_scratch();
     void* ps[] = {d_inst, d_beams, d_rows, d_row_items, d_row_item_base, d_tables, d_row_max, d_row_cand, d_scan,
-                  d_counter, d_slot, d_rcount, d_mcount, d_mslot};
-    release_after(last_done, device, ps, 14);
+                  d_counter, d_slot, d_rcount, d_mcount, d_mslot, d_ovf_rows, d_row_max64};
+    release_after(last_done, device, ps, 16);
     if (last_done) cudaEventDestroy(last_done);
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
@@ -333,6 +336,7 @@ extern "C" const char* dsc_status_str(dsc_status s) {
     case DSC_E_STATE: return "invalid state";
     case DSC_E_NOTFOUND: return "not found";
     case DSC_E_BUSY: return "not ready";
+    case DSC_W_INEXACT: return "complete, some decisions near the threshold in FP32";
   }
   return "unknown status";
 }
@@ -573,8 +577,10 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_scan, kScanBlocks + 1, s));
   TRY(dalloc(&P->d_counter, 4, s));
   if (P->nrows >= (1 << 24)) return fail(DSC_E_INVAL, "too many beamlets in one launch (%d)", P->nrows);
-  TRY(dalloc(&P->d_rcount, 2, s));
+  TRY(dalloc(&P->d_rcount, 3, s));
   TRY(dalloc(&P->d_mcount, P->nrows, s));
+  TRY(dalloc(&P->d_ovf_rows, P->nrows, s));
+  TRY(dalloc(&P->d_row_max64, P->nrows, s));
   TRY(dalloc(&P->d_mslot, (size_t)P->nrows * kMaxSlots, s));
   TRY(dalloc(&P->d_slot, 1, s));
   CU(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
@@ -678,11 +684,17 @@ static dsc_status refine_launch(Plan* P, const CompactParams& cp, cudaStream_t s
   rp.rcount = P->d_rcount;
   rp.cap_u = P->cap_u;
   rp.mcount = P->d_mcount;
+  rp.ovf_rows = P->d_ovf_rows;
+  rp.row_max64 = P->d_row_max64;
+  rp.row_item_base = P->d_row_item_base;
+  rp.inv_tau_m = cp.inv_tau_m;
   rp.mslot = P->d_mslot;
   rp.tile_cnt = P->d_tile_cnt;
   rp.nrows = P->nrows;
   rp.n_cand = P->n_cand;
   rp.slot = P->d_slot;
+  k_refine_rowmax<<<kRefineRowmaxBlocks, kRefineThreads, 0, s>>>(rp);
+  CHECK_LAUNCH();
   k_refine<<<refine_blocks(P->cap_u), kRefineThreads, 0, s>>>(rp);
   CHECK_LAUNCH();
   return DSC_OK;
@@ -695,7 +707,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   CU(cudaMemsetAsync(P->d_row_max, 0, sizeof(unsigned) * P->nrows, s));
   CU(cudaMemsetAsync(P->d_row_cand, 0, sizeof(long long) * P->nrows, s));
   CU(cudaMemsetAsync(P->d_counter, 0, sizeof(int) * 4, s));
-  CU(cudaMemsetAsync(P->d_rcount, 0, sizeof(unsigned long long) * 2, s));
+  CU(cudaMemsetAsync(P->d_rcount, 0, sizeof(unsigned long long) * 3, s));
   CU(cudaMemsetAsync(P->d_mcount, 0, sizeof(int) * P->nrows, s));
   // a1: beamlet frames, entry/exit, VOI box, work items
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
@@ -769,6 +781,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.rcount = P->d_rcount;
   cp.mcount = P->d_mcount;
   cp.mslot = P->d_mslot;
+  cp.ovf_rows = P->d_ovf_rows;
   cp.cap_u = P->cap_u;
   cp.nrows = P->nrows;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
@@ -789,7 +802,8 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
                                                         P->rp_off[k], k, k == P->ninst - 1, P->d_slot);
     CHECK_LAUNCH();
   }
-  k_copy_stats<<<(P->nrows + 255) / 256, 256, 0, s>>>(P->d_row_max, P->d_row_cand, P->nrows, P->d_rcount, P->d_slot);
+  k_copy_stats<<<(P->nrows + 255) / 256, 256, 0, s>>>(P->d_row_max, P->d_row_cand, P->nrows, P->d_rcount, P->cap_u,
+                                                     P->d_slot);
   CHECK_LAUNCH();
   TRY(record(ev, 7, s));
   if (nk) *nk = (int)(g_launches.load() - k0);
@@ -816,7 +830,7 @@ static dsc_status alloc_outputs(Plan* P, cudaStream_t s, std::shared_ptr<OutBufs
   TRY(dalloc(&q.row_max, P->nrows, s));
   TRY(dalloc(&q.row_cand, P->nrows, s));
   TRY(dalloc(&q.inst_begin, P->ninst + 1, s));
-  TRY(dalloc(&q.refine, 2, s));
+  TRY(dalloc(&q.refine, 3, s));
   TRY(dalloc(&q.status, 1, s));
   CU(cudaMemsetAsync(q.status, 0, sizeof(int), s));
   if (P->opts.value_dtype != DSC_VALUE_BF16) {
@@ -1178,20 +1192,22 @@ extern "C" dsc_status dsc_probe_tail(int32_t profile, const float* y_dev, int64_
   if (profile < 0 || profile > 2) return fail(DSC_E_INVAL, "profile: DSC_PROFILE_ERF, _LAPLACE or _LOGISTIC");
   if (n < 0 || (n > 0 && (!y_dev || !ours_dev || !cuda_dev))) return fail(DSC_E_INVAL, "null argument or n < 0");
   if (n == 0) return DSC_OK;
-  const long long threads = (n + 1) / 2;
+  const long long threads = (n + 3) / 4;
   k_tail_probe<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(profile, y_dev, n, ours_dev,
                                                                                     cuda_dev);
   CHECK_LAUNCH();
   return DSC_OK;
 }
 
-extern "C" dsc_status dsc_get_refine_counts(dsc_result* r, int64_t* near_threshold, int64_t* near_max) {
+extern "C" dsc_status dsc_get_refine_counts(dsc_result* r, int64_t* near_threshold, int64_t* near_max,
+                                            int64_t* fp32_decided) {
   if (!r || !near_threshold || !near_max) return fail(DSC_E_INVAL, "null argument");
   CU(cudaEventSynchronize(r->done));
-  unsigned long long c[2] = {0, 0};
+  unsigned long long c[3] = {0, 0, 0};
   CU(cudaMemcpy(c, r->out->slot.refine, sizeof c, cudaMemcpyDeviceToHost));
   *near_threshold = (int64_t)c[0];
   *near_max = (int64_t)c[1];
+  if (fp32_decided) *fp32_decided = (int64_t)c[2];
   return DSC_OK;
 }
 

@@ -11,7 +11,10 @@
 namespace dsc {
 
 constexpr int kEvalThreads = 128;     // threads per CTA of the evaluation / compaction kernels
-constexpr int kMaxLinesPerItem = 512;  // x-lines handled by one work item (multiple of kEvalThreads)
+#ifndef DSC_LINES_PER_ITEM
+#define DSC_LINES_PER_ITEM 256
+#endif
+constexpr int kMaxLinesPerItem = DSC_LINES_PER_ITEM;  // x-lines handled by one work item (multiple of kEvalThreads)
 constexpr int kWindow = 2048;         // candidates mapped to lines per pass of an item
 constexpr int kSiddonThreads = 32;    // lanes per ray (one warp, one CTA) of the depth-table kernels
 constexpr int kScanBlocks = 1024;     // blocks of the device-wide scan
@@ -115,7 +118,8 @@ struct OutSlot {
   long long* row_cand;     // per row
   long long* inst_begin;   // per instance: first output slot; [ninst] = total
   int* status;             // nonzero: kStatusWait (a bounded device wait expired) or kStatusIndex
-  unsigned long long* refine;  // [2] pairs listed for the FP64 re-evaluation: near a threshold, near a row maximum
+  unsigned long long* refine;  // [3] pairs listed for the FP64 re-evaluation: near a threshold, near a row
+                               // maximum; near-threshold pairs past the list's capacity (decided in FP32)
 };
 
 constexpr int kTilePer = 8;                       // candidates per thread of the compaction
@@ -145,9 +149,11 @@ struct CompactParams {
   // candidates within kRefineDelta of their row maximum go to their row's
   // slots (kMaxSlots per row)
   unsigned long long* rlist_u;   // refine_entry(candidate, row)
-  unsigned long long* rcount;     // [0] entries listed in rlist_u, [1] near-maximum candidates (may exceed capacities)
+  unsigned long long* rcount;     // [0] entries listed in rlist_u, [1] near-maximum candidates (may exceed capacities),
+                                  // [2] rows with more than kMaxSlots near-maximum candidates (listed in ovf_rows)
   int* mcount;                    // per row: near-maximum candidates seen
   long long* mslot;               // per row: kMaxSlots candidate indices
+  int* ovf_rows;                  // rows whose near-maximum candidates overflowed their slots (nrows entries)
   int cap_u;
   int nrows;
   float inv_tau_m;                // (1 - kRefineDelta) / tau (infinite for tau = 0)
@@ -165,7 +171,8 @@ __host__ __device__ __forceinline__ unsigned long long refine_entry(long long p,
 constexpr int kStatusWait = 1;
 constexpr int kStatusIndex = 2;
 
-// near-maximum candidates kept per row for its FP64 maximum (more: FP32 decides the row)
+// near-maximum candidates kept per row for its FP64 maximum; a row with more
+// is listed, and k_refine_rowmax takes its FP64 maximum from a scan of the row
 constexpr int kMaxSlots = 4;
 
 // relative window around a threshold (and below a row maximum) inside which
@@ -178,6 +185,8 @@ constexpr float kRefineDelta = 1e-5f;
 // the warp evaluates its pair and its row's near-maximum candidates, two
 // pairs at a time in half-warps
 constexpr int kRefineThreads = 128;
+// CTAs of k_refine_rowmax (grid-stride over the rows that overflowed their slots)
+constexpr int kRefineRowmaxBlocks = 152;
 inline unsigned refine_blocks(int cap) {
   const int warps = cap < 4096 ? cap : 4096;
   return (unsigned)((warps + kRefineThreads / 32 - 1) / (kRefineThreads / 32));
@@ -203,6 +212,10 @@ struct RefineParams {
   int cap_u;
   const int* mcount;              // per row: near-maximum candidates seen
   const long long* mslot;         // per row: kMaxSlots candidate indices
+  const int* ovf_rows;            // rows with more than kMaxSlots near-maximum candidates (rcount[2] of them)
+  double* row_max64;              // per row: FP64 maximum of an overflowing row (k_refine_rowmax)
+  const long long* row_item_base; // nrows + 1: first work item of each row
+  float inv_tau_m;                // (1 - kRefineDelta) / tau: a value >= thr * this is near its row maximum
   int* tile_cnt;                  // kept refined pairs are added to their tile's count
   int nrows;
   long long n_cand;

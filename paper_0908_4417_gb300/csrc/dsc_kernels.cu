@@ -455,14 +455,36 @@ __global__ void __launch_bounds__(kSiddonThreads) k_trilinear_table(const DInst*
 // x-lines of a work item
 // ---------------------------------------------------------------------------
 constexpr int kTabSmem = 1024;   // depth-table entries a work item stages in shared memory
+#ifndef DSC_LUT_SMEM
+#define DSC_LUT_SMEM 256
+#endif
+// beam-model table rows a CTA stages in shared memory (as (row, difference)
+// pairs) beside the depth table; 0: read through L1
+constexpr int kLutSmem = DSC_LUT_SMEM;
+#if DSC_LUT_SMEM
+#define SMLUT sm.lut
+#else
+#define SMLUT nullptr
+#endif
+#ifndef DSC_EVAL_HALVES
+#define DSC_EVAL_HALVES 0
+#endif
+// The x-lines of a work item, rebased on the item's candidate index jj (0 at
+// the item's first candidate): candidate jj on line li has ix = ixb + jj,
+// column colb + jj and depth coordinate sfb + jj * dsf, so a candidate needs
+// its line index and three loads.
 struct LineSm {
-  float4 sx[kMaxLinesPerItem];        // t, x' hi, x' lo, z' hi at ix = 0
-  float4 zc[kMaxLinesPerItem];        // z' lo, first ix (int bits), nx (iy + ny iz) (int bits), unused
-  long long sf[kMaxLinesPerItem];     // s at ix = 0 in fixed point (units of h 2^-32)
-  int off[kMaxLinesPerItem + 1];
+  float4 sx[kMaxLinesPerItem];        // t at ix = 0, colb (int bits), x' hi, z' hi at ix = 0
+  float4 zc[kMaxLinesPerItem];        // x' lo, z' lo at ix = 0, ixb (int bits), unused
+  long long sf[kMaxLinesPerItem];     // sfb: s of candidate jj = 0 (fixed point, units of h 2^-32)
+  unsigned short map[kWindow];        // line of each candidate of the window (8-byte aligned)
+  int off[kMaxLinesPerItem + 1];      // first candidate (jj) of each line
   int wscan[kEvalThreads / 32];
-  unsigned short map[kWindow];
   float tab[kTabSmem];                // the row's depth table, when it fits
+#if DSC_LUT_SMEM
+  float4 lut[2 * kLutSmem];           // the instance's beam-model table, when it fits
+  int lut_inst;                       // instance whose table is in lut (-1: none)
+#endif
   long long item;
   int row;
   int nl;
@@ -573,30 +595,35 @@ __device__ __forceinline__ int item_nlines(const DRow& R, long long chunk, int& 
   return min(R.lpc, nlines - l0);
 }
 
-// set up all lines of an item in shared memory (each thread takes lines t and
-// t + kEvalThreads); returns the candidate count
+// set up all lines of an item in shared memory (each thread takes kMaxLinesPerItem /
+// kEvalThreads consecutive lines), rebased on the item's candidate index;
+// returns the candidate count
 __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, long long chunk) {
   constexpr int per = kMaxLinesPerItem / kEvalThreads;
   int l0;
   int nl = item_nlines(R, chunk, l0);
   int t = threadIdx.x;
-  int len[per];
+  int len[per], lo[per], cb[per];
+  long long sfl[per];
   int mine = 0;
   const float inv_nyb = line_inv(R);
 #pragma unroll
   for (int q = 0; q < per; ++q) {
     int li = t * per + q;             // consecutive lines per thread keep the scan order
     len[q] = 0;
+    lo[q] = 0;
+    cb[q] = 0;
+    sfl[q] = 0;
     if (li < nl) {
       int iy, iz;
       line_yz(R, l0 + li, inv_nyb, iy, iz);
       ff s0, x0, z0;
       line_base(R, iy, iz, s0, x0, z0);
-      int lo;
-      len[q] = line_interval(R, mode, nx, iy, iz, lo);
-      sm.sx[li] = make_float4(R.tA_f + s0.hi, x0.hi, x0.lo, z0.hi);
-      sm.zc[li] = make_float4(z0.lo, __int_as_float(lo), __int_as_float(nx * (iy + ny * iz)), 0.0f);
-      sm.sf[li] = R.sfx0 + (long long)iy * R.sfx_s[1] + (long long)iz * R.sfx_s[2];
+      len[q] = line_interval(R, mode, nx, iy, iz, lo[q]);
+      cb[q] = nx * (iy + ny * iz);
+      sfl[q] = R.sfx0 + (long long)iy * R.sfx_s[1] + (long long)iz * R.sfx_s[2];
+      sm.sx[li] = make_float4(R.tA_f + s0.hi, 0.0f, x0.hi, z0.hi);
+      sm.zc[li] = make_float4(x0.lo, z0.lo, 0.0f, 0.0f);
     }
     mine += len[q];
   }
@@ -605,7 +632,13 @@ __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, l
 #pragma unroll
   for (int q = 0; q < per; ++q) {
     int li = t * per + q;
-    if (li < nl) sm.off[li] = excl;
+    if (li < nl) {
+      const int ixb = lo[q] - excl;   // ix of candidate jj on this line: ixb + jj
+      sm.off[li] = excl;
+      reinterpret_cast<int*>(&sm.sx[li])[1] = cb[q] + ixb;
+      reinterpret_cast<int*>(&sm.zc[li])[2] = ixb;
+      sm.sf[li] = sfl[q] + (long long)ixb * R.sfx_s[0];
+    }
     excl += len[q];
   }
   if (t == 0) { sm.nl = nl; sm.off[nl] = tot; }
@@ -700,7 +733,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (lane == 0) item_cand[item] = cnt;
+    // items are padded to a multiple of 4 candidates (the evaluation writes
+    // aligned groups of 4; padding slots hold -1, never kept)
+    if (lane == 0) item_cand[item] = (cnt + 3) & ~3;
   }
 }
 
@@ -717,6 +752,39 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 constexpr float kInvSqrtL = 0.83255461115769775635f;   // 1 / sqrt(log2 e)
 
 __device__ __forceinline__ float2 rcp2(float2 d) { return make_float2(rcp_approx(d.x), rcp_approx(d.y)); }
+
+// the reciprocals t = 1/(1 + p |v|) of the four erfc denominators of a
+// profile term (a: X and Z at y1, b: at y2), by product inversion:
+//   DSC_SHARED_RCP 2: one reciprocal r = 1/(q_x q_y) of the product of all
+//     four, q = da db; 1/q_x = r q_y, 1/q_y = r q_x, then 1/da = (1/q) db and
+//     1/db = (1/q) da (one rcp.approx and six multiplications);
+//   DSC_SHARED_RCP 1: r = 1/q per axis, 1/da = r db, 1/db = r da (two
+//     rcp.approx and three packed multiplications);
+//   0: four rcp.approx.
+// Each result is within a few ulp.  The denominators lie in [1, 1 + p |v|];
+// the host's limits on the model and the geometry keep the products finite.
+#ifndef DSC_SHARED_RCP
+#define DSC_SHARED_RCP 0
+#endif
+constexpr float kPs = kErfcP * kInvSqrtL;   // p / sqrt(log2 e)
+__device__ __forceinline__ void erfc_recips(float2 a, float2 b, float2& ta, float2& tb) {
+  const float2 da = make_float2(fmaf(kPs, fabsf(a.x), 1.0f), fmaf(kPs, fabsf(a.y), 1.0f));
+  const float2 db = make_float2(fmaf(kPs, fabsf(b.x), 1.0f), fmaf(kPs, fabsf(b.y), 1.0f));
+#if DSC_SHARED_RCP == 2
+  const float2 q = __fmul2_rn(da, db);
+  const float r = rcp_approx(__fmul_rn(q.x, q.y));
+  const float2 rq = make_float2(__fmul_rn(r, q.y), __fmul_rn(r, q.x));
+  ta = __fmul2_rn(rq, db);
+  tb = __fmul2_rn(rq, da);
+#elif DSC_SHARED_RCP == 1
+  const float2 rq = rcp2(__fmul2_rn(da, db));
+  ta = __fmul2_rn(rq, db);
+  tb = __fmul2_rn(rq, da);
+#else
+  ta = rcp2(da);
+  tb = rcp2(db);
+#endif
+}
 
 // given t = 1/(1 + p |v|): tp = t P(t) (P from `c`: the
 // fitted coefficients, or their negatives for -t P(t)), e = 2^(-v^2);
@@ -754,10 +822,11 @@ __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, f
   const float2 v2 = __fmul2_rn(__ffma2_rn(f2(c2h), abt, axz), f2(inv_s));  // y2, scaled (>= 0)
   float2 tp1, e1, tp2n, e2;
   if (PROF == 0) {
-    constexpr float kPs = kErfcP * kInvSqrtL;   // p / sqrt(log2 e)
-    erfc_parts(rcp2(make_float2(fmaf(kPs, fabsf(x.x), 1.0f), fmaf(kPs, fabsf(x.y), 1.0f))), x, kErfcC2, tp1, e1);
-    // scalar FMAs with immediate operands: no packed constant pairs to build
-    erfc_parts(rcp2(make_float2(fmaf(kPs, v2.x, 1.0f), fmaf(kPs, v2.y, 1.0f))), v2, kErfcC2n, tp2n, e2);
+    // denominators as scalar FMAs with immediate operands: no packed constant pairs to build
+    float2 t1, t2;
+    erfc_recips(x, v2, t1, t2);
+    erfc_parts(t1, x, kErfcC2, tp1, e1);
+    erfc_parts(t2, v2, kErfcC2n, tp2n, e2);
   } else {
     e1 = make_float2(ex2_approx(-fabsf(x.x)), ex2_approx(-fabsf(x.y)));
     e2 = make_float2(ex2_approx(-v2.x), ex2_approx(-v2.y));
@@ -769,10 +838,14 @@ __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, f
       tp2n = rcp2(__ffma2_rn(e2, f2(-0.5f), f2(-0.5f)));
     }
   }
-  // 2 G(y1) = (1 - s) + s tp e, s = +-1 the sign of y1 (its sign bit on 1.0f)
-  const float2 sg = make_float2(__uint_as_float((__float_as_uint(x.x) & 0x80000000u) | 0x3f800000u),
-                                __uint_as_float((__float_as_uint(x.y) & 0x80000000u) | 0x3f800000u));
-  const float2 erfc_x = __ffma2_rn(__fmul2_rn(sg, tp1), e1, make_float2(1.0f - sg.x, 1.0f - sg.y));   // 1 - s exact
+  // 2 G(y1) = (1 - s) + s tp e, s = +-1 the sign of y1: s tp is tp with y1's
+  // sign bit (tp >= 0), and 1 - s (0 or 2) is that sign bit shifted onto
+  // 2.0f's exponent bit -- integer operations, exact, off the FMA pipe
+  const unsigned sbx = __float_as_uint(x.x) & 0x80000000u, sby = __float_as_uint(x.y) & 0x80000000u;
+  const float2 stp1 = make_float2(__uint_as_float(__float_as_uint(tp1.x) | sbx),
+                                  __uint_as_float(__float_as_uint(tp1.y) | sby));
+  const float2 oms = make_float2(__uint_as_float(sbx >> 1), __uint_as_float(sby >> 1));
+  const float2 erfc_x = __ffma2_rn(stp1, e1, oms);
   return __ffma2_rn(tp2n, e2, erfc_x);
 }
 
@@ -780,8 +853,8 @@ __device__ __forceinline__ float2 erf_pair2(float c2h, float c2hn, float2 abt, f
 struct RowConst {
   long long dsf;         // slope of s per ix, fixed point (units of h 2^-32)
   float tx;              // slope of t per ix
-  float Xxh, Xxl, Zxh, Zxl;
-  float a_sad, b_sad;
+  float2 XZh, XZl;       // slopes of (x', z') per ix, float-float
+  float2 ab_sad;         // (a, b) / SAD
   int n_table;
   const float* tab;      // the row's depth table
   const float4* lut;     // beam-model table
@@ -790,22 +863,29 @@ struct RowConst {
   float cutoff_k;
 };
 
-// D for candidate ix of a line; returns -1 outside the SIGMA cutoff.  TS: the
-// row's depth table is staged in shared memory at stab
-template <int PROF, bool TS>
-__device__ __forceinline__ float eval_pair(const RowConst& C, int ix, float4 sx, float zlo, long long sf, int mode,
-                                           const float* stab) {
-  // t, x', z' of voxel ix on the line (compensated FP32 for x', z')
-  const float fi = (float)ix;
-  const float t = fmaf(fi, C.tx, sx.x);
-  const float xp = fmaf(fi, C.Xxh, sx.y) + fmaf(fi, C.Xxl, sx.z);
-  const float zp = fmaf(fi, C.Zxh, sx.w) + fmaf(fi, C.Zxl, zlo);
+// FP32 value of a small non-negative integer (n < 2^23) without a conversion
+// instruction: 2^23 + n is exact in FP32 and its bits are 0x4B000000 + n
+__device__ __forceinline__ float small_int_to_float(int n) {
+  return __fsub_rn(__int_as_float(0x4B000000 + n), 8388608.0f);
+}
+
+// D for a candidate at ix = fi of a line (A, B: the line's records, s: its
+// depth coordinate); -1 outside the sigma cutoff (SIG).  TS: the row's depth
+// table is staged in shared memory at stab
+template <int PROF, bool TS, bool SIG>
+__device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 A, float4 B, long long s,
+                                           const float* stab, const float4* slut) {
+  // t, x', z' of voxel ix on the line (compensated FP32 for x', z': hi and
+  // lo slopes times ix, added once)
+  const float t = fmaf(fi, C.tx, A.x);
+  const float2 fii = f2(fi);
+  const float2 xz = __fadd2_rn(__ffma2_rn(fii, C.XZh, make_float2(A.z, A.w)),
+                               __ffma2_rn(fii, C.XZl, make_float2(B.x, B.y)));
 
   // radiological depth at O' (Section 2.2): linear interpolation of the
   // table; s = t - tA in fixed point (units of h 2^-32): the cell is the
   // high word, the fraction the low word.  s <= 0 gives depth 0 (cell 0,
   // fraction 0), past the last entry the last value.
-  const long long s = sf + (long long)ix * C.dsf;
   const int cell = (int)(s >> 32);
   const bool neg = s <= 0;
   const bool past = cell >= C.n_table - 1;
@@ -815,19 +895,28 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, int ix, float4 sx,
   const float d = past ? d1 : fmaf(f, d1 - d0, d0);
 
   // beam-model table: T(d), c3_1..3(d) / K (K = Prof<PROF>::K, folded in
-  // when the table was built); past the end, the last row
-  float g = fmaxf(d * C.lut_scale, 0.0f);   // also maps a NaN depth to 0
-  float kl = fminf(floorf(g), C.lut_last - 1.0f);
-  float w = fminf(g - kl, 1.0f);
-  int kk = (int)kl;
-  const float4 A = __ldg(C.lut + 2 * kk), dA = __ldg(C.lut + 2 * kk + 1);   // row kk, row kk+1 - row kk
-  const float2 Pxy = __ffma2_rn(f2(w), make_float2(dA.x, dA.y), make_float2(A.x, A.y));
-  const float2 Pzw = __ffma2_rn(f2(w), make_float2(dA.z, dA.w), make_float2(A.z, A.w));
+  // when the table was built); past the end, the last row.  g is clamped to
+  // [0, last] (a NaN depth maps to 0), so its floor comes from 2^23 + g
+  // rounded to the nearest integer, one down where that is above g.
+  const float g = fminf(fmaxf(d * C.lut_scale, 0.0f), C.lut_last);
+  float kl = __fsub_rn(__fadd_rn(g, 8388608.0f), 8388608.0f);
+  kl = kl > g ? kl - 1.0f : kl;
+  kl = fminf(kl, C.lut_last - 1.0f);
+  const float w = g - kl;                  // in [0, 1], exact
+  const int kk = __float_as_int(__fadd_rn(kl, 8388608.0f)) - 0x4B000000;
+#if DSC_LUT_SMEM
+  const float4 L = TS ? slut[2 * kk] : __ldg(C.lut + 2 * kk);                 // row kk
+  const float4 dL = TS ? slut[2 * kk + 1] : __ldg(C.lut + 2 * kk + 1);        // row kk+1 - row kk
+#else
+  const float4 L = __ldg(C.lut + 2 * kk), dL = __ldg(C.lut + 2 * kk + 1);   // row kk, row kk+1 - row kk
+#endif
+  const float2 Pxy = __ffma2_rn(f2(w), make_float2(dL.x, dL.y), make_float2(L.x, L.y));
+  const float2 Pzw = __ffma2_rn(f2(w), make_float2(dL.z, dL.w), make_float2(L.z, L.w));
 
-  const float2 abt = __fmul2_rn(make_float2(C.a_sad, C.b_sad), f2(t));   // (a_t, b_t)
-  const float2 axz = make_float2(fabsf(xp), fabsf(zp));
+  const float2 abt = __fmul2_rn(C.ab_sad, f2(t));   // (a_t, b_t)
+  const float2 axz = make_float2(fabsf(xz.x), fabsf(xz.y));
   constexpr float kK = Prof<PROF>::K;
-  if (mode == 1) {
+  if (SIG) {
     float lim = (C.cutoff_k * kK) * Pxy.y;   // cutoff_k c3_1
     if (axz.x > fmaf(0.5f, abt.x, lim) || axz.y > fmaf(0.5f, abt.y, lim)) return -1.0f;
   }
@@ -851,10 +940,9 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, int ix, float4 sx,
 __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const DInst& G, const float* tab) {
   C.dsf = R.sfx_s[0];
   C.tx = R.Ss[0].hi;
-  C.Xxh = R.Xs[0].hi; C.Xxl = R.Xs[0].lo;
-  C.Zxh = R.Zs[0].hi; C.Zxl = R.Zs[0].lo;
-  C.a_sad = R.a_sad;
-  C.b_sad = R.b_sad;
+  C.XZh = make_float2(R.Xs[0].hi, R.Zs[0].hi);
+  C.XZl = make_float2(R.Xs[0].lo, R.Zs[0].lo);
+  C.ab_sad = make_float2(R.a_sad, R.b_sad);
   C.n_table = R.n_table;
   C.tab = tab;
   C.lut = G.lut;
@@ -865,43 +953,89 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
   C.cutoff_k = G.cutoff_k;
 }
 
-// the candidates [w0, w0 + wl) of an item's window, profile PROF (block-uniform);
-// TS: the depth table is in sm.tab
-template <int PROF, bool TS>
+// the candidates [w0, w0 + wl) of an item's window (the item's first wl
+// candidates past w0 are real; the rest of the last group of 4 is padding),
+// profile PROF (block-uniform); TS: the depth table is in sm.tab; SIG: the
+// sigma cutoff.  Each thread takes groups of 4 consecutive candidates (two
+// independent chains at a time), writes their values and columns with
+// aligned 8-byte stores (the item starts on a multiple of 4), and keeps the
+// maximum and, with SIG, the count inside the cutoff.
+template <int PROF, bool TS, bool SIG>
 __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm, int w0, int wl, float* out,
-                                            int* outc, int mode, float& vmax, int& valid) {
-  // two candidates per thread per pass: independent chains to interleave
-  for (int j = threadIdx.x; j < wl; j += 2 * kEvalThreads) {
-    const int j2 = j + kEvalThreads;
-    const bool two = j2 < wl;
-    const int jb = two ? j2 : j;
-    int li = min((int)sm.map[j], sm.nl - 1);
-    int lb = min((int)sm.map[jb], sm.nl - 1);
-    float4 sx = sm.sx[li], sxb = sm.sx[lb];
-    float4 zc = sm.zc[li], zcb = sm.zc[lb];
-    int ix = __float_as_int(zc.y) + (w0 + j - sm.off[li]);
-    int ixb = __float_as_int(zcb.y) + (w0 + jb - sm.off[lb]);
-    float D = eval_pair<PROF, TS>(C, ix, sx, zc.x, sm.sf[li], mode, sm.tab);
-    float Db = eval_pair<PROF, TS>(C, ixb, sxb, zcb.x, sm.sf[lb], mode, sm.tab);
-    out[w0 + j] = D;
-    outc[w0 + j] = __float_as_int(zc.z) + ix;
-    vmax = fmaxf(vmax, D);
-    if (mode == 1) valid += D >= 0.0f;
-    if (two) {
-      out[w0 + jb] = Db;
-      outc[w0 + jb] = __float_as_int(zcb.z) + ixb;
-      vmax = fmaxf(vmax, Db);
-      if (mode == 1) valid += Db >= 0.0f;
+                                            int* outc, float& vmax, int& valid) {
+  const int nl1 = sm.nl - 1;
+  for (int g = 4 * (int)threadIdx.x; g < wl; g += 4 * kEvalThreads) {
+    const int jj = w0 + g;                              // item-relative index of the group's first candidate
+    const uint2 mm = *reinterpret_cast<const uint2*>(sm.map + g);
+#if DSC_EVAL_HALVES
+    // two candidates at a time (two independent chains), stored as 8 bytes each
+#pragma unroll
+    for (int h = 0; h < 4; h += 2) {
+      float D[2];
+      int col[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const unsigned m16 = h ? mm.y : mm.x;
+        const int li = min((int)(q ? (m16 >> 16) : (m16 & 0xffffu)), nl1);   // entries past wl: any line will do
+        const float4 A = sm.sx[li], B = sm.zc[li];
+        const int j = jj + h + q;
+        const int ix = __float_as_int(B.z) + j;
+        col[q] = __float_as_int(A.y) + j;
+        D[q] = eval_pair<PROF, TS, SIG>(C, small_int_to_float(ix), A, B, sm.sf[li] + (long long)j * C.dsf, sm.tab,
+                                        SMLUT);
+        if (g + h + q >= wl) { D[q] = -1.0f; col[q] = 0; }   // padding
+      }
+      *reinterpret_cast<float2*>(out + jj + h) = make_float2(D[0], D[1]);
+      *reinterpret_cast<int2*>(outc + jj + h) = make_int2(col[0], col[1]);
+      vmax = fmaxf(vmax, fmaxf(D[0], D[1]));
+      if (SIG) valid += (D[0] >= 0.0f) + (D[1] >= 0.0f);
     }
+#else
+    const int lidx[4] = {(int)(mm.x & 0xffffu), (int)(mm.x >> 16), (int)(mm.y & 0xffffu), (int)(mm.y >> 16)};
+    float D[4];
+    int col[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int li = min(lidx[k], nl1);                 // entries past wl are stale: any line will do
+      const float4 A = sm.sx[li], B = sm.zc[li];
+      const int j = jj + k;
+      const int ix = __float_as_int(B.z) + j;
+      col[k] = __float_as_int(A.y) + j;
+      D[k] = eval_pair<PROF, TS, SIG>(C, small_int_to_float(ix), A, B, sm.sf[li] + (long long)j * C.dsf, sm.tab,
+                                      SMLUT);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (g + k >= wl) { D[k] = -1.0f; col[k] = 0; }     // padding
+    *reinterpret_cast<float4*>(out + jj) = make_float4(D[0], D[1], D[2], D[3]);
+    *reinterpret_cast<int4*>(outc + jj) = make_int4(col[0], col[1], col[2], col[3]);
+    vmax = fmaxf(vmax, fmaxf(fmaxf(D[0], D[1]), fmaxf(D[2], D[3])));
+#endif
+#if !DSC_EVAL_HALVES
+    if (SIG) valid += (D[0] >= 0.0f) + (D[1] >= 0.0f) + (D[2] >= 0.0f) + (D[3] >= 0.0f);
+#endif
   }
+}
+
+template <int PROF, bool TS>
+__device__ __forceinline__ void eval_window_mode(bool sig, const RowConst& C, const LineSm& sm, int w0, int wl,
+                                                 float* out, int* outc, float& vmax, int& valid) {
+  if (sig) eval_window<PROF, TS, true>(C, sm, w0, wl, out, outc, vmax, valid);
+  else eval_window<PROF, TS, false>(C, sm, w0, wl, out, outc, vmax, valid);
 }
 
 // persistent: CTAs take work items from a queue; every candidate's D goes to
 // vals[item_off[item] + k] and the row maximum is kept with atomicMax on the
 // float bits (D >= 0)
-__global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
+#ifndef DSC_EVAL_MINBLOCKS
+#define DSC_EVAL_MINBLOCKS 8
+#endif
+__global__ void __launch_bounds__(kEvalThreads, DSC_EVAL_MINBLOCKS) k_eval(EvalParams p) {
   __shared__ LineSm sm;
   const long long ni = *p.n_items;
+#if DSC_LUT_SMEM
+  if (threadIdx.x == 0) sm.lut_inst = -1;           // read after the first barrier below
+#endif
   for (;;) {
     if (threadIdx.x == 0) {
       long long it = atomicAdd(p.item_counter, 1);
@@ -915,7 +1049,12 @@ __global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
     const DRow& R = p.rows[row];
     const DInst& G = p.inst[R.inst];
     const int mode = G.cutoff_mode;
+    const bool sig = mode == 1;
     const long long a_off = p.item_off[item];
+#if DSC_LUT_SMEM
+    // read before item_lines' barriers; thread 0 updates it after them
+    const bool lut_stale = sm.lut_inst != R.inst;
+#endif
     const int total = min(item_lines(sm, R, mode, G.nx, G.ny, item - p.row_item_base[row]),
                           (int)(p.item_off[item + 1] - a_off));   // never past the counted range
     RowConst C;
@@ -923,27 +1062,36 @@ __global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
     // the row's depth table into shared memory when it fits (block-uniform);
     // the previous item's readers finished at its closing barrier, and this
     // item's first reader comes after the barrier in item_map
+#if DSC_LUT_SMEM
+    // the depth table and the beam-model table both staged, or neither
+    const bool ts = R.n_table <= kTabSmem && G.n_lut <= kLutSmem;
+    if (ts && lut_stale) {
+      for (int k = threadIdx.x; k < 2 * G.n_lut; k += kEvalThreads) sm.lut[k] = C.lut[k];
+      if (threadIdx.x == 0) sm.lut_inst = R.inst;     // read after the next barrier (item_map)
+    }
+#else
     const bool ts = R.n_table <= kTabSmem;
+#endif
     if (ts)
       for (int k = threadIdx.x; k < R.n_table; k += kEvalThreads) sm.tab[k] = C.tab[k];
     float* out = p.vals + a_off;
     int* outc = p.cols + a_off;
     float vmax = 0.0f;
-    int valid = (mode != 1 && threadIdx.x == 0) ? total : 0;   // outside the sigma cutoff every candidate counts
+    int valid = (!sig && threadIdx.x == 0) ? total : 0;   // outside the sigma cutoff every candidate counts
     for (int w0 = 0; w0 < total; w0 += kWindow) {
       int wl = min(kWindow, total - w0);
       item_map(sm, w0, wl);
       if (ts) {
         switch (G.profile) {
-          case 1: eval_window<1, true>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
-          case 2: eval_window<2, true>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
-          default: eval_window<0, true>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+          case 1: eval_window_mode<1, true>(sig, C, sm, w0, wl, out, outc, vmax, valid); break;
+          case 2: eval_window_mode<2, true>(sig, C, sm, w0, wl, out, outc, vmax, valid); break;
+          default: eval_window_mode<0, true>(sig, C, sm, w0, wl, out, outc, vmax, valid); break;
         }
       } else {
         switch (G.profile) {
-          case 1: eval_window<1, false>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
-          case 2: eval_window<2, false>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
-          default: eval_window<0, false>(C, sm, w0, wl, out, outc, mode, vmax, valid); break;
+          case 1: eval_window_mode<1, false>(sig, C, sm, w0, wl, out, outc, vmax, valid); break;
+          case 2: eval_window_mode<2, false>(sig, C, sm, w0, wl, out, outc, vmax, valid); break;
+          default: eval_window_mode<0, false>(sig, C, sm, w0, wl, out, outc, vmax, valid); break;
         }
       }
       __syncthreads();
@@ -965,32 +1113,45 @@ __global__ void __launch_bounds__(kEvalThreads, 7) k_eval(EvalParams p) {
 // ---------------------------------------------------------------------------
 // the lateral-profile tail T(y), y >= 0 in units of the spread, with the
 // evaluation's own primitives and constants (argument scale K, the fitted
-// erfc, rcp.approx, ex2.approx), two values per thread in packed FP32x2 as
-// erf_pair2 forms them, beside CUDA's own function of the same tail
+// erfc, rcp.approx, ex2.approx), four values per thread in packed FP32x2 as
+// erf_pair2 forms a term's four tails (the same shared reciprocal), beside
+// CUDA's own function of the same tail
 // ---------------------------------------------------------------------------
 template <int PROF>
-__device__ __forceinline__ float2 tail2(float2 y) {
-  const float2 v = __fmul2_rn(y, f2(Prof<PROF>::K));
-  float2 tp, e;
+__device__ __forceinline__ void tail4(float2 ya, float2 yb, float2& ra, float2& rb) {
+  const float2 va = __fmul2_rn(ya, f2(Prof<PROF>::K)), vb = __fmul2_rn(yb, f2(Prof<PROF>::K));
+  float2 tpa, ea, tpb, eb;
   if (PROF == 0) {
-    constexpr float kPs = kErfcP * kInvSqrtL;
-    erfc_parts(rcp2(__ffma2_rn(f2(kPs), v, f2(1.0f))), v, kErfcC2, tp, e);
+    float2 ta, tb;
+    erfc_recips(va, vb, ta, tb);                       // the evaluation's four denominators of a term
+    erfc_parts(ta, va, kErfcC2, tpa, ea);
+    erfc_parts(tb, vb, kErfcC2, tpb, eb);
   } else {
-    e = make_float2(ex2_approx(-v.x), ex2_approx(-v.y));
-    tp = PROF == 1 ? f2(1.0f) : rcp2(__ffma2_rn(e, f2(0.5f), f2(0.5f)));
+    ea = make_float2(ex2_approx(-va.x), ex2_approx(-va.y));
+    eb = make_float2(ex2_approx(-vb.x), ex2_approx(-vb.y));
+    tpa = PROF == 1 ? f2(1.0f) : rcp2(__ffma2_rn(ea, f2(0.5f), f2(0.5f)));
+    tpb = PROF == 1 ? f2(1.0f) : rcp2(__ffma2_rn(eb, f2(0.5f), f2(0.5f)));
   }
-  return __fmul2_rn(tp, e);
+  ra = __fmul2_rn(tpa, ea);
+  rb = __fmul2_rn(tpb, eb);
 }
 
 __global__ void k_tail_probe(int profile, const float* __restrict__ y, long long n, float* __restrict__ ours,
                              float* __restrict__ cuda_ref) {
-  const long long i = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  const long long i = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
   if (i >= n) return;
-  const float2 yy = make_float2(y[i], i + 1 < n ? y[i + 1] : 0.0f);
-  const float2 r = profile == 1 ? tail2<1>(yy) : (profile == 2 ? tail2<2>(yy) : tail2<0>(yy));
-  for (int h = 0; h < 2 && i + h < n; ++h) {
-    const float a = h ? yy.y : yy.x;
-    ours[i + h] = h ? r.y : r.x;
+  float yy[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) yy[h] = i + h < n ? y[i + h] : 0.0f;
+  float2 ra, rb;
+  const float2 ya = make_float2(yy[0], yy[1]), yb = make_float2(yy[2], yy[3]);
+  if (profile == 1) tail4<1>(ya, yb, ra, rb);
+  else if (profile == 2) tail4<2>(ya, yb, ra, rb);
+  else tail4<0>(ya, yb, ra, rb);
+  const float r[4] = {ra.x, ra.y, rb.x, rb.y};
+  for (int h = 0; h < 4 && i + h < n; ++h) {
+    const float a = yy[h];
+    ours[i + h] = r[h];
     float c;
     if (profile == 1) c = expf(-1.41421356237309504880f * a);                     // exp(-sqrt 2 y)
     else if (profile == 2) {
@@ -1141,9 +1302,11 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
     // decision in FP32: it is listed for the FP64 re-evaluation, which adds
     // it to the count if kept, and it leaves this count.  A value within
     // kRefineDelta of the row maximum goes to the row's slots, from which the
-    // re-evaluation takes the FP64 maximum.  A full list leaves the FP32
-    // decision in place.  The item of each position is found again from the
-    // tile's first item.
+    // re-evaluation takes the FP64 maximum; a row with more such values than
+    // slots is listed once, and its FP64 maximum comes from a scan of the row
+    // (k_refine_rowmax).  A full list leaves the FP32 decision in place (and
+    // is counted).  The item of each position is found again from the tile's
+    // first item.
     long long it2 = item0, next2 = p.tile_next[tile];
 #pragma unroll
     for (int i = 0; i < kTilePer; ++i) {              // static positions: K stays in registers
@@ -1168,7 +1331,12 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
       if (D >= t1 * p.inv_tau_m) {
         atomicAdd(p.rcount + 1, 1ull);
         const int k = atomicAdd(p.mcount + r, 1);
-        if (k < kMaxSlots) p.mslot[(size_t)r * kMaxSlots + k] = pos;
+        if (k < kMaxSlots) {
+          p.mslot[(size_t)r * kMaxSlots + k] = pos;
+        } else if (k == kMaxSlots) {                   // the row overflows its slots: list it once
+          const unsigned long long e = atomicAdd(p.rcount + 2, 1ull);
+          if (e < (unsigned long long)p.nrows) p.ovf_rows[e] = r;
+        }
       }
     }
   }
@@ -1307,15 +1475,23 @@ __global__ void k_row_ptr(const long long* __restrict__ row_item_base, const lon
   }
 }
 
-// per-row statistics into the result
+// per-row statistics into the result; refine = {pairs listed near a
+// threshold (within the list's capacity), near-maximum candidates, listed
+// pairs past the capacity (their decision stayed FP32)}
 __global__ void k_copy_stats(const unsigned* __restrict__ row_max, const long long* __restrict__ row_cand, int nrows,
-                             const unsigned long long* __restrict__ rcount, const OutSlot* __restrict__ slot) {
+                             const unsigned long long* __restrict__ rcount, int cap_u,
+                             const OutSlot* __restrict__ slot) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < nrows) {
     slot->row_max[r] = row_max[r];
     slot->row_cand[r] = row_cand[r];
   }
-  if (r < 2 && slot->refine) slot->refine[r] = rcount[r];
+  if (r == 0 && slot->refine) {
+    const unsigned long long cap = (unsigned long long)cap_u, n0 = rcount[0];
+    slot->refine[0] = n0 < cap ? n0 : cap;
+    slot->refine[1] = rcount[1];
+    slot->refine[2] = n0 > cap ? n0 - cap : 0ull;
+  }
 }
 
 // ---------------------------------------------------------------------------

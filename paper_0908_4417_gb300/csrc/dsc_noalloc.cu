@@ -36,6 +36,7 @@ __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_tile_prep(CompactParams);
 __global__ void k_lut_pairs(const float4*, int, int, float4*);
 __global__ void k_refine(RefineParams);
+__global__ void k_refine_rowmax(RefineParams);
 __global__ void k_tile_write(CompactParams, const long long*);
 __global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
                           long long, int, int, long long, int, int, const OutSlot*);
@@ -81,7 +82,9 @@ static dsc_status na_fail(dsc_status s, const char* fmt, ...) {
 
 // Host code cannot use g_noalloc_scratch's name as a device address: it
 // names a host-side shadow.  The device address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current, and is
+// kept for the life of the process (the library is not used across a reset
+// of a device's primary context).
 static dsc_status na_base(unsigned char** base) {
   int dev = 0;
   NA_CU(cudaGetDevice(&dev));
@@ -204,6 +207,16 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   dsc_status st = na_base(&base);
   if (st != DSC_OK) return st;
   std::lock_guard<std::mutex> lk(g_na_mu);   // one host thread at a time carves and launches
+  // Declared after the lock, so it runs before the unlock: once work has been
+  // queued, every return (an error included) first waits for that work, and
+  // the next call cannot reuse the array while this one's kernels still run.
+  struct SyncOnReturn {
+    cudaStream_t s;
+    bool armed;
+    ~SyncOnReturn() {
+      if (armed) cudaStreamSynchronize(s);
+    }
+  } drain{s, false};
 
   Carve cv{base};
   float4* d_lut_rows = cv.take<float4>(model->n);
@@ -222,13 +235,16 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   float* d_scale = cv.take<float>(1);
   int* d_status = cv.take<int>(1);
   long long* d_inst_begin = cv.take<long long>(2);
-  unsigned long long* d_rcount = cv.take<unsigned long long>(2);
+  unsigned long long* d_rcount = cv.take<unsigned long long>(3);
   int* d_mcount = cv.take<int>(nrows);
   long long* d_mslot = cv.take<long long>((size_t)nrows * kMaxSlots);
-  if (!d_mslot)
+  int* d_ovf_rows = cv.take<int>(nrows);
+  double* d_row_max64 = cv.take<double>(nrows);
+  if (!d_row_max64)
     return na_fail(DSC_E_INVAL, "needs more than %zu bytes of working memory (the fixed maximum) for %d beamlets",
                    kNoAllocBytes, nrows);
 
+  drain.armed = true;
   NA_CU(cudaMemcpyAsync(d_lut_rows, model->table4, sizeof(float4) * model->n, cudaMemcpyHostToDevice, s));
   k_lut_pairs<<<(model->n + 127) / 128, 128, 0, s>>>(d_lut_rows, model->n, model->profile, d_lut);
   NA_LAUNCH();
@@ -237,7 +253,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   I.d_max = model->d_max;
   for (int i = 0; i < 3; ++i) { I.c1d[i] = model->c1[i]; I.c2d[i] = model->c2[i]; }
   NA_CU(cudaMemcpyAsync(d_inst, &I, sizeof(DInst), cudaMemcpyHostToDevice, s));
-  NA_CU(cudaMemsetAsync(d_rcount, 0, sizeof(unsigned long long) * 2, s));
+  NA_CU(cudaMemsetAsync(d_rcount, 0, sizeof(unsigned long long) * 3, s));
   NA_CU(cudaMemsetAsync(d_mcount, 0, sizeof(int) * nrows, s));
   for (int b = 0, row = 0; b < nbeams; ++b) {
     DBeam D{};
@@ -364,6 +380,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.rcount = d_rcount;
   cp.mcount = d_mcount;
   cp.mslot = d_mslot;
+  cp.ovf_rows = d_ovf_rows;
   cp.cap_u = cap_u;
   cp.nrows = nrows;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
@@ -394,17 +411,25 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   rp.cap_u = cap_u;
   rp.mcount = d_mcount;
   rp.mslot = d_mslot;
+  rp.ovf_rows = d_ovf_rows;
+  rp.row_max64 = d_row_max64;
+  rp.row_item_base = d_rib;
+  rp.inv_tau_m = cp.inv_tau_m;
   rp.tile_cnt = d_tile_cnt;
   rp.nrows = nrows;
   rp.n_cand = n_cand;
   rp.slot = d_slot;
+  k_refine_rowmax<<<kRefineRowmaxBlocks, kRefineThreads, 0, s>>>(rp);
+  NA_LAUNCH();
   k_refine<<<refine_blocks(cap_u), kRefineThreads, 0, s>>>(rp);
   NA_LAUNCH();
   st = na_scan(d_tile_cnt, nullptr, n_tiles, d_scan, d_tile_off, s, n_tiles);
   if (st != DSC_OK) return st;
   long long nnz = 0;
   int status = 0;
+  unsigned long long listed = 0;
   NA_CU(cudaMemcpyAsync(&nnz, d_tile_off + n_tiles, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  NA_CU(cudaMemcpyAsync(&listed, d_rcount, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   NA_CU(cudaStreamSynchronize(s));
   if (nnz > capacity)
     return na_fail(DSC_E_INVAL, "output capacity %lld < %lld kept entries", (long long)capacity, nnz);
@@ -418,5 +443,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   if (status & kStatusIndex) return na_fail(DSC_E_CUDA, "a kernel found an index out of range (status %d)", status);
   if (status) return na_fail(DSC_E_TIMEOUT, "a bounded device wait expired (status %d)", status);
   *nnz_out = nnz;
+  if (listed > (unsigned long long)cap_u)   // complete, but these decisions stayed FP32
+    return na_fail(DSC_W_INEXACT, "%llu pairs within 1e-5 of their threshold past the FP64 list's %d entries "
+                   "were decided in FP32", listed - (unsigned long long)cap_u, cap_u);
   return DSC_OK;
 }

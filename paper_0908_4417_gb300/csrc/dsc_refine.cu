@@ -115,12 +115,69 @@ __device__ double eval_pair64_half(const DRow& R, const DInst& G, const DBeam& B
 
 }  // namespace
 
+// The FP64 maximum of every row whose near-maximum candidates overflowed its
+// slots (listed by the count pass, rcount[2] of them): one CTA per listed row
+// scans the row's candidates, evaluates each value within kRefineDelta of the
+// row's FP32 maximum again in FP64 (the count pass's own criterion; two pairs
+// per warp at a time, in half-warps) and stores the largest in row_max64.
+// Runs before k_refine, which decides the row's listed pairs against it.
+__global__ void __launch_bounds__(kRefineThreads) k_refine_rowmax(RefineParams P) {
+  constexpr float kTiny = 1.40129846e-45f;
+  __shared__ double s_max[kRefineThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, half = lane >> 4, sub = lane & 15;
+  const unsigned long long n = min(P.rcount[2], (unsigned long long)P.nrows);
+  const long long ni = *P.n_items;
+  for (unsigned long long e = blockIdx.x; e < n; e += gridDim.x) {
+    const int r = P.ovf_rows[e];
+    if ((unsigned)r >= (unsigned)P.nrows) {           // checked (block-uniform): skip and flag
+      if (threadIdx.x == 0) atomicOr(P.slot->status, kStatusIndex);
+      continue;
+    }
+    const DRow& R = P.rows[r];
+    const DInst& G = P.inst[R.inst];
+    const DBeam& B = P.beams[R.beam];
+    const float* tab = P.tables + (size_t)r * P.table_stride;
+    const long long i0 = P.row_item_base[r], i1 = P.row_item_base[r + 1];
+    const long long c0 = i0 < ni ? P.item_off[i0] : P.n_cand;
+    const long long c1 = min(i1 < ni ? P.item_off[i1] : P.n_cand, P.n_cand);
+    const float mlo = fmaxf(P.tau * __uint_as_float(P.row_max[r]), kTiny) * P.inv_tau_m;
+    const long long nvox = (long long)G.nx * G.ny * G.nz;
+    double M = 0.0;
+    for (long long cb = c0 + 32ll * w; cb < c1; cb += 32ll * (kRefineThreads / 32)) {   // warp-uniform
+      const long long c = cb + lane;
+      const float v = c < c1 ? P.vals[c] : -1.0f;
+      unsigned m = __ballot_sync(0xffffffffu, v >= mlo);
+      while (m) {                                     // warp-uniform: two flagged candidates at a time
+        const int a = __ffs(m) - 1;
+        m &= m - 1u;
+        const int b = m ? __ffs(m) - 1 : a;
+        if (m) m &= m - 1u;
+        int col = P.cols[cb + (half ? b : a)];
+        if (col < 0 || (long long)col >= nvox) {      // checked: evaluate voxel 0 instead, and flag
+          atomicOr(P.slot->status, kStatusIndex);
+          col = 0;
+        }
+        const double D = eval_pair64_half(R, G, B, tab, col, sub);
+        M = fmax(M, fmax(__shfl_sync(0xffffffffu, D, 0), __shfl_sync(0xffffffffu, D, 16)));
+      }
+    }
+    if (lane == 0) s_max[w] = M;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double mm = 0.0;
+      for (int k = 0; k < kRefineThreads / 32; ++k) mm = fmax(mm, s_max[k]);
+      P.row_max64[r] = mm;
+    }
+    __syncthreads();
+  }
+}
+
 // keep decisions of the listed pairs in FP64, a warp per pair.  The warp
 // evaluates the pair and its row's near-maximum candidates, takes M_j as the
 // largest of the latter, and decides D >= tau M_j; the value written back
 // makes the compaction's FP32 test agree, and kept pairs join their tile's
-// count.  A row whose near-maximum candidates overflowed its slots keeps the
-// FP32 decision.
+// count.  A row whose near-maximum candidates overflowed its slots takes its
+// FP64 maximum from k_refine_rowmax.
 __global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams P) {
   constexpr float kTiny = 1.40129846e-45f;
   const int lane = threadIdx.x & 31, half = lane >> 4, sub = lane & 15;
@@ -140,7 +197,9 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams P) {
     const DBeam& B = P.beams[R.beam];
     const float* tab = P.tables + (size_t)r * P.table_stride;
     const int mc = P.mcount[r];
-    const int total = 1 + min(mc, kMaxSlots);         // the pair, then the row's near-maximum candidates
+    // the pair, then the row's near-maximum candidates (a row that overflowed
+    // its slots has its FP64 maximum from k_refine_rowmax)
+    const int total = mc > kMaxSlots ? 1 : 1 + mc;
     double own = 0.0, M = 0.0;
     for (int j0 = 0; j0 < total; j0 += 2) {           // warp-uniform
       const int j = j0 + half;
@@ -157,10 +216,11 @@ __global__ void __launch_bounds__(kRefineThreads) k_refine(RefineParams P) {
       if (j0 + 1 < total) M = fmax(M, d1);
     }
     if (lane != 0) continue;
+    if (mc > kMaxSlots) M = P.row_max64[r];
     const float thr1 = fmaxf(P.tau * __uint_as_float(P.row_max[r]), kTiny);   // the compaction's FP32 threshold
     float v;
     bool keep;
-    if (mc >= 1 && mc <= kMaxSlots && M > 0.0) {
+    if (mc >= 1 && M > 0.0) {
       keep = own > 0.0 && own >= P.tau_d * M;
       v = __double2float_rn(own);
       if (keep && v < thr1) v = thr1;

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libdsc.so")
 
 DSC_OK = 0
 DSC_E_BUSY = 8
+DSC_W_INEXACT = 9
 DSC_CUTOFF_VOI6, DSC_CUTOFF_SIGMA, DSC_CUTOFF_NONE = 0, 1, 2
 DSC_VALUE_F32, DSC_VALUE_BF16 = 0, 1
 DSC_PROFILE_ERF, DSC_PROFILE_LAPLACE, DSC_PROFILE_LOGISTIC = 0, 1, 2
@@ -123,7 +124,7 @@ def lib():
                                        C.POINTER(C.c_float)]),
             "dsc_measure_alu_peaks": (C.c_int, [C.c_double, C.POINTER(C.c_double), I32, P]),
             "dsc_probe_tail": (C.c_int, [I32, P, I64, P, P, P]),
-            "dsc_get_refine_counts": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64)]),
+            "dsc_get_refine_counts": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -273,10 +274,11 @@ def dsc_probe_tail(profile: int, y_ptr: int, n: int, ours_ptr: int, cuda_ptr: in
 
 
 def dsc_get_refine_counts(res) -> tuple:
-    """(pairs re-evaluated in FP64 near a threshold, near a row maximum)."""
-    a, b = C.c_int64(), C.c_int64()
-    _check(lib().dsc_get_refine_counts(res, C.byref(a), C.byref(b)))
-    return int(a.value), int(b.value)
+    """(pairs re-evaluated in FP64 near a threshold, near a row maximum,
+    near-threshold pairs past the list's capacity, decided in FP32)."""
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().dsc_get_refine_counts(res, C.byref(a), C.byref(b), C.byref(c)))
+    return int(a.value), int(b.value), int(c.value)
 
 
 def dsc_result_wait(res):
@@ -364,16 +366,23 @@ def dsc_server_destroy(srv):
 
 
 def dsc_compute_dij_noalloc(grid, density_ptr: int, model, beams, opts: ComputeOpts, row_ptr_ptr: int, col_ptr: int,
-                            val_ptr: int, capacity: int, stream=0) -> int:
+                            val_ptr: int, capacity: int, stream=0, inexact: list = None) -> int:
     """D_ij into caller-allocated device buffers, no allocation by the library.
-    Returns the number of kept entries."""
+    Returns the number of kept entries.  DSC_W_INEXACT (complete, but some
+    decisions near the threshold were taken in FP32) is not raised: it is
+    appended to `inexact` when a list is given."""
     g = grid_desc(grid)
     mr = _ModelRef(model)
     arr = (BeamDesc * len(beams))(*[beam_desc(b) for b in beams])
     nnz = C.c_int64()
-    _check(lib().dsc_compute_dij_noalloc(C.byref(g), int(density_ptr), C.byref(mr.s), arr, len(beams), C.byref(opts),
-                                         int(row_ptr_ptr), int(col_ptr), int(val_ptr), int(capacity), C.byref(nnz),
-                                         stream))
+    st = lib().dsc_compute_dij_noalloc(C.byref(g), int(density_ptr), C.byref(mr.s), arr, len(beams), C.byref(opts),
+                                       int(row_ptr_ptr), int(col_ptr), int(val_ptr), int(capacity), C.byref(nnz),
+                                       stream)
+    if st == DSC_W_INEXACT:
+        if inexact is not None:
+            inexact.append(lib().dsc_last_error().decode(errors="replace"))
+        st = DSC_OK
+    _check(st)
     return nnz.value
 
 

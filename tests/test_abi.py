@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_library_metadata(lib):
-    assert dsc.dsc_abi_version() == 2
+    assert dsc.dsc_abi_version() == 3
     assert lib.dsc_status_str(0) == b"ok"
     assert lib.dsc_status_str(5) == b"device wait timed out"
     assert dsc.dsc_launch_count() >= 0
@@ -54,7 +54,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.dsc_probe_tail(0, None, 4, None, None, None) == 1
     assert lib.dsc_probe_tail(0, None, 0, None, None, None) == 0       # nothing to do
     a, b = C.c_int64(), C.c_int64()
-    assert lib.dsc_get_refine_counts(None, C.byref(a), C.byref(b)) == 1
+    assert lib.dsc_get_refine_counts(None, C.byref(a), C.byref(b), C.byref(a)) == 1
 
 
 def test_struct_layouts_match_header():

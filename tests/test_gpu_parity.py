@@ -641,8 +641,9 @@ def test_compaction_equals_host_filter(dsc, name):
         same = ~near[idx]
         assert np.array_equal(c1.val[same], c0.val[idx][same])                # and their values, bit for bit
         assert np.all(np.abs(c1.val[~same] / c0.val[idx][~same] - 1.0) < 1e-5)
-        nt, nm = dsc.dsc_get_refine_counts(res[1])
+        nt, nm, nf = dsc.dsc_get_refine_counts(res[1])
         assert nt == int(near.sum()) and nm >= int(np.sum(np.diff(c0.row_ptr) > 0))
+        assert nf == 0                                   # every listed decision was taken in FP64
         per_beam = np.array([b.n_u * b.n_v for b in w.beams])
         beam_of_row = np.repeat(np.arange(len(w.beams)), per_beam)
         scale = c2.beam_scale[beam_of_row[row1]]
@@ -654,6 +655,37 @@ def test_compaction_equals_host_filter(dsc, name):
         for r in res:
             dsc.dsc_release_result(r)
         dsc.dsc_destroy_geometry(g)
+
+
+def test_near_maximum_overflow_is_decided_in_fp64(dsc):
+    """A row with more than 4 candidates within 1e-5 of its maximum: water, a
+    beam model that is the same at every depth, a nearly parallel beam (SAD
+    77 m: D falls 6.5e-6 per 3 mm layer at these voxels) and the beamlet axis
+    on a voxel edge line, so the four mirror voxels of each layer tie; the two
+    shallowest layers (8 candidates) lie within 1e-5 of the maximum, the third
+    1.3e-5 below it.  The threshold sits 2e-6 below the maximum, so layers 0
+    and 1 are within 1e-5 of it (2e-6 above, 4.5e-6 below) but outside the
+    oracle's 1e-6 band.  The row is scanned for its FP64 maximum, no decision
+    stays FP32, and the CSR equals the oracle's: the shallowest layer alone."""
+    lut = np.empty((256, 4), np.float32)
+    lut[:, 0] = 0.9
+    lut[:, 1:] = (2.0, 5.0, 11.0)
+    m = P.Model(lut=lut, d_max=300.0, cutoff_mode=P.CUTOFF_VOI6)
+    g = P.centred_grid(12, 20, 12, 3.0, 3.0, 3.0)
+    w = P.Workload("overflow", g, np.ones(g.shape, np.float32), m,
+                   [P.Beam(0.0, 77000.0, (0.0, 0.0, 0.0), 3.0, 3.0, 1, 1)], tau=1.0 - 2e-6)
+    csr, res, geo = run(dsc, w)
+    try:
+        orc = O.compute_workload(w)
+        nt, nm, nf = dsc.dsc_get_refine_counts(res)
+        assert nm == 8 and nt == 8 and nf == 0, (nt, nm, nf)
+        assert len(orc.amb_row) == 0                      # nothing in the oracle's bands
+        gc, gv = csr.row(0)
+        oc, ov = orc.row(0)
+        assert oc.size == 4 and np.array_equal(gc, oc)    # the four voxels of the shallowest layer
+        assert np.abs(gv / ov - 1.0).max() < TOL
+    finally:
+        cleanup(dsc, res, geo)
 
 
 def test_batched_instances_against_oracle(dsc):

@@ -63,6 +63,18 @@ def test_two_calls_in_a_row_match_compute_dij(dsc):
         assert rel.max() <= TOL
 
 
+def test_smaller_problem_after_a_larger_one(dsc):
+    """The array keeps the previous call's contents: a small problem after a
+    large one (the reverse of the order above) must not pick up any of it --
+    the same CSR as the allocating entry point, bit for bit."""
+    for w in (P.slabs_128(value_dtype=P.VALUE_F32), P.water_32()):
+        ref = reference(dsc, w)
+        nnz, row_ptr, col, val = noalloc(dsc, w, ref.nnz + 64)
+        assert nnz == ref.nnz
+        assert np.array_equal(row_ptr, ref.row_ptr) and np.array_equal(col, ref.col)
+        assert np.array_equal(val, ref.val.astype(np.float32))
+
+
 def test_trilinear_table_and_logistic_profile(dsc):
     """The option flags and the model's profile reach the fixed-memory path
     too: same CSR as the allocating entry point."""
