@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--instances", type=int, default=32, help="batched: re-plan instances")
     p.add_argument("--requests", type=int, default=64, help="serving: requests")
     p.add_argument("--rate", type=float, default=4.0, help="serving: mean Poisson arrival rate (1/s)")
+    p.add_argument("--no-sub", action="store_true",
+                   help="default line without its batched and serving sub-measurements")
     p.add_argument("--stages", action="store_true",
                    help="per-stage device times of W + K whole computations of the workload, one JSON line "
                         "(no tuning, oracle or end-to-end legs: a short program for kernel profilers)")
@@ -326,7 +328,7 @@ def run_ours(args):
         vsize = 2 if w.value_dtype == dsc.DSC_VALUE_BF16 else 4
         h_rp = torch.empty(nrows + 1, dtype=torch.int64).pin_memory()
         h_col = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
-        h_val = torch.empty(max(nnz, 1) * vsize, dtype=torch.uint8).pin_memory()
+        h_val = torch.empty(max(nnz, 1) * 4, dtype=torch.uint8).pin_memory()
         h_sc = torch.empty(max(nbeams, 1), dtype=torch.float32).pin_memory()
         # Pipelined across steps: step k+1's upload and computation are queued
         # before step k's CSR is read back (on a second stream), so the host
@@ -340,28 +342,32 @@ def run_ours(args):
             dsc.dsc_copy_csr_to_host(res, h_rp.data_ptr(), h_col.data_ptr(), h_val.data_ptr(), h_sc.data_ptr(), csp)
             dsc.dsc_release_result(res)
 
-        pending = None
-        for k in range(e2e_steps + 2):
-            if k == 2:
-                stream.synchronize()
-                cstream.synchronize()
-                t0 = time.perf_counter()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            dsc.dsc_upload_density(g, host_rho.data_ptr(), False, sp)
-            r = dsc.dsc_compute_dij(g, plain, sp)
-            if pending is not None:
-                read_back(pending)             # the previous step's result (its copy is in the window)
-            pending = r
-        read_back(pending)
-        join = torch.cuda.Event()
-        join.record(cstream)
-        stream.wait_event(join)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e1.record(stream)
-        stream.synchronize()
-        e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
-        wall_s = max_over_ranks(time.perf_counter() - t0, dev)
+        def end_to_end(opts_e):
+            pending = None
+            for k in range(e2e_steps + 2):
+                if k == 2:
+                    stream.synchronize()
+                    cstream.synchronize()
+                    t0 = time.perf_counter()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                dsc.dsc_upload_density(g, host_rho.data_ptr(), False, sp)
+                r = dsc.dsc_compute_dij(g, opts_e, sp)
+                if pending is not None:
+                    read_back(pending)             # the previous step's result (its copy is in the window)
+                pending = r
+            read_back(pending)
+            join = torch.cuda.Event()
+            join.record(cstream)
+            stream.wait_event(join)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(stream)
+            stream.synchronize()
+            return max_over_ranks(e0.elapsed_time(e1) / 1e3, dev), max_over_ranks(time.perf_counter() - t0, dev)
+
+        e2e_s, wall_s = end_to_end(plain)
+        # the same with BF16 storage (per-beam scale): 6 instead of 8 bytes per kept entry read back
+        e2e16_s, wall16_s = end_to_end(dsc.compute_opts(w.tau, dsc.DSC_VALUE_BF16, w.h_frac, 0))
 
         # ---- the ALU denominators measured on this GPU (outside the timed region) ----
         pclk = Clocks(gpu_id(props, local if world > 1 else 0))
@@ -371,6 +377,12 @@ def run_ours(args):
     dsc.dsc_destroy_geometry(g)
     if rank != 0:
         return
+    sub = {}
+    if world == 1 and not args.no_sub:
+        # the batched (32 uneven re-plan instances) and served (Poisson 4/s)
+        # forms against plain per-plan launches, compact: a few steps each
+        sub["batched"] = measure_batched(dsc, P.batched(32), stream, steps=3, warmup=1, reps=1)
+        sub["serving"] = measure_serving(dsc, P, 32, 4.0, stream, bf16_share=0.25)
     ms = 1e3 * total_s / args.steps
     value = whole_job_rate(pairs, args.steps, world, total_s)
     eval_ms = statistics.mean(s["eval"] for s in stages)
@@ -385,6 +397,7 @@ def run_ours(args):
     stage_ms = {k: round(statistics.mean(s[k] for s in stages), 4) for k in stages[0]}
     h2d = int(host_rho.numel() * 4)
     d2h = int((nrows + 1) * 8 + nnz * 4 + nnz * vsize + nbeams * 4)
+    d2h16 = int((nrows + 1) * 8 + nnz * 4 + nnz * 2 + nbeams * 4)
     sms = props.multi_processor_count
     hbm_meas = None
     try:
@@ -431,6 +444,10 @@ def run_ours(args):
         "e2e": {"value": whole_job_rate(pairs, e2e_steps, world, e2e_s), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps,
                 "host_wall_ms_per_step": 1e3 * wall_s / e2e_steps},
+        "e2e_bf16": {"value": whole_job_rate(pairs, e2e_steps, world, e2e16_s), "unit": "pairs/s",
+                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h16,
+                     "ms_per_step": 1e3 * e2e16_s / e2e_steps, "host_wall_ms_per_step": 1e3 * wall16_s / e2e_steps,
+                     "value_dtype": "bf16 with per-beam scale"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": KEVAL_DRAM_BYTES_PER_PAIR * pairs,
@@ -467,6 +484,7 @@ def run_ours(args):
     }
     if cpu is not None:
         out["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "single_core")}
+    out.update(sub)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -485,19 +503,13 @@ def _timed(fn, stream, steps):
     return a.elapsed_time(b) / 1e3
 
 
-def run_batched(args):
+def measure_batched(dsc, ws, stream, steps, warmup, reps=3):
     """Many uneven re-plan instances in one batched launch sequence (one
     persistent evaluation over a shared work queue, replayed as a CUDA graph)
-    against the same instances as sequential per-plan launches."""
-    import torch
-    from paper_0908_4417_gb300 import build as B
-    B.build()
-    from paper_0908_4417_gb300 import dsc, phantoms as P
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.Stream(dev)
+    against the same instances as sequential per-plan launches, same tile
+    shape (the autotuner's, on these instances).  Device time per batch with
+    CUDA events on the launching stream."""
     sp = stream.cuda_stream
-    ws = P.batched(args.instances)
     gs = []
     for w in ws:
         g = dsc.dsc_create_geometry(w.grid, w.density, False, w.model, sp)
@@ -520,10 +532,10 @@ def run_batched(args):
             dsc.dsc_release_result(r)
         held.clear()
 
+    import torch
     with torch.cuda.stream(stream):
-        # tile shape from the autotuner, on these instances, before any timing
-        (tc, bps), tune_ms = dsc.dsc_autotune(gs, opts, sp, reps=3)
-        for _ in range(args.warmup):
+        (tc, bps), tune_ms = dsc.dsc_autotune(gs, opts, sp, reps=reps)
+        for _ in range(warmup):
             batch(); drain(); sequential(); drain()
         batch()
         stream.synchronize()
@@ -532,110 +544,154 @@ def run_batched(args):
         drain()
         n0 = dsc.dsc_launch_count()
         t_batch = 0.0
-        for _ in range(args.steps):
+        for _ in range(steps):
             t_batch += _timed(batch, stream, 1)
             drain()
         launches = dsc.dsc_launch_count() - n0
         t_seq = 0.0
-        for _ in range(args.steps):
+        for _ in range(steps):
             t_seq += _timed(sequential, stream, 1)
             drain()
     for g in gs:
         dsc.dsc_destroy_geometry(g)
-    out = {"metric": "voxel-beamlet pairs/s (batched re-plan instances)", "value": pairs * args.steps / t_batch,
-           "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"batched_{args.instances}", "instances": args.instances,
-                      "tuning": {"target_cand": tc, "eval_blocks_per_sm": bps, "autotune_median_ms": tune_ms},
-                      "rows": sum(w.nrows for w in ws), "pairs_per_step": pairs, "nnz_per_step": nnz,
-                      "l2": "working set far above L2 (no flush needed)",
-                      "sequential_pairs_per_s": pairs * args.steps / t_seq,
-                      "sequential_ms_per_step": 1e3 * t_seq / args.steps,
-                      "batched_over_sequential": t_seq / t_batch},
-           "gpu_launches": int(launches)}
-    print(json.dumps(out), flush=True)
+    return {"instances": len(ws), "rows": sum(w.nrows for w in ws), "pairs_per_batch": pairs, "nnz_per_batch": nnz,
+            "steps": steps, "batched_pairs_per_s": pairs * steps / t_batch, "batched_ms": 1e3 * t_batch / steps,
+            "sequential_pairs_per_s": pairs * steps / t_seq, "sequential_ms": 1e3 * t_seq / steps,
+            "batched_over_sequential": t_seq / t_batch,
+            "tuning": {"target_cand": tc, "eval_blocks_per_sm": bps, "autotune_median_ms": tune_ms},
+            "gpu_launches_per_batch": launches // max(steps, 1),
+            "basis": "device time (CUDA events) per batch of all instances; sequential = one dsc_compute_dij per "
+                     "instance on the same stream, same tile shape",
+            "parity": "tests/test_gpu_parity.py::test_batched_instances_against_oracle (4 instances in full, "
+                      "28 on 64 sampled rows) and ::test_batched_bf16_instances"}
 
 
-def run_serving(args):
-    """Continuous-batching server on a seeded Poisson stream of re-plan
-    requests (resident geometries, fresh beam sets), then the same requests
-    submitted at once (server throughput) and as sequential per-plan launches."""
-    import numpy as np
+def run_batched(args):
+    """The batched re-plan workload alone, as its own JSON line."""
     import torch
     from paper_0908_4417_gb300 import build as B
     B.build()
     from paper_0908_4417_gb300 import dsc, phantoms as P
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    m = measure_batched(dsc, P.batched(args.instances), stream, args.steps, args.warmup)
+    out = {"metric": "voxel-beamlet pairs/s (batched re-plan instances)", "value": m["batched_pairs_per_s"],
+           "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": m["batched_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batched_{args.instances}", "l2": "working set far above L2 (no flush needed)",
+                      **m},
+           "gpu_launches": int(m["gpu_launches_per_batch"] * args.steps)}
+    print(json.dumps(out), flush=True)
+
+
+def measure_serving(dsc, P, n_requests, rate, stream, bf16_share=0.0):
+    """Continuous-batching server on a seeded Poisson stream of re-plan
+    requests (8 resident geometries, fresh 5-9-field beam sets from the
+    batched distribution, HBM-footprint admission, 2 device slots), then the
+    same requests submitted at once (server throughput) and as sequential
+    per-plan launches.  Latency is submit to device completion; the device
+    intervals of the slots' launches (CUDA events) show the overlap."""
+    import numpy as np
     sp = stream.cuda_stream
     base = [P.batched_instance(7000 + k) for k in range(8)]
     gs = [dsc.dsc_create_geometry(w.grid, w.density, False, w.model, sp) for w in base]
     stream.synchronize()
     draw = P._Draw(8080)
     reqs = []
-    for _ in range(args.requests):
+    for i in range(n_requests):
         k = draw.randint(0, len(base) - 1)
         b0 = base[k].beams[0]
         nf = draw.randint(5, 9)
         beams = [P.Beam(360.0 * draw.u(), b0.sad, b0.iso, b0.a, b0.b, b0.n_u, b0.n_v) for _ in range(nf)]
         reqs.append((k, beams))
-    gaps = -np.log(P.uniform01(8081, np.arange(args.requests, dtype=np.uint64))) / args.rate
+    gaps = -np.log(P.uniform01(8081, np.arange(n_requests, dtype=np.uint64))) / rate
     arrive = np.cumsum(gaps) - gaps[0]
     opts = dsc.compute_opts(1e-3, dsc.DSC_VALUE_F32, 0.5, 0)
+    opts_bf16 = dsc.compute_opts(1e-3, dsc.DSC_VALUE_BF16, 0.5, 0)
+    n_bf16 = int(round(bf16_share * n_requests))
 
     def serve(times):
         srv = dsc.dsc_server_create(96 << 30, max_inflight=2, max_batch=8)
         t0 = time.perf_counter()
         ids = []
-        for (k, beams), ta in zip(reqs, times):
+        for i, ((k, beams), ta) in enumerate(zip(reqs, times)):
             dt = ta - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            ids.append(dsc.dsc_server_submit(srv, gs[k], beams, opts))
+            ids.append(dsc.dsc_server_submit(srv, gs[k], beams, opts_bf16 if i < n_bf16 else opts))
+        spans = []
         for rid in ids:
-            dsc.dsc_release_result(dsc.dsc_server_poll(srv, rid, -1))
+            r = dsc.dsc_server_poll(srv, rid, -1)
+            spans.append(dsc.dsc_get_server_timing(r))
+            dsc.dsc_release_result(r)
         span = time.perf_counter() - t0
         st = dsc.dsc_server_stats(srv)
         dsc.dsc_server_destroy(srv)
+        # launches (distinct device intervals) whose interval intersects one on the other slot
+        launches = sorted(set(spans))
+        overl = sum(1 for a in launches if any(b[0] != a[0] and a[1] < b[2] and b[1] < a[2] for b in launches))
+        st["launches"] = len(launches)
+        st["launches_overlapping_other_slot"] = overl
         return st, span
 
     def sequential():
         t0 = time.perf_counter()
         lat, pairs = [], 0
-        for k, beams in reqs:
+        for i, (k, beams) in enumerate(reqs):
             ts = time.perf_counter()
             g = gs[k]
             dsc.dsc_clear_beams(g)
             for b in beams:
                 dsc.dsc_add_beam(g, b)
-            r = dsc.dsc_compute_dij(g, opts, sp)
+            r = dsc.dsc_compute_dij(g, opts_bf16 if i < n_bf16 else opts, sp)
             dsc.dsc_result_wait(r)
             pairs += int(dsc.dsc_get_csr(r, False).pairs)
             dsc.dsc_release_result(r)
             lat.append(1e3 * (time.perf_counter() - ts))
         return pairs, time.perf_counter() - t0, lat
 
-    serve(np.zeros(min(8, args.requests)))            # warm-up (module load, pools)
+    serve(np.zeros(min(8, n_requests)))               # warm-up (module load, pools)
     st_p, span_p = serve(arrive)                        # Poisson arrivals
-    st_s, span_s = serve(np.zeros(args.requests))       # all at once: server throughput
+    st_s, span_s = serve(np.zeros(n_requests))          # all at once: server throughput
     pairs_q, span_q, lat_q = sequential()
     for g in gs:
         dsc.dsc_destroy_geometry(g)
     lat_q = sorted(lat_q)
-    out = {"metric": "voxel-beamlet pairs/s (served re-plan requests)", "value": st_s["pairs_done"] / span_s,
+    return {"requests": n_requests, "resident_geometries": len(gs), "poisson_rate_per_s": rate,
+            "bf16_requests": n_bf16, "slots": 2, "max_batch": 8,
+            "poisson_p50_ms": st_p["p50_ms"], "poisson_p99_ms": st_p["p99_ms"],
+            "poisson_pairs_per_s": st_p["pairs_done"] / span_p,
+            "saturated_p50_ms": st_s["p50_ms"], "saturated_p99_ms": st_s["p99_ms"],
+            "saturated_pairs_per_s": st_s["pairs_done"] / span_s,
+            "sequential_pairs_per_s": pairs_q / span_q,
+            "sequential_p50_ms": lat_q[len(lat_q) // 2],
+            "sequential_p99_ms": lat_q[min(len(lat_q) - 1, int(0.99 * len(lat_q)))],
+            "served_over_sequential": (st_s["pairs_done"] / span_s) / (pairs_q / span_q),
+            "saturated_launches": st_s["launches"],
+            "saturated_launches_overlapping_other_slot": st_s["launches_overlapping_other_slot"],
+            "basis": "latency = submit to device completion (host clock); pairs/s = pairs of all requests over "
+                     "the wall time from first submit to last result; overlap from CUDA events on the slots' "
+                     "streams",
+            "parity": "tests/test_gpu_parity.py::test_server_results_same_alone_and_in_mix (results identical "
+                      "alone and in the mix, slots overlapping on the device) and "
+                      "::test_server_bf16_request_against_oracle"}
+
+
+def run_serving(args):
+    """The serving workload alone, as its own JSON line."""
+    import torch
+    from paper_0908_4417_gb300 import build as B
+    B.build()
+    from paper_0908_4417_gb300 import dsc, phantoms as P
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    m = measure_serving(dsc, P, args.requests, args.rate, stream)
+    out = {"metric": "voxel-beamlet pairs/s (served re-plan requests)", "value": m["saturated_pairs_per_s"],
            "unit": "pairs/s", "n_gpus": 1, "steps": args.requests, "warmup": min(8, args.requests),
-           "ms_per_step": 1e3 * span_s / args.requests, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"serving_{args.requests}", "requests": args.requests,
-                      "resident_geometries": len(gs), "poisson_rate_per_s": args.rate,
-                      "poisson_p50_ms": st_p["p50_ms"], "poisson_p99_ms": st_p["p99_ms"],
-                      "poisson_pairs_per_s": st_p["pairs_done"] / span_p,
-                      "saturated_p50_ms": st_s["p50_ms"], "saturated_p99_ms": st_s["p99_ms"],
-                      "sequential_pairs_per_s": pairs_q / span_q,
-                      "sequential_p50_ms": lat_q[len(lat_q) // 2],
-                      "sequential_p99_ms": lat_q[min(len(lat_q) - 1, int(0.99 * len(lat_q)))],
-                      "served_over_sequential": (st_s["pairs_done"] / span_s) / (pairs_q / span_q)}}
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": {"workload": f"serving_{args.requests}", **m}}
     print(json.dumps(out), flush=True)
 
 

@@ -311,6 +311,13 @@ dsc_status dsc_server_poll(dsc_server* srv, uint64_t req_id, int32_t wait_ms, ds
 dsc_status dsc_server_stats(dsc_server* srv, double* p50_ms, double* p99_ms, int64_t* n_done, int64_t* pairs_done);
 /* Drains queued work, then frees the server. */
 void dsc_server_destroy(dsc_server* srv);
+/* For a result returned by dsc_server_poll: the device slot (stream) that
+ * computed it and the device interval of that slot's launch (the request's
+ * batch), in ms after the server's creation, from CUDA events recorded on the
+ * slot's stream around the launch.  Two requests whose intervals intersect
+ * had their work on the GPU at the same time.  DSC_E_STATE for a result that
+ * did not come from a server. */
+dsc_status dsc_get_server_timing(dsc_result* res, int32_t* slot, double* start_ms, double* end_ms);
 
 /* --- computation without allocation -------------------------------------- */
 /* dsc_compute_dij without any memory allocation by the library, for callers

@@ -190,6 +190,10 @@ struct dsc_result {
   cudaEvent_t done = nullptr;
   bool have_counts = false;
   long long out_begin = 0, nnz = 0, pairs = 0;
+  // served results: the server slot and the device interval of the launch
+  // that computed it (ms after the server's creation; -1: not served)
+  int srv_slot = -1;
+  double srv_t0_ms = -1.0, srv_t1_ms = -1.0;
   // host copies (copy_to_host = 1)
   long long* h_row_ptr = nullptr;
   int* h_col = nullptr;
@@ -1263,7 +1267,8 @@ struct SrvReq {
 
 struct SrvSlot {
   cudaStream_t s = nullptr;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;       // end of the slot's launch (timing enabled)
+  cudaEvent_t ev_start = nullptr; // its start (timing enabled)
   bool busy = false;
   size_t footprint = 0;
   std::shared_ptr<Plan> plan;
@@ -1279,6 +1284,7 @@ struct dsc_server {
   std::deque<std::shared_ptr<SrvReq>> queue;
   std::map<uint64_t, std::shared_ptr<SrvReq>> reqs;
   std::vector<SrvSlot> slots;
+  cudaEvent_t t0 = nullptr;     // the server's creation: origin of the slots' device intervals
   std::thread worker;
   bool stop = false;
   std::vector<double> lat_ms;
@@ -1330,7 +1336,17 @@ static bool same_opts(const dsc_compute_opts& a, const dsc_compute_opts& b) {
 
 static void srv_finish_slot(dsc_server* S, SrvSlot& sl) {
   double t = now_s();
+  float ms0 = -1.0f, ms1 = -1.0f;
+  if (cudaEventElapsedTime(&ms0, S->t0, sl.ev_start) != cudaSuccess ||
+      cudaEventElapsedTime(&ms1, S->t0, sl.ev) != cudaSuccess)
+    ms0 = ms1 = -1.0f;
+  const int slot_index = (int)(&sl - S->slots.data());
   for (auto& q : sl.reqs) {
+    if (q->result) {
+      q->result->srv_slot = slot_index;
+      q->result->srv_t0_ms = ms0;
+      q->result->srv_t1_ms = ms1;
+    }
     q->t_done = t;
     q->state = 2;
     S->lat_ms.push_back(1e3 * (t - q->t_submit));
@@ -1392,6 +1408,7 @@ static void srv_loop(dsc_server* S) {
       for (auto& q : batch) geoms.push_back(&q->view);
       std::vector<dsc_result*> outs(batch.size(), nullptr);
       lk.unlock();
+      cudaEventRecord(sl.ev_start, sl.s);
       dsc_status st = compute_common(geoms.data(), (int)geoms.size(), &batch[0]->opts, sl.s, outs.data(), false);
       std::string err = st == DSC_OK ? "" : g_err;
       if (st == DSC_OK) cudaEventRecord(sl.ev, sl.s);
@@ -1431,10 +1448,15 @@ extern "C" dsc_status dsc_server_create(size_t hbm_budget_bytes, int32_t max_inf
   S->slots.resize(max_inflight);
   for (auto& sl : S->slots) {
     if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreate(&sl.ev) != cudaSuccess || cudaEventCreate(&sl.ev_start) != cudaSuccess) {
       delete S;
       return fail(DSC_E_CUDA, "stream/event creation failed");
     }
+  }
+  if (cudaEventCreate(&S->t0) != cudaSuccess || cudaEventRecord(S->t0, S->slots[0].s) != cudaSuccess ||
+      cudaEventSynchronize(S->t0) != cudaSuccess) {
+    delete S;
+    return fail(DSC_E_CUDA, "server reference event failed");
   }
   S->worker = std::thread(srv_loop, S);
   *out = S;
@@ -1529,7 +1551,18 @@ extern "C" void dsc_server_destroy(dsc_server* S) {
     if (sl.s) cudaStreamSynchronize(sl.s);
     sl.plan.reset();
     if (sl.ev) cudaEventDestroy(sl.ev);
+    if (sl.ev_start) cudaEventDestroy(sl.ev_start);
     if (sl.s) cudaStreamDestroy(sl.s);
   }
+  if (S->t0) cudaEventDestroy(S->t0);
   delete S;
+}
+
+extern "C" dsc_status dsc_get_server_timing(dsc_result* r, int32_t* slot, double* start_ms, double* end_ms) {
+  if (!r || !slot || !start_ms || !end_ms) return fail(DSC_E_INVAL, "null argument");
+  if (r->srv_slot < 0) return fail(DSC_E_STATE, "not a served result, or its device interval is unknown");
+  *slot = r->srv_slot;
+  *start_ms = r->srv_t0_ms;
+  *end_ms = r->srv_t1_ms;
+  return DSC_OK;
 }

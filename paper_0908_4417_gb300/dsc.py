@@ -35,7 +35,7 @@ EXPORTS = [
     "dsc_release_result", "dsc_get_beamlets", "dsc_get_depth_tables", "dsc_get_row_stats", "dsc_get_stage_times",
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
     "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune", "dsc_dose", "dsc_beamlet_dot",
-    "dsc_measure_alu_peaks", "dsc_probe_tail", "dsc_get_refine_counts",
+    "dsc_measure_alu_peaks", "dsc_probe_tail", "dsc_get_refine_counts", "dsc_get_server_timing",
 ]
 
 
@@ -125,6 +125,7 @@ def lib():
             "dsc_measure_alu_peaks": (C.c_int, [C.c_double, C.POINTER(C.c_double), I32, P]),
             "dsc_probe_tail": (C.c_int, [I32, P, I64, P, P, P]),
             "dsc_get_refine_counts": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
+            "dsc_get_server_timing": (C.c_int, [P, C.POINTER(I32), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -279,6 +280,14 @@ def dsc_get_refine_counts(res) -> tuple:
     a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
     _check(lib().dsc_get_refine_counts(res, C.byref(a), C.byref(b), C.byref(c)))
     return int(a.value), int(b.value), int(c.value)
+
+
+def dsc_get_server_timing(res) -> tuple:
+    """(slot, device start ms, device end ms) of a served result's launch,
+    times after the server's creation."""
+    slot, a, b = C.c_int32(), C.c_double(), C.c_double()
+    _check(lib().dsc_get_server_timing(res, C.byref(slot), C.byref(a), C.byref(b)))
+    return int(slot.value), float(a.value), float(b.value)
 
 
 def dsc_result_wait(res):

@@ -98,6 +98,45 @@ def test_slabs_128_bf16_error_report(dsc):
     cleanup(dsc, res, g)
 
 
+def test_prostate_bf16_sampled_rows(dsc):
+    """The 9-field prostate with BF16 storage: 96 sampled rows against the FP64
+    oracle within 2^-8 (bf16 rounding of D / s_b, s_b the beam maximum)."""
+    w = P.prostate_256()
+    w.value_dtype = P.VALUE_BF16
+    csr, res, g = run(dsc, w)
+    try:
+        rows = np.sort(np.random.default_rng(9).choice(w.nrows, 96, replace=False))
+        beam_of_row = np.repeat(np.arange(len(w.beams)), [b.n_u * b.n_v for b in w.beams])
+        got = [(c, v * csr.beam_scale[beam_of_row[r]]) for r, (c, v) in zip(rows, gpu_rows(csr, rows))]
+        st = compare(got, O.compute_workload(w, rows=rows), 2.0 ** -8)
+        print("prostate_256 bf16 max_rel", st["max_rel"], "eps", st["eps"])
+    finally:
+        cleanup(dsc, res, g)
+
+
+def test_batched_bf16_instances(dsc):
+    """Four batched re-plan instances in one launch with BF16 storage: 48
+    sampled rows of each against the FP64 oracle within 2^-8."""
+    ws = P.batched(4)
+    gs = [dsc.geometry_from_workload(w) for w in ws]
+    batch = dsc.dsc_compute_dij_batch(gs, dsc.compute_opts(P.TAU, P.VALUE_BF16, 0.5))
+    rng = np.random.default_rng(48)
+    try:
+        worst = 0.0
+        for w, r in zip(ws, batch):
+            c = dsc.HostCSR(r)
+            rows = np.sort(rng.choice(w.nrows, 48, replace=False))
+            beam_of_row = np.repeat(np.arange(len(w.beams)), [b.n_u * b.n_v for b in w.beams])
+            got = [(cc, vv * c.beam_scale[beam_of_row[rr]]) for rr, (cc, vv) in zip(rows, gpu_rows(c, rows))]
+            worst = max(worst, compare(got, O.compute_workload(w, rows=rows), 2.0 ** -8)["max_rel"])
+        print("batched bf16 worst max_rel", worst)
+    finally:
+        for r in batch:
+            dsc.dsc_release_result(r)
+        for g in gs:
+            dsc.dsc_destroy_geometry(g)
+
+
 def test_prostate_full_size_sampled_rows(dsc):
     """The benchmark workload at full size (9 fields, 2304 rows) in the same
     launch configuration; 72 rows spread over all beams are checked against
@@ -517,17 +556,52 @@ def test_server_results_same_alone_and_in_mix(dsc):
     for rep in range(3):
         for k, w in enumerate(ws):
             ids.append((k, dsc.dsc_server_submit(srv, gs[k], w.beams, opts)))
+    spans = []
     for k, rid in ids:
         res = dsc.dsc_server_poll(srv, rid, -1)
         c = dsc.HostCSR(res)
         assert np.array_equal(c.row_ptr, alone[k].row_ptr) and np.array_equal(c.col, alone[k].col)
         assert np.array_equal(c.val, alone[k].val)
+        spans.append(dsc.dsc_get_server_timing(res))
         dsc.dsc_release_result(res)
     st = dsc.dsc_server_stats(srv)
     assert st["n_done"] == 9 and st["p99_ms"] >= st["p50_ms"] > 0
     assert st["pairs_done"] == 3 * sum(a.pairs for a in alone)
     dsc.dsc_server_destroy(srv)
+    # continuous batching: the two slots' launches were on the GPU at the same
+    # time (device intervals from CUDA events on the slots' streams intersect)
+    assert all(0.0 <= t0 < t1 for _, t0, t1 in spans), spans
+    assert {sl for sl, _, _ in spans} == {0, 1}
+    assert any(a[0] != b[0] and a[1] < b[2] and b[1] < a[2] for a in spans for b in spans), spans
+    r = dsc.dsc_compute_dij(gs[0], opts)
+    with pytest.raises(dsc.DscError) as e:
+        dsc.dsc_get_server_timing(r)                 # not a served result
+    assert e.value.status == 6
+    dsc.dsc_release_result(r)
     for g in gs:
+        dsc.dsc_destroy_geometry(g)
+
+
+def test_server_bf16_request_against_oracle(dsc):
+    """A served request with the BF16 storage option: values bf16(D / s_b) s_b
+    within 2^-8 of the FP64 oracle on every row, structure as the oracle's
+    outside the bands."""
+    w = small_instances(1)[0]
+    g = dsc.geometry_from_workload(w)
+    srv = dsc.dsc_server_create(8 << 30, max_inflight=2, max_batch=2)
+    rid = dsc.dsc_server_submit(srv, g, w.beams, dsc.compute_opts(P.TAU, P.VALUE_BF16, 0.5))
+    res = dsc.dsc_server_poll(srv, rid, -1)
+    try:
+        c = dsc.HostCSR(res)
+        assert c.value_dtype == P.VALUE_BF16
+        per_beam = np.array([b.n_u * b.n_v for b in w.beams])
+        scale = c.beam_scale[np.repeat(np.arange(len(w.beams)), per_beam)]
+        st = compare([(cc, vv * scale[r]) for r, (cc, vv) in enumerate(gpu_rows(c, range(w.nrows)))],
+                     O.compute_workload(w), 2.0 ** -8)
+        print("served bf16 max_rel", st["max_rel"], "eps", st["eps"])
+    finally:
+        dsc.dsc_release_result(res)
+        dsc.dsc_server_destroy(srv)
         dsc.dsc_destroy_geometry(g)
 
 
