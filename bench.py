@@ -32,9 +32,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # FP32 operations of one voxel-beamlet pair as the evaluation kernel forms it
-# (FMA = 2): geometry 20, depth 7, beam-model table 15, three erf-pair terms
-# 48 + 12 erf evaluations x 18 (degree-7 erfc), inverse square and product 3.
-F_PAIR = 309
+# (FMA = 2, a packed FP32x2 instruction = two lanes' worth; the exact
+# integer <-> float conversions done with FP32 adds are not counted):
+# geometry 14 (t, x' and z' in float-float, a_t and b_t), depth 4, beam-model
+# table 10, per profile term 23 (scaled arguments y1 and y2: 12, the erf
+# pair's combination: 8, the sum of Eq. 3: 3) and 4 erfc evaluations of 18
+# (denominator 2, degree-7 Horner 14, the square and the product: 2), and
+# the inverse square and products 3: 14 + 4 + 10 + 3 x (23 + 72) + 3.
+F_PAIR = 316
 FP32_LANES_PER_SM = 128
 # MUFU operations (rcp.approx, ex2.approx) of one pair in the evaluation
 # kernel's formulation, by lateral profile.  Per profile term one reciprocal
@@ -45,9 +50,10 @@ MUFU_PAIR = {0: {"rcp": 16, "ex2": 12}, 1: {"rcp": 4, "ex2": 12}, 2: {"rcp": 16,
 # HBM3e bandwidth of the part as specified (GB/s), next to the measured copy
 HBM_NOMINAL_GBS = 7900.0
 # DRAM bytes (read + write) of the evaluation kernel per candidate pair, from
-# one Nsight Compute capture of the current kernel on the 2-field prostate
-# (27.85 M pairs, 164.0 MB); the full workload's traffic is this times its pairs
-KEVAL_DRAM_BYTES_PER_PAIR = 5.887
+# one Nsight Compute capture of the kernel as built on the 2-field prostate
+# (27.85 M pairs, 2.0 MB read + 163.4 MB written); the full workload's
+# traffic is this times its pairs
+KEVAL_DRAM_BYTES_PER_PAIR = 5.939
 
 
 def parse():
