@@ -791,7 +791,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
   k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((P->n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
   CHECK_LAUNCH();
-  const unsigned tiles = (unsigned)std::max<long long>(1, (P->n_tiles + kEvalThreads / 32 - 1) / (kEvalThreads / 32));
+  const unsigned tiles = compact_blocks(P->n_tiles);
   k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_cnt);
   CHECK_LAUNCH();
   TRY(refine_launch(P, cp, s));

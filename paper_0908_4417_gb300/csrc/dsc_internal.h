@@ -123,7 +123,19 @@ struct OutSlot {
 };
 
 constexpr int kTilePer = 8;                       // candidates per thread of the compaction
-constexpr int kTile = 32 * kTilePer;              // candidates per compaction tile (one warp)
+constexpr int kTile = 32 * kTilePer;              // candidates per compaction tile
+#ifndef DSC_TPW
+#define DSC_TPW 1
+#endif
+// tiles per warp in the count and write passes: a warp loads all its tiles'
+// candidates before deciding any, so more loads are in flight
+constexpr int kTilesPerWarp = DSC_TPW;
+// CTAs (of kEvalThreads) of the count and write passes over n_tiles tiles
+inline unsigned compact_blocks(long long n_tiles) {
+  const long long warps = (n_tiles + kTilesPerWarp - 1) / kTilesPerWarp;
+  const long long b = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+  return (unsigned)(b > 0 ? b : 1);
+}
 
 struct CompactParams {
   const DRow* rows;

@@ -1216,9 +1216,9 @@ struct TileKeep {
 
 // candidates [p0, p0 + kTilePer) and their keep flags; item0 holds the
 // tile's first candidate, and each lane walks the (rare) item boundaries
+// the lane's kTilePer candidate values (and columns) from [p0, p0 + kTilePer); past the end -1
 template <bool kCols>
-__device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, long long tile, TileKeep& K) {
-  const long long item0 = p.tile_item0[tile];
+__device__ __forceinline__ void tile_load(const CompactParams& p, long long p0, TileKeep& K) {
   const long long n = p.n_cand;
   if (p0 + kTilePer <= n) {
     const float4* v4 = reinterpret_cast<const float4*>(p.vals + p0);
@@ -1240,6 +1240,14 @@ __device__ __forceinline__ void tile_keep(const CompactParams& p, long long p0, 
       if (kCols) K.C[i] = in ? __ldcs(p.cols + p0 + i) : 0;
     }
   }
+}
+
+// keep flags of the loaded candidates; item0 holds the tile's first
+// candidate, and each lane walks the (rare) item boundaries
+template <bool kCols>
+__device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0, long long tile, TileKeep& K) {
+  const long long item0 = p.tile_item0[tile];
+  const long long n = p.n_cand;
   const long long ni = *p.n_items;
   const long long* __restrict__ off = p.item_off;
   const bool bf16 = kCols && p.value_dtype == 1;
@@ -1382,75 +1390,95 @@ __global__ void k_tile_prep(CompactParams p) {
   }
 }
 
-__global__ void __launch_bounds__(kEvalThreads, 12) k_tile_count(CompactParams p, int* tile_cnt) {
+#ifndef DSC_COMPACT_MINB
+#define DSC_COMPACT_MINB 12
+#endif
+
+__global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_count(CompactParams p, int* tile_cnt) {
   const int lane = threadIdx.x & 31;
-  const long long tile = (long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5);
-  const long long base = tile * kTile;
-  if (base >= p.n_cand) return;                        // warp-uniform
-  TileKeep K;
-  tile_keep<false>(p, base + (long long)lane * kTilePer, tile, K);
-  int c = __popc(K.keep);
+  const long long t0 = ((long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5)) * kTilesPerWarp;
+  if (t0 * kTile >= p.n_cand) return;                  // warp-uniform
+  TileKeep K[kTilesPerWarp];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if (lane == 0) tile_cnt[tile] = c;
+  for (int u = 0; u < kTilesPerWarp; ++u)
+    if ((t0 + u) * kTile < p.n_cand) tile_load<false>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
+#pragma unroll
+  for (int u = 0; u < kTilesPerWarp; ++u) {
+    const long long tile = t0 + u;
+    if (tile * kTile >= p.n_cand) break;               // warp-uniform
+    tile_decide<false>(p, tile * kTile + (long long)lane * kTilePer, tile, K[u]);
+    int c = __popc(K[u].keep);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) tile_cnt[tile] = c;
+  }
 }
 
-__global__ void __launch_bounds__(kEvalThreads) k_tile_write(CompactParams p, const long long* __restrict__ tile_off) {
+__global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_write(CompactParams p,
+                                                                              const long long* __restrict__ tile_off) {
   __shared__ int s_col[kTileWarps][kTile];
   __shared__ float s_val[kTileWarps][kTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long tile = (long long)blockIdx.x * kTileWarps + w;
   const long long n = p.n_cand;
-  const long long base = tile * kTile;
-  if (base >= n) return;                               // warp-uniform
+  const long long t0 = ((long long)blockIdx.x * kTileWarps + w) * kTilesPerWarp;
+  if (t0 * kTile >= n) return;                         // warp-uniform
   const long long ni = *p.n_items;
   const long long* __restrict__ off = p.item_off;
-  const long long p0 = base + (long long)lane * kTilePer;
-  TileKeep K;
-  tile_keep<true>(p, p0, tile, K);
-  const int cnt = __popc(K.keep);
-  int incl = cnt;
+  TileKeep K[kTilesPerWarp];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int x = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += x;
-  }
-  const int tot = __shfl_sync(0xffffffffu, incl, 31);
-  const int excl = incl - cnt;
-  const long long prefix = tile_off[tile];
-  // kept count before each item start in this lane's range (items starting
-  // exactly at the tile's first candidate go to lane 0)
-  if (p.tile_starts[tile]) {                           // warp-uniform
-    long long j = p.tile_first[tile];
-    while (j < ni && off[j] < p0) ++j;
-    for (; j < ni && off[j] < p0 + kTilePer && off[j] < n; ++j) {
-      int r = (int)(off[j] - p0);
-      p.item_out[j] = prefix + excl + __popc(K.keep & ((1u << r) - 1u));
-    }
-  }
-  int q = excl;
+  for (int u = 0; u < kTilesPerWarp; ++u)
+    if ((t0 + u) * kTile < n) tile_load<true>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
 #pragma unroll
-  for (int i = 0; i < kTilePer; ++i) {
-    if (K.keep & (1u << i)) {
-      s_col[w][q] = K.C[i];
-      s_val[w][q] = K.D[i];
-      ++q;
+  for (int u = 0; u < kTilesPerWarp; ++u) {
+    const long long tile = t0 + u;
+    if (tile * kTile >= n) break;                      // warp-uniform
+    const long long p0 = tile * kTile + (long long)lane * kTilePer;
+    tile_decide<true>(p, p0, tile, K[u]);
+    const int cnt = __popc(K[u].keep);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int x = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += x;
     }
-  }
-  __syncwarp();
-  int* col = p.slot->col;
-  if (p.value_dtype == 1) {
-    __nv_bfloat16* val = (__nv_bfloat16*)p.slot->val;
-    for (int k = lane; k < tot; k += 32) {
-      col[prefix + k] = s_col[w][k];
-      val[prefix + k] = __float2bfloat16_rn(s_val[w][k]);
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - cnt;
+    const long long prefix = tile_off[tile];
+    // kept count before each item start in this lane's range (items starting
+    // exactly at the tile's first candidate go to lane 0)
+    if (p.tile_starts[tile]) {                         // warp-uniform
+      long long j = p.tile_first[tile];
+      while (j < ni && off[j] < p0) ++j;
+      for (; j < ni && off[j] < p0 + kTilePer && off[j] < n; ++j) {
+        int r = (int)(off[j] - p0);
+        p.item_out[j] = prefix + excl + __popc(K[u].keep & ((1u << r) - 1u));
+      }
     }
-  } else {
-    float* val = (float*)p.slot->val;
-    for (int k = lane; k < tot; k += 32) {
-      col[prefix + k] = s_col[w][k];
-      val[prefix + k] = s_val[w][k];
+    int q = excl;
+#pragma unroll
+    for (int i = 0; i < kTilePer; ++i) {
+      if (K[u].keep & (1u << i)) {
+        s_col[w][q] = K[u].C[i];
+        s_val[w][q] = K[u].D[i];
+        ++q;
+      }
     }
+    __syncwarp();
+    int* col = p.slot->col;
+    if (p.value_dtype == 1) {
+      __nv_bfloat16* val = (__nv_bfloat16*)p.slot->val;
+      for (int k = lane; k < tot; k += 32) {
+        col[prefix + k] = s_col[w][k];
+        val[prefix + k] = __float2bfloat16_rn(s_val[w][k]);
+      }
+    } else {
+      float* val = (float*)p.slot->val;
+      for (int k = lane; k < tot; k += 32) {
+        col[prefix + k] = s_col[w][k];
+        val[prefix + k] = s_val[w][k];
+      }
+    }
+    __syncwarp();                                      // the staging buffer is reused by the next tile
   }
 }
 

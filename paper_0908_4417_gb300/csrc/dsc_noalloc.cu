@@ -389,7 +389,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
   NA_LAUNCH();
   // kept count first, so the capacity is checked before any output is touched
-  const unsigned tiles = (unsigned)(n_tiles > 0 ? (n_tiles + kEvalThreads / 32 - 1) / (kEvalThreads / 32) : 1);
+  const unsigned tiles = compact_blocks(n_tiles);
   k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, d_tile_cnt);
   NA_LAUNCH();
   RefineParams rp{};
