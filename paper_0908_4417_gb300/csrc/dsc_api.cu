@@ -166,7 +166,7 @@ struct OutBufs {
   ~OutBufs() {
     void* ps[] = {slot.row_ptr, slot.col, slot.val, slot.beam_scale, slot.row_max, slot.row_cand, slot.inst_begin,
                   slot.status, slot.refine};
-    release_after(done, device, ps, 9);
+    release_after(done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
     if (done) cudaEventDestroy(done);
   }
 };
@@ -265,7 +265,7 @@ struct Plan {
   void free_scratch() {
     void* ps[] = {d_item_cand, d_item_off, d_tile_cnt, d_tile_off, d_item_out, d_vals, d_cols, d_item_row,
                   d_tile_item0, d_tile_first, d_tile_thr, d_tile_scale, d_tile_next, d_tile_starts, d_rlist_u};
-    release_after(last_done, device, ps, 15);
+    release_after(last_done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
     d_item_cand = nullptr; d_item_off = nullptr; d_tile_cnt = nullptr; d_tile_off = nullptr; d_item_out = nullptr;
     d_vals = nullptr; d_cols = nullptr; d_item_row = nullptr; d_tile_item0 = nullptr; d_tile_first = nullptr;
     d_tile_thr = nullptr; d_tile_scale = nullptr; d_tile_next = nullptr; d_tile_starts = nullptr; d_rlist_u = nullptr;
@@ -275,7 +275,7 @@ struct Plan {
     free_scratch();
     void* ps[] = {d_inst, d_beams, d_rows, d_row_items, d_row_item_base, d_tables, d_row_max, d_row_cand, d_scan,
                   d_counter, d_slot, d_rcount, d_mcount, d_mslot, d_ovf_rows, d_row_max64};
-    release_after(last_done, device, ps, 16);
+    release_after(last_done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
     if (last_done) cudaEventDestroy(last_done);
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
