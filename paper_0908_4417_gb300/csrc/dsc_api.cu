@@ -38,11 +38,11 @@ __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
 __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
 __global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*, const int*);
 __global__ void k_item_rows(const long long*, int, int*);
-__global__ void k_tile_map(const long long*, const long long*, long long, long long*, long long*);
+__global__ void k_tile_map(const long long*, const long long*, long long, const int*, long long*, long long*,
+                           long long*, int*, int*);
 __global__ void k_eval(EvalParams);
 __global__ void k_beam_scale(const DBeam*, int, const unsigned*, const OutSlot*);
 __global__ void k_tile_count(CompactParams, int*);
-__global__ void k_tile_prep(CompactParams);
 __global__ void k_lut_pairs(const float4*, int, int, float4*);
 __global__ void k_dose_scale(const unsigned*, const float*, int, int*);
 __global__ void k_dose_scatter(const long long*, const long long*, const int*, const void*, int, const DRow*, int,
@@ -237,6 +237,7 @@ struct Plan {
   float* d_tile_scale = nullptr;
   long long* d_tile_next = nullptr;
   int* d_tile_starts = nullptr;
+  int* d_tile_row = nullptr;
   long long n_tiles = 0;
   float* d_vals = nullptr;
   int* d_cols = nullptr;
@@ -255,6 +256,8 @@ struct Plan {
   OutSlot* d_slot = nullptr;         // output pointers of the computation in flight
   cudaGraphExec_t graph = nullptr;   // the captured launch sequence
   cudaStream_t cap_stream = nullptr; // private stream the sequence is captured on
+  cudaStream_t cap_side = nullptr;   // second branch of the captured sequence (the depth tables)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t last_done = nullptr;   // end of the latest computation
   cudaStream_t last_stream = nullptr;
   int grid_eval = 0, grid_items = 0;
@@ -264,11 +267,13 @@ struct Plan {
   std::mutex mu;                     // one computation at a time per plan
   void free_scratch() {
     void* ps[] = {d_item_cand, d_item_off, d_tile_cnt, d_tile_off, d_item_out, d_vals, d_cols, d_item_row,
-                  d_tile_item0, d_tile_first, d_tile_thr, d_tile_scale, d_tile_next, d_tile_starts, d_rlist_u};
+                  d_tile_item0, d_tile_first, d_tile_thr, d_tile_scale, d_tile_next, d_tile_starts, d_rlist_u,
+                  d_tile_row};
     release_after(last_done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
     d_item_cand = nullptr; d_item_off = nullptr; d_tile_cnt = nullptr; d_tile_off = nullptr; d_item_out = nullptr;
     d_vals = nullptr; d_cols = nullptr; d_item_row = nullptr; d_tile_item0 = nullptr; d_tile_first = nullptr;
     d_tile_thr = nullptr; d_tile_scale = nullptr; d_tile_next = nullptr; d_tile_starts = nullptr; d_rlist_u = nullptr;
+    d_tile_row = nullptr;
     if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
   }
   ~Plan() {
@@ -278,6 +283,9 @@ struct Plan {
     release_after(last_done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
     if (last_done) cudaEventDestroy(last_done);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (cap_side) cudaStreamDestroy(cap_side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
   }
 };
 
@@ -588,6 +596,9 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_mslot, (size_t)P->nrows * kMaxSlots, s));
   TRY(dalloc(&P->d_slot, 1, s));
   CU(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  CU(cudaStreamCreateWithFlags(&P->cap_side, cudaStreamNonBlocking));
+  CU(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+  CU(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&P->last_done, cudaEventDisableTiming));
   CU(cudaMemcpyAsync(P->d_inst, P->h_inst.data(), sizeof(DInst) * n, cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(P->d_beams, P->h_beams.data(), sizeof(DBeam) * P->nbeams, cudaMemcpyHostToDevice, s));
@@ -609,8 +620,10 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval, kEvalThreads, 0));
   nb = std::max(1, nb);
   P->grid_eval = (P->eval_bps > 0 ? std::min(P->eval_bps, nb) : nb) * sms;
+  // the candidate count runs beside the depth tables (one 32-thread CTA per
+  // beamlet): at most half of an SM's threads, so that both are resident
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count, kEvalThreads, 0));
-  P->grid_items = std::max(1, nb) * sms;
+  P->grid_items = std::min(std::max(1, nb), 8) * sms;
   k_item_rows<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_row_item_base, P->nrows, P->d_item_row);
   CHECK_LAUNCH();
   k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, P->d_row_item_base, P->nrows,
@@ -630,6 +643,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_tile_scale, P->n_tiles, s));
   TRY(dalloc(&P->d_tile_next, P->n_tiles, s));
   TRY(dalloc(&P->d_tile_starts, P->n_tiles, s));
+  TRY(dalloc(&P->d_tile_row, P->n_tiles, s));
   // about 1e-5 of the candidates fall within kRefineDelta of their threshold
   P->cap_u = (int)std::min<long long>(std::max<long long>(1 << 16, P->n_cand >> 10), 1 << 28);
   TRY(dalloc(&P->d_rlist_u, P->cap_u, s));
@@ -719,12 +733,22 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s, P->nrows));
   TRY(record(ev, 1, s));
-  // a2: radiological-depth tables
+  // a2: radiological-depth tables.  The captured sequence (no stage events)
+  // traces them on a second branch beside a3, which does not read them; the
+  // branches join before the evaluation.
+  const bool fork = ev == nullptr;
+  cudaStream_t ts = s;
+  if (fork) {
+    CU(cudaEventRecord(P->ev_fork, s));
+    CU(cudaStreamWaitEvent(P->cap_side, P->ev_fork, 0));
+    ts = P->cap_side;
+  }
   if (P->opts.flags & DSC_FLAG_TRILINEAR_TABLE)
-    k_trilinear_table<<<P->nrows, kSiddonThreads, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride);
+    k_trilinear_table<<<P->nrows, kSiddonThreads, 0, ts>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride);
   else
-    k_siddon<<<P->nrows, kSiddonThreads, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride);
+    k_siddon<<<P->nrows, kSiddonThreads, 0, ts>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride);
   CHECK_LAUNCH();
+  if (fork) CU(cudaEventRecord(P->ev_join, ts));
   TRY(record(ev, 2, s));
   // a3: candidate pairs per work item
   k_item_rows<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_row_item_base, P->nrows, P->d_item_row);
@@ -733,8 +757,10 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
                                                  P->d_item_cand, P->d_item_row);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_item_cand, n_items, 0, P->d_scan, P->d_item_off, s, P->n_items));
-  k_tile_map<<<256, 256, 0, s>>>(P->d_item_off, n_items, P->n_cand, P->d_tile_item0, P->d_tile_first);
+  k_tile_map<<<1024, 256, 0, s>>>(P->d_item_off, n_items, P->n_cand, P->d_item_row, P->d_tile_item0, P->d_tile_first,
+                                 P->d_tile_next, P->d_tile_starts, P->d_tile_row);
   CHECK_LAUNCH();
+  if (fork) CU(cudaStreamWaitEvent(s, P->ev_join, 0));
   TRY(record(ev, 3, s));
   // a4: FSPB evaluation
   EvalParams ep{};
@@ -779,6 +805,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.tile_scale = P->d_tile_scale;
   cp.tile_next = P->d_tile_next;
   cp.tile_starts = P->d_tile_starts;
+  cp.tile_row = P->d_tile_row;
   cp.value_dtype = P->opts.value_dtype;
   cp.slot = P->d_slot;
   cp.rlist_u = P->d_rlist_u;
@@ -789,8 +816,6 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.cap_u = P->cap_u;
   cp.nrows = P->nrows;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
-  k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((P->n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
-  CHECK_LAUNCH();
   const unsigned tiles = compact_blocks(P->n_tiles);
   k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_cnt);
   CHECK_LAUNCH();

@@ -150,10 +150,11 @@ struct CompactParams {
   long long* item_out;            // n_items: kept entries before each item's first candidate
   const long long* tile_item0;    // per tile: item holding its first candidate
   const long long* tile_first;    // per tile: first item starting at or after its first candidate
-  float* tile_thr;                // per tile: threshold of tile_item0's row (k_tile_prep)
-  float* tile_scale;              // per tile: BF16 scale of that row's beam
-  long long* tile_next;           // per tile: start of the item after tile_item0
-  int* tile_starts;               // per tile: an item starts inside the tile
+  const int* tile_row;            // per tile: row of tile_item0
+  float* tile_thr;                // per tile: threshold of that row (written by the count pass)
+  float* tile_scale;              // per tile: BF16 scale of that row's beam (written by the count pass)
+  const long long* tile_next;     // per tile: start of the item after tile_item0
+  const int* tile_starts;         // per tile: an item starts inside the tile
   int value_dtype;
   const OutSlot* slot;
   // decisions FP32 cannot settle: candidates within kRefineDelta (relative)

@@ -1253,7 +1253,19 @@ __device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0
   const bool bf16 = kCols && p.value_dtype == 1;
   long long it = item0;
   long long next = p.tile_next[tile];
-  float thr = p.tile_thr[tile];
+  float thr;
+  if (kCols) {
+    thr = p.tile_thr[tile];
+  } else {
+    // the count pass forms the threshold of the tile's first row (the row
+    // maxima are final) and leaves it, and the BF16 scale, for the write pass
+    const int r0 = p.tile_row[tile];
+    thr = p.tau * __uint_as_float(p.row_max[r0]);
+    if ((threadIdx.x & 31) == 0) {
+      p.tile_thr[tile] = thr;
+      if (p.value_dtype == 1) p.tile_scale[tile] = p.slot->beam_scale[p.rows[r0].beam];
+    }
+  }
   float scale = bf16 ? p.tile_scale[tile] : 1.0f;
   if (next <= p0) {                                    // this lane starts past the first boundary
     while (next <= p0 && it + 1 < ni) {
@@ -1351,42 +1363,42 @@ __device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0
   K.keep = keep;
 }
 
-// per tile: the item holding its first candidate (tile_item0) and the first
-// item starting at or after it (tile_first), from one thread per item
+// per tile, from the work decomposition alone (it runs before the
+// evaluation): the item holding the tile's first candidate (tile_item0), that
+// item's row (tile_row) and the start of the item after it (tile_next), the
+// first item starting at or after the tile's first candidate (tile_first),
+// and whether an item starts inside the tile (tile_starts), so that the
+// compaction starts from independent loads instead of a chain of dependent
+// ones; one warp per item, a tile per lane
 __global__ void k_tile_map(const long long* __restrict__ item_off, const long long* __restrict__ n_items_p,
-                           long long n_cand, long long* tile_item0, long long* tile_first) {
+                           long long n_cand, const int* __restrict__ item_row, long long* tile_item0,
+                           long long* tile_first, long long* tile_next, int* tile_starts, int* tile_row) {
   const long long ni = *n_items_p;
   const long long n_tiles = (n_cand + kTile - 1) / kTile;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ni; i += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < ni; i += nw) {
     const long long a = item_off[i], b = item_off[i + 1];
+    const long long next = i + 1 < ni ? b : n_cand;
+    const int r = item_row[i];
     // tiles whose first candidate lies in item i
-    for (long long t = (a + kTile - 1) / kTile; t * kTile < b && t < n_tiles; ++t) tile_item0[t] = i;
+    for (long long t = (a + kTile - 1) / kTile + lane; t * kTile < b && t < n_tiles; t += 32) {
+      tile_item0[t] = i;
+      tile_next[t] = next;
+      tile_row[t] = r;
+    }
     // tiles whose first candidate is in (off[i-1], off[i]]: item i is the first one starting at or after it
     const long long prev = i > 0 ? item_off[i - 1] : -1;
-    for (long long t = prev < 0 ? 0 : prev / kTile + 1; t * kTile <= a && t < n_tiles; ++t) tile_first[t] = i;
+    for (long long t = (prev < 0 ? 0 : prev / kTile + 1) + lane; t * kTile <= a && t < n_tiles; t += 32) {
+      tile_first[t] = i;
+      tile_starts[t] = a < min(n_cand, (t + 1) * kTile);
+    }
     // tiles starting after the last item's start: no item starts at or after them
     if (i == ni - 1)
-      for (long long t = a / kTile + 1; t < n_tiles; ++t) tile_first[t] = ni;
-  }
-}
-
-// per tile, once the row maxima are final: the threshold and BF16 scale of
-// the item holding the tile's first candidate, the next item boundary, and
-// whether any item starts inside the tile (so the compaction starts from
-// independent loads instead of a chain of dependent ones)
-__global__ void k_tile_prep(CompactParams p) {
-  const long long n = p.n_cand;
-  const long long n_tiles = (n + kTile - 1) / kTile;
-  const long long ni = *p.n_items;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_tiles;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long it = p.tile_item0[t];
-    const int r = p.item_row[it];
-    p.tile_thr[t] = p.tau * __uint_as_float(p.row_max[r]);
-    p.tile_scale[t] = p.value_dtype == 1 ? p.slot->beam_scale[p.rows[r].beam] : 1.0f;
-    p.tile_next[t] = it + 1 < ni ? p.item_off[it + 1] : n;
-    const long long f = p.tile_first[t];
-    p.tile_starts[t] = f < ni && p.item_off[f] < min(n, (t + 1) * kTile);
+      for (long long t = a / kTile + 1 + lane; t < n_tiles; t += 32) {
+        tile_first[t] = ni;
+        tile_starts[t] = 0;
+      }
   }
 }
 

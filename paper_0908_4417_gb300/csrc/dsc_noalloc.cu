@@ -30,10 +30,10 @@ __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
 __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
 __global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*, const int*);
 __global__ void k_item_rows(const long long*, int, int*);
-__global__ void k_tile_map(const long long*, const long long*, long long, long long*, long long*);
+__global__ void k_tile_map(const long long*, const long long*, long long, const int*, long long*, long long*,
+                           long long*, int*, int*);
 __global__ void k_eval(EvalParams);
 __global__ void k_tile_count(CompactParams, int*);
-__global__ void k_tile_prep(CompactParams);
 __global__ void k_lut_pairs(const float4*, int, int, float4*);
 __global__ void k_refine(RefineParams);
 __global__ void k_refine_rowmax(RefineParams);
@@ -323,6 +323,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   float* d_tile_scale = cv.take<float>(n_tiles);
   long long* d_tile_next = cv.take<long long>(n_tiles);
   int* d_tile_starts = cv.take<int>(n_tiles);
+  int* d_tile_row = cv.take<int>(n_tiles);
   const int cap_u = (int)std::min<long long>(std::max<long long>(1 << 16, n_cand >> 10), 1 << 28);
   unsigned long long* d_rlist_u = cv.take<unsigned long long>(cap_u);
   if (!d_rlist_u)
@@ -374,6 +375,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.tile_scale = d_tile_scale;
   cp.tile_next = d_tile_next;
   cp.tile_starts = d_tile_starts;
+  cp.tile_row = d_tile_row;
   cp.value_dtype = DSC_VALUE_F32;
   cp.slot = d_slot;
   cp.rlist_u = d_rlist_u;
@@ -384,9 +386,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.cap_u = cap_u;
   cp.nrows = nrows;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
-  k_tile_map<<<256, 256, 0, s>>>(d_item_off, n_items_dev, n_cand, d_tile_item0, d_tile_first);
-  NA_LAUNCH();
-  k_tile_prep<<<(unsigned)std::max<long long>(1, std::min<long long>((n_tiles + 255) / 256, 4096)), 256, 0, s>>>(cp);
+  k_tile_map<<<1024, 256, 0, s>>>(d_item_off, n_items_dev, n_cand, d_item_row, d_tile_item0, d_tile_first, d_tile_next,
+                                 d_tile_starts, d_tile_row);
   NA_LAUNCH();
   // kept count first, so the capacity is checked before any output is touched
   const unsigned tiles = compact_blocks(n_tiles);
