@@ -379,6 +379,9 @@ def run_ours(args):
         pclk = Clocks(gpu_id(props, local if world > 1 else 0))
         alu = dsc.dsc_measure_alu_peaks(200.0, sp)
         alu["clocks"] = pclk.stop()
+        # the host link's rate each way, the bound of the end-to-end path
+        # (pinned copies of one step's CSR size, outside the timed region)
+        link = dsc.dsc_measure_host_link(max(1 << 20, int((nrows + 1) * 8 + nnz * (4 + vsize) + nbeams * 4)), 3, sp)
 
     dsc.dsc_destroy_geometry(g)
     if rank != 0:
@@ -404,6 +407,15 @@ def run_ours(args):
     h2d = int(host_rho.numel() * 4)
     d2h = int((nrows + 1) * 8 + nnz * 4 + nnz * vsize + nbeams * 4)
     d2h16 = int((nrows + 1) * 8 + nnz * 4 + nnz * 2 + nbeams * 4)
+
+    def link_bound(d2h_bytes, e2e_ms):
+        # a step's result down and (pipelined, the other direction) the next
+        # step's density up: the slower of the two at the measured rates
+        ms = 1e3 * max(d2h_bytes / (link["d2h_gbs"] * 1e9), h2d / (link["h2d_gbs"] * 1e9))
+        return {"d2h_gbs": link["d2h_gbs"], "h2d_gbs": link["h2d_gbs"], "bound_ms_per_step": ms,
+                "frac_of_bound": ms / e2e_ms,
+                "basis": "pinned cudaMemcpyAsync of the step's CSR size each way, shortest of 3 "
+                         "(dsc_measure_host_link); bound = max(d2h bytes / d2h rate, h2d bytes / h2d rate)"}
     sms = props.multi_processor_count
     hbm_meas = None
     try:
@@ -449,11 +461,13 @@ def run_ours(args):
                                           "fp32_decided_past_capacity": refine_fp32}},
         "e2e": {"value": whole_job_rate(pairs, e2e_steps, world, e2e_s), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps,
-                "host_wall_ms_per_step": 1e3 * wall_s / e2e_steps},
+                "host_wall_ms_per_step": 1e3 * wall_s / e2e_steps,
+                "host_link": link_bound(d2h, 1e3 * e2e_s / e2e_steps)},
         "e2e_bf16": {"value": whole_job_rate(pairs, e2e_steps, world, e2e16_s), "unit": "pairs/s",
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h16,
                      "ms_per_step": 1e3 * e2e16_s / e2e_steps, "host_wall_ms_per_step": 1e3 * wall16_s / e2e_steps,
-                     "value_dtype": "bf16 with per-beam scale"},
+                     "value_dtype": "bf16 with per-beam scale",
+                     "host_link": link_bound(d2h16, 1e3 * e2e16_s / e2e_steps)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": KEVAL_DRAM_BYTES_PER_PAIR * pairs,

@@ -259,6 +259,17 @@ dsc_status dsc_beamlet_dot(dsc_result* res, const float* g_dev, float* out_dev, 
  * launches; n >= 6.  Waits for the stream.  DSC_E_INVAL for a short `out` or
  * ms_per_loop out of range. */
 dsc_status dsc_measure_alu_peaks(double ms_per_loop, double* out, int32_t n, void* stream);
+/* The host link's rate in each direction, which bounds the end-to-end path
+ * (a step's density up, its CSR down): `bytes` (1 MiB to 8 GiB) copied with
+ * cudaMemcpyAsync between a device buffer and a pinned host buffer, both
+ * allocated by the call and freed before it returns, on `stream`; one untimed
+ * copy each way, then the shortest of `reps` (1 to 100) copies, timed with
+ * CUDA events.  out[0] = device-to-host GB/s (10^9 bytes/s), out[1] =
+ * host-to-device GB/s, out[2], out[3] = their ms; n >= 4.  Waits for the
+ * stream.  DSC_E_INVAL for a short `out` or an argument out of range,
+ * DSC_E_NOMEM when a buffer cannot be allocated.  Not part of the paper:
+ * a measurement of this machine. */
+dsc_status dsc_measure_host_link(int64_t bytes, int32_t reps, double* out, int32_t n, void* stream);
 
 /* --- stage inspection (per-step parity and timing) ---------------------- */
 /* The lateral-profile tail T(y) = 2 G(y) of Eq. 3 (profile DSC_PROFILE_ERF:

@@ -143,3 +143,70 @@ extern "C" dsc_status dsc_measure_alu_peaks(double ms_per_loop, double* out, int
   if (ef != cudaSuccess) return peak_fail(DSC_E_CUDA, "free", ef);
   return DSC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// host-link bandwidth: the end-to-end path moves each step's density up and
+// its CSR down, so its bound is the link's rate in each direction
+// ---------------------------------------------------------------------------
+namespace {
+dsc_status link_fail(dsc_status st, const char* what, cudaError_t e) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "dsc_measure_host_link: %s%s%s", what, e != cudaSuccess ? ": " : "",
+           e != cudaSuccess ? cudaGetErrorString(e) : "");
+  dsc::set_error(buf);
+  return st;
+}
+}  // namespace
+
+extern "C" dsc_status dsc_measure_host_link(int64_t bytes, int32_t reps, double* out, int32_t n, void* stream) {
+  if (!out || n < 4) return link_fail(DSC_E_INVAL, "out needs 4 entries", cudaSuccess);
+  if (bytes < (1 << 20) || bytes > (8ll << 30)) return link_fail(DSC_E_INVAL, "bytes outside [1 MiB, 8 GiB]", cudaSuccess);
+  if (reps < 1 || reps > 100) return link_fail(DSC_E_INVAL, "reps outside [1, 100]", cudaSuccess);
+  cudaStream_t s = (cudaStream_t)stream;
+  void* d = nullptr;
+  void* h = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, (size_t)bytes, s);
+  if (e != cudaSuccess) return link_fail(DSC_E_NOMEM, "device buffer", e);
+  dsc_status st = DSC_OK;
+  const char* what = "";
+  if ((e = cudaHostAlloc(&h, (size_t)bytes, cudaHostAllocDefault)) != cudaSuccess) {
+    st = DSC_E_NOMEM;
+    what = "pinned host buffer";
+  } else if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
+             (e = cudaMemsetAsync(d, 0, (size_t)bytes, s)) != cudaSuccess) {
+    st = DSC_E_CUDA;
+    what = "set-up";
+  }
+  // best of `reps` copies each way, after one untimed copy each way
+  float best[2] = {0.0f, 0.0f};
+  for (int dir = 0; dir < 2 && st == DSC_OK; ++dir) {
+    for (int r = 0; r <= reps && st == DSC_OK; ++r) {
+      float ms = 0.0f;
+      if ((e = cudaEventRecord(e0, s)) != cudaSuccess ||
+          (e = dir == 0 ? cudaMemcpyAsync(h, d, (size_t)bytes, cudaMemcpyDeviceToHost, s)
+                        : cudaMemcpyAsync(d, h, (size_t)bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+          (e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+          (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+        st = DSC_E_CUDA;
+        what = "timed copy";
+      } else if (r > 0 && (best[dir] == 0.0f || ms < best[dir])) {
+        best[dir] = ms;
+      }
+    }
+  }
+  if (st == DSC_OK) {
+    for (int dir = 0; dir < 2; ++dir) {
+      out[dir] = (double)bytes / (best[dir] * 1e-3) / 1e9;
+      out[2 + dir] = best[dir];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  const cudaError_t ef = cudaFreeAsync(d, s);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  if (h) cudaFreeHost(h);
+  if (st != DSC_OK) return link_fail(st, what, e);
+  if (ef != cudaSuccess || es != cudaSuccess) return link_fail(DSC_E_CUDA, "free", ef != cudaSuccess ? ef : es);
+  return DSC_OK;
+}

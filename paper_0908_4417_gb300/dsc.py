@@ -36,6 +36,7 @@ EXPORTS = [
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
     "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune", "dsc_dose", "dsc_beamlet_dot",
     "dsc_measure_alu_peaks", "dsc_probe_tail", "dsc_get_refine_counts", "dsc_get_server_timing",
+    "dsc_measure_host_link",
 ]
 
 
@@ -123,6 +124,7 @@ def lib():
             "dsc_autotune": (C.c_int, [C.POINTER(P), I32, C.POINTER(ComputeOpts), P, I32, C.POINTER(Tuning),
                                        C.POINTER(C.c_float)]),
             "dsc_measure_alu_peaks": (C.c_int, [C.c_double, C.POINTER(C.c_double), I32, P]),
+            "dsc_measure_host_link": (C.c_int, [I64, I32, C.POINTER(C.c_double), I32, P]),
             "dsc_probe_tail": (C.c_int, [I32, P, I64, P, P, P]),
             "dsc_get_refine_counts": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
             "dsc_get_server_timing": (C.c_int, [P, C.POINTER(I32), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -266,6 +268,14 @@ def dsc_measure_alu_peaks(ms_per_loop: float = 200.0, stream=0) -> dict:
     _check(lib().dsc_measure_alu_peaks(float(ms_per_loop), out, 6, stream))
     return {"fp32_tflops": out[0], "ex2_tops": out[1], "rcp_tops": out[2],
             "ms": {"fma": out[3], "ex2": out[4], "rcp": out[5]}}
+
+
+def dsc_measure_host_link(nbytes: int, reps: int = 3, stream=0) -> dict:
+    """Host-link rates measured with pinned copies of nbytes each way (GB/s,
+    10^9 bytes/s, the shortest of `reps`), with their device ms."""
+    out = (C.c_double * 4)()
+    _check(lib().dsc_measure_host_link(int(nbytes), int(reps), out, 4, stream))
+    return {"d2h_gbs": out[0], "h2d_gbs": out[1], "ms": {"d2h": out[2], "h2d": out[3]}}
 
 
 def dsc_probe_tail(profile: int, y_ptr: int, n: int, ours_ptr: int, cuda_ptr: int, stream=0):

@@ -50,6 +50,12 @@ def test_null_arguments_are_rejected(lib):
     assert lib.dsc_measure_alu_peaks(0.5, peaks, 6, None) == 1
     assert b"ms_per_loop" in lib.dsc_last_error()
     assert lib.dsc_measure_alu_peaks(float("nan"), peaks, 6, None) == 1
+    link = (C.c_double * 4)()
+    assert lib.dsc_measure_host_link(1 << 20, 3, None, 4, None) == 1
+    assert lib.dsc_measure_host_link(1 << 20, 3, link, 3, None) == 1
+    assert lib.dsc_measure_host_link(1000, 3, link, 4, None) == 1
+    assert lib.dsc_measure_host_link(1 << 20, 0, link, 4, None) == 1
+    assert lib.dsc_measure_host_link(1 << 20, 101, link, 4, None) == 1
     assert lib.dsc_probe_tail(3, None, 0, None, None, None) == 1
     assert lib.dsc_probe_tail(0, None, 4, None, None, None) == 1
     assert lib.dsc_probe_tail(0, None, 0, None, None, None) == 0       # nothing to do

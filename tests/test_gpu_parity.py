@@ -637,6 +637,19 @@ def test_alu_peaks_are_plausible(dsc):
         assert 5.0 < ms < 200.0, r
 
 
+def test_host_link_rates_are_plausible(dsc):
+    """The host-link measurement (the end-to-end bound) reports rates between
+    1 GB/s and the link's nominal ceiling each way, and copy times consistent
+    with them; it leaves no error behind."""
+    n = 64 << 20
+    r = dsc.dsc_measure_host_link(n, 2, torch.cuda.current_stream().cuda_stream)
+    for d in ("d2h", "h2d"):
+        gbs = r[d + "_gbs"]
+        assert 1.0 < gbs < 1000.0, r
+        assert abs(n / (r["ms"][d] * 1e-3) / 1e9 - gbs) < 1e-6 * gbs, r
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("profile", [P.PROFILE_ERF, P.PROFILE_LAPLACE, P.PROFILE_LOGISTIC])
 def test_profile_tails_against_fp64_and_cuda(dsc, profile):
     """The evaluation's lateral-profile tail T(y) (for Eq. 3 the fitted erfc,
