@@ -817,7 +817,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.nrows = P->nrows;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
   const unsigned tiles = compact_blocks(P->n_tiles);
-  k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_cnt);
+  k_tile_count<<<tile_blocks(P->n_tiles, kCountTilesPerWarp), kEvalThreads, 0, s>>>(cp, P->d_tile_cnt);
   CHECK_LAUNCH();
   TRY(refine_launch(P, cp, s));
   TRY(scan_launch(P->d_tile_cnt, nullptr, P->n_tiles, P->d_scan, P->d_tile_off, s, P->n_tiles));

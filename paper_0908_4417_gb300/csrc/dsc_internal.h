@@ -130,12 +130,19 @@ constexpr int kTile = 32 * kTilePer;              // candidates per compaction t
 // tiles per warp in the count and write passes: a warp loads all its tiles'
 // candidates before deciding any, so more loads are in flight
 constexpr int kTilesPerWarp = DSC_TPW;
-// CTAs (of kEvalThreads) of the count and write passes over n_tiles tiles
-inline unsigned compact_blocks(long long n_tiles) {
-  const long long warps = (n_tiles + kTilesPerWarp - 1) / kTilesPerWarp;
+#ifndef DSC_CTPW
+#define DSC_CTPW DSC_TPW
+#endif
+// tiles per warp in the count pass alone
+constexpr int kCountTilesPerWarp = DSC_CTPW;
+// CTAs (of kEvalThreads) over n_tiles tiles, tpw tiles per warp
+inline unsigned tile_blocks(long long n_tiles, int tpw) {
+  const long long warps = (n_tiles + tpw - 1) / tpw;
   const long long b = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
   return (unsigned)(b > 0 ? b : 1);
 }
+// CTAs of the write pass
+inline unsigned compact_blocks(long long n_tiles) { return tile_blocks(n_tiles, kTilesPerWarp); }
 
 struct CompactParams {
   const DRow* rows;

@@ -1405,17 +1405,22 @@ __global__ void k_tile_map(const long long* __restrict__ item_off, const long lo
 #ifndef DSC_COMPACT_MINB
 #define DSC_COMPACT_MINB 12
 #endif
+// the count pass holds no columns: 16 CTAs per SM (32 registers) keep more
+// of its loads in flight
+#ifndef DSC_COUNT_MINB
+#define DSC_COUNT_MINB 16
+#endif
 
-__global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_count(CompactParams p, int* tile_cnt) {
+__global__ void __launch_bounds__(kEvalThreads, DSC_COUNT_MINB) k_tile_count(CompactParams p, int* tile_cnt) {
   const int lane = threadIdx.x & 31;
-  const long long t0 = ((long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5)) * kTilesPerWarp;
+  const long long t0 = ((long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5)) * kCountTilesPerWarp;
   if (t0 * kTile >= p.n_cand) return;                  // warp-uniform
-  TileKeep K[kTilesPerWarp];
+  TileKeep K[kCountTilesPerWarp];
 #pragma unroll
-  for (int u = 0; u < kTilesPerWarp; ++u)
+  for (int u = 0; u < kCountTilesPerWarp; ++u)
     if ((t0 + u) * kTile < p.n_cand) tile_load<false>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
 #pragma unroll
-  for (int u = 0; u < kTilesPerWarp; ++u) {
+  for (int u = 0; u < kCountTilesPerWarp; ++u) {
     const long long tile = t0 + u;
     if (tile * kTile >= p.n_cand) break;               // warp-uniform
     tile_decide<false>(p, tile * kTile + (long long)lane * kTilePer, tile, K[u]);

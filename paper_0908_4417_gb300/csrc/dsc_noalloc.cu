@@ -391,7 +391,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   NA_LAUNCH();
   // kept count first, so the capacity is checked before any output is touched
   const unsigned tiles = compact_blocks(n_tiles);
-  k_tile_count<<<tiles, kEvalThreads, 0, s>>>(cp, d_tile_cnt);
+  k_tile_count<<<tile_blocks(n_tiles, kCountTilesPerWarp), kEvalThreads, 0, s>>>(cp, d_tile_cnt);
   NA_LAUNCH();
   RefineParams rp{};
   rp.inst = d_inst;
