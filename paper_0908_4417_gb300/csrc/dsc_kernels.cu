@@ -1004,9 +1004,11 @@ __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm,
       D[k] = eval_pair<PROF, TS, SIG>(C, small_int_to_float(ix), A, B, sm.sf[li] + (long long)j * C.dsf, sm.tab,
                                       SMLUT);
     }
+    if (g + 4 > wl) {                                   // only a window's last group holds padding
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (g + k >= wl) { D[k] = -1.0f; col[k] = 0; }     // padding
+      for (int k = 0; k < 4; ++k)
+        if (g + k >= wl) { D[k] = -1.0f; col[k] = 0; }
+    }
     *reinterpret_cast<float4*>(out + jj) = make_float4(D[0], D[1], D[2], D[3]);
     *reinterpret_cast<int4*>(outc + jj) = make_int4(col[0], col[1], col[2], col[3]);
     vmax = fmaxf(vmax, fmaxf(fmaxf(D[0], D[1]), fmaxf(D[2], D[3])));
