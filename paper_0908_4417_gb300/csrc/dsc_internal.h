@@ -15,7 +15,7 @@ constexpr int kEvalThreads = 128;     // threads per CTA of the evaluation / com
 #define DSC_LINES_PER_ITEM 256
 #endif
 constexpr int kMaxLinesPerItem = DSC_LINES_PER_ITEM;  // x-lines handled by one work item (multiple of kEvalThreads)
-constexpr int kWindow = 2048;         // candidates mapped to lines per pass of an item
+constexpr int kWindow = 4096;         // candidates mapped to lines per pass of an item
 constexpr int kSiddonThreads = 32;    // lanes per ray (one warp, one CTA) of the depth-table kernels
 constexpr int kScanBlocks = 1024;     // blocks of the device-wide scan
 constexpr int kScanThreads = 256;

@@ -466,9 +466,6 @@ constexpr int kLutSmem = DSC_LUT_SMEM;
 #else
 #define SMLUT nullptr
 #endif
-#ifndef DSC_EVAL_HALVES
-#define DSC_EVAL_HALVES 0
-#endif
 // The x-lines of a work item, rebased on the item's candidate index jj (0 at
 // the item's first candidate): candidate jj on line li has ix = ixb + jj,
 // column colb + jj and depth coordinate sfb + jj * dsf, so a candidate needs
@@ -477,7 +474,7 @@ struct LineSm {
   float4 sx[kMaxLinesPerItem];        // t at ix = 0, colb (int bits), x' hi, z' hi at ix = 0
   float4 zc[kMaxLinesPerItem];        // x' lo, z' lo at ix = 0, ixb (int bits), unused
   long long sf[kMaxLinesPerItem];     // sfb: s of candidate jj = 0 (fixed point, units of h 2^-32)
-  unsigned short map[kWindow];        // line of each candidate of the window (8-byte aligned)
+  unsigned char map[kWindow];         // line of each candidate of the window (4-byte aligned)
   int off[kMaxLinesPerItem + 1];      // first candidate (jj) of each line
   int wscan[kEvalThreads / 32];
   float tab[kTabSmem];                // the row's depth table, when it fits
@@ -646,35 +643,38 @@ __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, l
   return tot;
 }
 
-// line index of every candidate in [w0, w0 + wl): mark line starts, then an
-// inclusive max-scan over the window
+// line index of every candidate in [w0, w0 + wl), one byte each (an item
+// has at most 256 lines): mark line starts, then an inclusive max-scan over
+// the window (two passes over each thread's consecutive entries in shared
+// memory).  One-byte entries let a window of 4096 candidates share the
+// space of 2048 two-byte ones, which halves the barriers per candidate.
+static_assert(kMaxLinesPerItem <= 256, "line indices of an item fit a byte");
 __device__ void item_map(LineSm& sm, int w0, int wl) {
   constexpr int per = kWindow / kEvalThreads;
-  int t = threadIdx.x;
-  int nl = sm.nl;
-  int base = t * per;
-  int mk[per];
+  constexpr int words = per / 4;
+  const int t = threadIdx.x;
+  const int nl = sm.nl;
+  unsigned* mw = reinterpret_cast<unsigned*>(sm.map) + t * words;
+  // zero-filled: line indices rise along the window and position 0 always
+  // holds a start, so a running maximum over the starts gives every line
 #pragma unroll
-  for (int j = 0; j < per; ++j) mk[j] = -1;
-  // scatter the starts into a shared buffer (the map itself as scratch)
-  for (int j = t; j < kWindow; j += kEvalThreads) sm.map[j] = 0xffff;
+  for (int j = 0; j < words; ++j) mw[j] = 0u;
   __syncthreads();
   for (int li = t; li < nl; li += kEvalThreads) {
     int o = sm.off[li], e = sm.off[li + 1];
     if (e > o) {
-      if (o >= w0 && o < w0 + wl) sm.map[o - w0] = (unsigned short)li;
-      else if (o < w0 && e > w0) sm.map[0] = (unsigned short)li;
+      if (o >= w0 && o < w0 + wl) sm.map[o - w0] = (unsigned char)li;
+      else if (o < w0 && e > w0) sm.map[0] = (unsigned char)li;
     }
   }
   __syncthreads();
-  int run = -1;
+  int run = 0;
 #pragma unroll
-  for (int j = 0; j < per; ++j) {
-    int v = sm.map[base + j];
-    if (v != 0xffff) run = v;
-    mk[j] = run;
+  for (int j = 0; j < words; ++j) {
+    const unsigned v = mw[j];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) run = max(run, (int)((v >> (8 * k)) & 0xffu));
   }
-  // warp inclusive max-scan of the per-thread last value, then across warps
   int lane = t & 31, w = t >> 5;
   int incl = run;
 #pragma unroll
@@ -684,16 +684,25 @@ __device__ void item_map(LineSm& sm, int w0, int wl) {
   }
   if (lane == 31) sm.wscan[w] = incl;
   __syncthreads();
-  int wpre = -1;
+  int wpre = 0;
 #pragma unroll
   for (int i = 0; i < kEvalThreads / 32; ++i)
     if (i < w) wpre = max(wpre, sm.wscan[i]);
   int excl = __shfl_up_sync(0xffffffffu, incl, 1);
-  if (lane == 0) excl = -1;
-  int carry = max(wpre, excl);
-  __syncthreads();
+  if (lane == 0) excl = 0;
+  run = max(wpre, excl);
+  // second pass: running maximum from the carry
 #pragma unroll
-  for (int j = 0; j < per; ++j) sm.map[base + j] = (unsigned short)max(mk[j], carry);
+  for (int j = 0; j < words; ++j) {
+    const unsigned v = mw[j];
+    unsigned o = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      run = max(run, (int)((v >> (8 * k)) & 0xffu));
+      o |= (unsigned)run << (8 * k);
+    }
+    mw[j] = o;
+  }
   __syncthreads();
 }
 
@@ -956,42 +965,18 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
 // the candidates [w0, w0 + wl) of an item's window (the item's first wl
 // candidates past w0 are real; the rest of the last group of 4 is padding),
 // profile PROF (block-uniform); TS: the depth table is in sm.tab; SIG: the
-// sigma cutoff.  Each thread takes groups of 4 consecutive candidates (two
-// independent chains at a time), writes their values and columns with
-// aligned 8-byte stores (the item starts on a multiple of 4), and keeps the
-// maximum and, with SIG, the count inside the cutoff.
+// sigma cutoff.  Each thread takes groups of 4 consecutive candidates (four
+// independent chains), writes their values and columns with aligned 16-byte
+// stores (the item starts on a multiple of 4), and keeps the maximum and,
+// with SIG, the count inside the cutoff.
 template <int PROF, bool TS, bool SIG>
 __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm, int w0, int wl, float* out,
                                             int* outc, float& vmax, int& valid) {
   const int nl1 = sm.nl - 1;
   for (int g = 4 * (int)threadIdx.x; g < wl; g += 4 * kEvalThreads) {
     const int jj = w0 + g;                              // item-relative index of the group's first candidate
-    const uint2 mm = *reinterpret_cast<const uint2*>(sm.map + g);
-#if DSC_EVAL_HALVES
-    // two candidates at a time (two independent chains), stored as 8 bytes each
-#pragma unroll
-    for (int h = 0; h < 4; h += 2) {
-      float D[2];
-      int col[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const unsigned m16 = h ? mm.y : mm.x;
-        const int li = min((int)(q ? (m16 >> 16) : (m16 & 0xffffu)), nl1);   // entries past wl: any line will do
-        const float4 A = sm.sx[li], B = sm.zc[li];
-        const int j = jj + h + q;
-        const int ix = __float_as_int(B.z) + j;
-        col[q] = __float_as_int(A.y) + j;
-        D[q] = eval_pair<PROF, TS, SIG>(C, small_int_to_float(ix), A, B, sm.sf[li] + (long long)j * C.dsf, sm.tab,
-                                        SMLUT);
-        if (g + h + q >= wl) { D[q] = -1.0f; col[q] = 0; }   // padding
-      }
-      *reinterpret_cast<float2*>(out + jj + h) = make_float2(D[0], D[1]);
-      *reinterpret_cast<int2*>(outc + jj + h) = make_int2(col[0], col[1]);
-      vmax = fmaxf(vmax, fmaxf(D[0], D[1]));
-      if (SIG) valid += (D[0] >= 0.0f) + (D[1] >= 0.0f);
-    }
-#else
-    const int lidx[4] = {(int)(mm.x & 0xffffu), (int)(mm.x >> 16), (int)(mm.y & 0xffffu), (int)(mm.y >> 16)};
+    const unsigned mmb = *reinterpret_cast<const unsigned*>(sm.map + g);
+    const int lidx[4] = {(int)(mmb & 0xffu), (int)((mmb >> 8) & 0xffu), (int)((mmb >> 16) & 0xffu), (int)(mmb >> 24)};
     float D[4];
     int col[4];
 #pragma unroll
@@ -1012,10 +997,7 @@ __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm,
     *reinterpret_cast<float4*>(out + jj) = make_float4(D[0], D[1], D[2], D[3]);
     *reinterpret_cast<int4*>(outc + jj) = make_int4(col[0], col[1], col[2], col[3]);
     vmax = fmaxf(vmax, fmaxf(fmaxf(D[0], D[1]), fmaxf(D[2], D[3])));
-#endif
-#if !DSC_EVAL_HALVES
     if (SIG) valid += (D[0] >= 0.0f) + (D[1] >= 0.0f) + (D[2] >= 0.0f) + (D[3] >= 0.0f);
-#endif
   }
 }
 
