@@ -645,20 +645,23 @@ __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, l
 
 // line index of every candidate in [w0, w0 + wl), one byte each (an item
 // has at most 256 lines): mark line starts, then an inclusive max-scan over
-// the window (two passes over each thread's consecutive entries in shared
-// memory).  One-byte entries let a window of 4096 candidates share the
-// space of 2048 two-byte ones, which halves the barriers per candidate.
+// the window.  Each thread reads its 32 consecutive entries as two 16-byte
+// vectors (scalar accesses at that stride conflict 8 ways in the banks),
+// scans them in registers and writes them back the same way.  One-byte
+// entries let a window of 4096 candidates share the space of 2048 two-byte
+// ones, which halves the barriers per candidate.
 static_assert(kMaxLinesPerItem <= 256, "line indices of an item fit a byte");
 __device__ void item_map(LineSm& sm, int w0, int wl) {
   constexpr int per = kWindow / kEvalThreads;
-  constexpr int words = per / 4;
+  constexpr int vecs = per / 16;                        // 16-byte vectors per thread
+  static_assert(per % 16 == 0, "whole 16-byte vectors of the map per thread");
   const int t = threadIdx.x;
   const int nl = sm.nl;
-  unsigned* mw = reinterpret_cast<unsigned*>(sm.map) + t * words;
+  uint4* mv = reinterpret_cast<uint4*>(sm.map) + t * vecs;
   // zero-filled: line indices rise along the window and position 0 always
   // holds a start, so a running maximum over the starts gives every line
 #pragma unroll
-  for (int j = 0; j < words; ++j) mw[j] = 0u;
+  for (int j = 0; j < vecs; ++j) mv[j] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   for (int li = t; li < nl; li += kEvalThreads) {
     int o = sm.off[li], e = sm.off[li + 1];
@@ -668,13 +671,17 @@ __device__ void item_map(LineSm& sm, int w0, int wl) {
     }
   }
   __syncthreads();
+  unsigned wv[4 * vecs];
+#pragma unroll
+  for (int j = 0; j < vecs; ++j) {
+    const uint4 q = mv[j];
+    wv[4 * j] = q.x; wv[4 * j + 1] = q.y; wv[4 * j + 2] = q.z; wv[4 * j + 3] = q.w;
+  }
   int run = 0;
 #pragma unroll
-  for (int j = 0; j < words; ++j) {
-    const unsigned v = mw[j];
+  for (int j = 0; j < 4 * vecs; ++j)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) run = max(run, (int)((v >> (8 * k)) & 0xffu));
-  }
+    for (int k = 0; k < 4; ++k) run = max(run, (int)((wv[j] >> (8 * k)) & 0xffu));
   int lane = t & 31, w = t >> 5;
   int incl = run;
 #pragma unroll
@@ -693,16 +700,18 @@ __device__ void item_map(LineSm& sm, int w0, int wl) {
   run = max(wpre, excl);
   // second pass: running maximum from the carry
 #pragma unroll
-  for (int j = 0; j < words; ++j) {
-    const unsigned v = mw[j];
+  for (int j = 0; j < 4 * vecs; ++j) {
+    const unsigned v = wv[j];
     unsigned o = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       run = max(run, (int)((v >> (8 * k)) & 0xffu));
       o |= (unsigned)run << (8 * k);
     }
-    mw[j] = o;
+    wv[j] = o;
   }
+#pragma unroll
+  for (int j = 0; j < vecs; ++j) mv[j] = make_uint4(wv[4 * j], wv[4 * j + 1], wv[4 * j + 2], wv[4 * j + 3]);
   __syncthreads();
 }
 
