@@ -914,14 +914,13 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 A
 
   // beam-model table: T(d), c3_1..3(d) / K (K = Prof<PROF>::K, folded in
   // when the table was built); past the end, the last row.  g is clamped to
-  // [0, last] (a NaN depth maps to 0), so its floor comes from 2^23 + g
-  // rounded to the nearest integer, one down where that is above g.
+  // [0, last] (a NaN depth maps to 0); its row is the truncation of
+  // min(g, last - 1), a conversion on the MUFU pipe (less busy than the FMA
+  // pipe and the ALU, which the same floor from 2^23 + g rounding would use),
+  // and w = 1 at g = last.
   const float g = fminf(fmaxf(d * C.lut_scale, 0.0f), C.lut_last);
-  float kl = __fsub_rn(__fadd_rn(g, 8388608.0f), 8388608.0f);
-  kl = kl > g ? kl - 1.0f : kl;
-  kl = fminf(kl, C.lut_last - 1.0f);
-  const float w = g - kl;                  // in [0, 1], exact
-  const int kk = __float_as_int(__fadd_rn(kl, 8388608.0f)) - 0x4B000000;
+  const int kk = __float2int_rz(fminf(g, C.lut_last - 1.0f));   // g >= 0: the floor
+  const float w = g - small_int_to_float(kk);   // in [0, 1], exact
 #if DSC_LUT_SMEM
   const float4 L = TS ? slut[2 * kk] : __ldg(C.lut + 2 * kk);                 // row kk
   const float4 dL = TS ? slut[2 * kk + 1] : __ldg(C.lut + 2 * kk + 1);        // row kk+1 - row kk
