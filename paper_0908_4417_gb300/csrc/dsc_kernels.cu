@@ -1204,6 +1204,7 @@ struct TileKeep {
   float D[kTilePer];
   int C[kTilePer];
   unsigned keep;
+  int cnt;            // count pass: kept entries of the lane
 };
 
 // candidates [p0, p0 + kTilePer) and their keep flags; item0 holds the
@@ -1279,6 +1280,26 @@ __device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0
   float ulo = 0.0f, uhi = 0.0f, mlo = 0.0f;
   if (!kCols) { ulo = thr1 * kLo; uhi = thr1 * kHi; mlo = thr1 * p.inv_tau_m; }
   int nx = next >= n ? kTilePer : (int)min(next - p0, (long long)kTilePer);
+  if (!kCols && nx >= kTilePer) {
+    // count pass, the common case: one row for the lane's candidates; count
+    // them, and fall through to the per-candidate flags only when one lies
+    // in a refinement window
+    int cnt = 0;
+    bool sp = false;
+    float m = K.D[0];
+#pragma unroll
+    for (int i = 0; i < kTilePer; ++i) {
+      const float D = K.D[i];
+      const bool above = D >= uhi;
+      cnt += above;
+      sp |= D > ulo && !above;
+      m = fmaxf(m, D);
+    }
+    if (!sp && !(m >= mlo)) {
+      K.cnt = cnt;
+      return;
+    }
+  }
   unsigned keep = 0, special = 0;
 #pragma unroll
   for (int i = 0; i < kTilePer; ++i) {
@@ -1353,6 +1374,7 @@ __device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0
     }
   }
   K.keep = keep;
+  K.cnt = __popc(keep);
 }
 
 // per tile, from the work decomposition alone (it runs before the
@@ -1416,7 +1438,7 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COUNT_MINB) k_tile_count(Com
     const long long tile = t0 + u;
     if (tile * kTile >= p.n_cand) break;               // warp-uniform
     tile_decide<false>(p, tile * kTile + (long long)lane * kTilePer, tile, K[u]);
-    int c = __popc(K[u].keep);
+    int c = K[u].cnt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0) tile_cnt[tile] = c;
