@@ -1280,6 +1280,18 @@ __device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0
   float ulo = 0.0f, uhi = 0.0f, mlo = 0.0f;
   if (!kCols) { ulo = thr1 * kLo; uhi = thr1 * kHi; mlo = thr1 * p.inv_tau_m; }
   int nx = next >= n ? kTilePer : (int)min(next - p0, (long long)kTilePer);
+  if (kCols && nx >= kTilePer) {
+    // write pass, the common case: one row for the lane's candidates
+    unsigned kp = 0;
+#pragma unroll
+    for (int i = 0; i < kTilePer; ++i)
+      if (K.D[i] >= thr1) {
+        kp |= 1u << i;
+        if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
+      }
+    K.keep = kp;
+    return;
+  }
   if (!kCols && nx >= kTilePer) {
     // count pass, the common case: one row for the lane's candidates; count
     // them, and fall through to the per-candidate flags only when one lies
