@@ -614,13 +614,15 @@ __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, l
     if (li < nl) {
       int iy, iz;
       line_yz(R, l0 + li, inv_nyb, iy, iz);
-      ff s0, x0, z0;
-      line_base(R, iy, iz, s0, x0, z0);
       len[q] = line_interval(R, mode, nx, iy, iz, lo[q]);
-      cb[q] = nx * (iy + ny * iz);
-      sfl[q] = R.sfx0 + (long long)iy * R.sfx_s[1] + (long long)iz * R.sfx_s[2];
-      sm.sx[li] = make_float4(R.tA_f + s0.hi, 0.0f, x0.hi, z0.hi);
-      sm.zc[li] = make_float4(x0.lo, z0.lo, 0.0f, 0.0f);
+      if (len[q] > 0) {                  // an empty line's record is never read
+        ff s0, x0, z0;
+        line_base(R, iy, iz, s0, x0, z0);
+        cb[q] = nx * (iy + ny * iz);
+        sfl[q] = R.sfx0 + (long long)iy * R.sfx_s[1] + (long long)iz * R.sfx_s[2];
+        sm.sx[li] = make_float4(R.tA_f + s0.hi, 0.0f, x0.hi, z0.hi);
+        sm.zc[li] = make_float4(x0.lo, z0.lo, 0.0f, 0.0f);
+      }
     }
     mine += len[q];
   }
