@@ -36,7 +36,8 @@ namespace dsc {
 __global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
 __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
-__global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*, const int*);
+__global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*);
+__global__ void k_slices(const DInst*, DRow*, int, int*, int*, int, int*);
 __global__ void k_item_rows(const long long*, int, int*);
 __global__ void k_tile_map(const long long*, const long long*, long long, const int*, long long*, long long*,
                            long long*, int*, int*);
@@ -223,6 +224,9 @@ struct Plan {
   DBeam* d_beams = nullptr;
   DRow* d_rows = nullptr;
   int* d_row_items = nullptr;
+  int* d_slice_pre = nullptr;        // per row: lines before each z-slice of its box (k_slices)
+  int* d_slice_lo = nullptr;         // per row: first iy of each z-slice's lines
+  int slice_stride = 0;              // entries per row: the largest nz + 1
   long long* d_row_item_base = nullptr;
   float* d_tables = nullptr;
   int* d_item_cand = nullptr;
@@ -278,7 +282,8 @@ struct Plan {
   }
   ~Plan() {
     free_scratch();
-    void* ps[] = {d_inst, d_beams, d_rows, d_row_items, d_row_item_base, d_tables, d_row_max, d_row_cand, d_scan,
+    void* ps[] = {d_inst, d_beams, d_rows, d_row_items, d_slice_pre, d_slice_lo, d_row_item_base, d_tables, d_row_max,
+                  d_row_cand, d_scan,
                   d_counter, d_slot, d_rcount, d_mcount, d_mslot, d_ovf_rows, d_row_max64};
     release_after(last_done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
     if (last_done) cudaEventDestroy(last_done);
@@ -288,6 +293,8 @@ struct Plan {
     if (ev_join) cudaEventDestroy(ev_join);
   }
 };
+
+static SliceTab slice_tab(const Plan* P) { return SliceTab{P->d_slice_pre, P->d_slice_lo, P->slice_stride}; }
 
 // ---------------------------------------------------------------------------
 // plan cache
@@ -582,6 +589,10 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_beams, P->nbeams, s));
   TRY(dalloc(&P->d_rows, P->nrows, s));
   TRY(dalloc(&P->d_row_items, P->nrows, s));
+  P->slice_stride = 2;
+  for (const DInst& I : P->h_inst) P->slice_stride = std::max(P->slice_stride, I.nz + 1);
+  TRY(dalloc(&P->d_slice_pre, (size_t)P->nrows * P->slice_stride, s));
+  TRY(dalloc(&P->d_slice_lo, (size_t)P->nrows * P->slice_stride, s));
   TRY(dalloc(&P->d_row_item_base, P->nrows + 1, s));
   TRY(dalloc(&P->d_tables, (size_t)P->nrows * P->stride, s));
   TRY(dalloc(&P->d_row_max, P->nrows, s));
@@ -608,6 +619,9 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
                                                  P->d_row_items, P->target_cand);
   CHECK_LAUNCH();
+  k_slices<<<(P->nrows + 3) / 4, 128, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_slice_pre, P->d_slice_lo,
+                                              P->slice_stride, P->d_row_items);
+  CHECK_LAUNCH();
   TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s, P->nrows));
   CU(cudaMemcpyAsync(&P->n_items, P->d_row_item_base + P->nrows, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
@@ -626,8 +640,9 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   P->grid_items = std::min(std::max(1, nb), 8) * sms;
   k_item_rows<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_row_item_base, P->nrows, P->d_item_row);
   CHECK_LAUNCH();
-  k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, P->d_row_item_base, P->nrows,
-                                                 P->d_row_item_base + P->nrows, P->d_item_cand, P->d_item_row);
+  k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, slice_tab(P.get()), P->d_row_item_base,
+                                                 P->nrows, P->d_row_item_base + P->nrows, P->d_item_cand,
+                                                 P->d_item_row);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_item_cand, P->d_row_item_base + P->nrows, 0, P->d_scan, P->d_item_off, s, P->n_items));
   CU(cudaMemcpyAsync(&P->n_cand, P->d_item_off + P->n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -731,6 +746,9 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
                                                  P->d_row_items, P->target_cand);
   CHECK_LAUNCH();
+  k_slices<<<(P->nrows + 3) / 4, 128, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_slice_pre, P->d_slice_lo,
+                                              P->slice_stride, P->d_row_items);
+  CHECK_LAUNCH();
   TRY(scan_launch(P->d_row_items, nullptr, P->nrows, P->d_scan, P->d_row_item_base, s, P->nrows));
   TRY(record(ev, 1, s));
   // a2: radiological-depth tables.  The captured sequence (no stage events)
@@ -753,8 +771,8 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   // a3: candidate pairs per work item
   k_item_rows<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_row_item_base, P->nrows, P->d_item_row);
   CHECK_LAUNCH();
-  k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, P->d_row_item_base, P->nrows, n_items,
-                                                 P->d_item_cand, P->d_item_row);
+  k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, slice_tab(P), P->d_row_item_base, P->nrows,
+                                                 n_items, P->d_item_cand, P->d_item_row);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_item_cand, n_items, 0, P->d_scan, P->d_item_off, s, P->n_items));
   k_tile_map<<<1024, 256, 0, s>>>(P->d_item_off, n_items, P->n_cand, P->d_item_row, P->d_tile_item0, P->d_tile_first,
@@ -766,6 +784,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   EvalParams ep{};
   ep.inst = P->d_inst;
   ep.rows = P->d_rows;
+  ep.slices = slice_tab(P);
   ep.tables = P->d_tables;
   ep.table_stride = P->stride;
   ep.row_item_base = P->d_row_item_base;

@@ -87,11 +87,23 @@ struct DRow {
   int ix0, ix1;
   int lpc;                 // lines per work item
   int nitems;
+  int nlines;              // x-lines enumerated: those of the box that can meet the VOI (k_slices)
+};
+
+// The x-lines of a row that can meet its VOI, slice by slice (k_slices):
+// for slice s = iz - iz0 of row r, slice_pre[r * stride + s] lines come
+// before it and its lines are iy = slice_lo[r * stride + s] + 0, 1, ...;
+// slice_pre[r * stride + nzr] is the row's total (nzr = iz1 - iz0 + 1).
+struct SliceTab {
+  const int* pre;
+  const int* lo;
+  int stride;
 };
 
 struct EvalParams {
   const DInst* inst;
   const DRow* rows;
+  SliceTab slices;
   const float* tables;      // [nrows][table_stride]
   int table_stride;
   const long long* row_item_base;  // nrows + 1

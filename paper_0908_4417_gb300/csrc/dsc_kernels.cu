@@ -223,9 +223,140 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
   }
   int lpc = (int)fmin((double)kMaxLinesPerItem, fmax(1.0, (double)target_cand / est));
   R.lpc = lpc;
+  // the box's lines; k_slices keeps only those that can meet the VOI
+  R.nlines = (int)lines;
   R.nitems = (int)((lines + lpc - 1) / lpc);
   rows[r] = R;
   row_items[r] = R.nitems;
+}
+
+// ---------------------------------------------------------------------------
+// k_slices: the x-lines of each row's voxel box that can meet its VOI, one
+// warp per row, a lane per z-slice.  At the slice's voxel-centre height the
+// VOI's cross-section is convex: the four lateral half-planes
+// |x'| <= kx t + bx, |z'| <= kz t + bz (linear in x and y at fixed z), cut to
+// the box's range of voxel centres in x and y.  The slice's lines are those
+// whose centre y lies within the polygon's y-extent, found from its
+// vertices.  FP32 with a margin of kSliceMargin mm: a line that the
+// evaluation's own FP32 interval test could give a candidate is never left
+// out (its rounding is far below the margin); a line kept by the margin may
+// still have none.  Without a lateral cutoff every line of the box is kept.
+// Writes the row's slice table, line count and work items (replacing the
+// box's).
+// ---------------------------------------------------------------------------
+constexpr float kSliceMargin = 0.02f;
+
+// y-extent at height zc of {A_k x + B_k y <= C_k, k < 8}, from the
+// feasible pairwise intersections (within tol); false when empty
+__device__ __forceinline__ bool polygon_y_extent(const float (&A)[8], const float (&B)[8], const float (&C)[8],
+                                                 float tol, float& ymin, float& ymax) {
+  bool any = false;
+  ymin = 3.0e38f;
+  ymax = -3.0e38f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < 8; ++j) {
+      const float det = A[i] * B[j] - A[j] * B[i];
+      if (fabsf(det) < 1e-9f) continue;
+      const float id = __frcp_rn(det);
+      const float x = (C[i] * B[j] - C[j] * B[i]) * id;
+      const float y = (A[i] * C[j] - A[j] * C[i]) * id;
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ok = ok && (A[k] * x + B[k] * y <= C[k] + tol);
+      if (ok) {
+        any = true;
+        ymin = fminf(ymin, y);
+        ymax = fmaxf(ymax, y);
+      }
+    }
+  }
+  return any;
+}
+
+__global__ void __launch_bounds__(128) k_slices(const DInst* __restrict__ inst, DRow* rows, int nrows, int* slice_pre,
+                                                int* slice_lo, int stride, int* row_items) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (r >= nrows) return;                              // warp-uniform
+  DRow& R = rows[r];
+  const DInst& G = inst[R.inst];
+  const bool box = R.hit && R.ix1 >= R.ix0 && R.iy1 >= R.iy0 && R.iz1 >= R.iz0;
+  const int nzr = box ? min(R.iz1 - R.iz0 + 1, stride - 1) : 0;
+  const int nyb = R.iy1 - R.iy0 + 1;
+  const bool cut = G.cutoff_mode != 2;
+  int* pre = slice_pre + (size_t)r * stride;
+  int* lo = slice_lo + (size_t)r * stride;
+  // the four lateral half-planes a.w <= b with w = p - S: a = +-x - k e,
+  // +-z - k e; in x and y at height zc: A x + B y <= b - a2 (zc - S2) + A S0 + B S1
+  float A[8], B[8], C0[8], Cz[8];
+  {
+    const float kx = R.kx, kz = R.kz;
+    const float e0 = (float)R.e[0], e1 = (float)R.e[1], e2 = (float)R.e[2];
+    const float x0 = (float)R.x[0], x1 = (float)R.x[1], x2 = (float)R.x[2];
+    const float z0 = (float)R.z[0], z1 = (float)R.z[1], z2 = (float)R.z[2];
+    const float S0 = (float)R.S[0], S1 = (float)R.S[1], S2 = (float)R.S[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float sg = (k & 1) ? -1.0f : 1.0f;             // +x', -x', +z', -z'
+      const float kk = k < 2 ? kx : kz;
+      const float u0 = k < 2 ? x0 : z0, u1 = k < 2 ? x1 : z1, u2 = k < 2 ? x2 : z2;
+      const float a0 = sg * u0 - kk * e0, a1 = sg * u1 - kk * e1, a2 = sg * u2 - kk * e2;
+      A[k] = a0;
+      B[k] = a1;
+      C0[k] = (k < 2 ? R.bx : R.bz) + a0 * S0 + a1 * S1 + a2 * S2;   // C = C0 - Cz zc
+      Cz[k] = a2;
+    }
+    // the box's voxel-centre range in x and y
+    const float xc0 = (float)(G.ox + (R.ix0 + 0.5) * G.dx), xc1 = (float)(G.ox + (R.ix1 + 0.5) * G.dx);
+    const float yc0 = (float)(G.oy + (R.iy0 + 0.5) * G.dy), yc1 = (float)(G.oy + (R.iy1 + 0.5) * G.dy);
+    A[4] = -1.0f; B[4] = 0.0f; C0[4] = -xc0; Cz[4] = 0.0f;
+    A[5] = 1.0f;  B[5] = 0.0f; C0[5] = xc1;  Cz[5] = 0.0f;
+    A[6] = 0.0f;  B[6] = -1.0f; C0[6] = -yc0; Cz[6] = 0.0f;
+    A[7] = 0.0f;  B[7] = 1.0f;  C0[7] = yc1;  Cz[7] = 0.0f;
+  }
+  const float dyi = (float)(1.0 / G.dy), oyh = (float)(G.oy + 0.5 * G.dy);
+  int run = 0;
+  for (int s0 = 0; s0 < nzr; s0 += 32) {               // warp-uniform
+    const int s = s0 + lane;
+    int cnt = 0, ylo = R.iy0;
+    if (s < nzr) {
+      if (!cut) {
+        cnt = nyb;
+      } else {
+        const float zc = (float)(G.oz + (R.iz0 + s + 0.5) * G.dz);
+        float C[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) C[k] = C0[k] - Cz[k] * zc;
+        float ymin, ymax;
+        if (polygon_y_extent(A, B, C, kSliceMargin, ymin, ymax)) {
+          // centres y = oy + (iy + 0.5) dy within [ymin - margin, ymax + margin]
+          const int a0 = (int)ceilf((ymin - kSliceMargin - oyh) * dyi);
+          const int a1 = (int)floorf((ymax + kSliceMargin - oyh) * dyi);
+          ylo = max(a0, R.iy0);
+          cnt = max(0, min(a1, R.iy1) - ylo + 1);
+        }
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (s < nzr) {
+      pre[s] = run + incl - cnt;
+      lo[s] = ylo;
+    }
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) {
+    pre[nzr] = run;
+    R.nlines = run;
+    R.nitems = (run + R.lpc - 1) / R.lpc;
+    row_items[r] = R.nitems;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -568,34 +699,57 @@ __device__ __forceinline__ int block_excl_scan(int v, int& excl, int* wscan) {
 // 2^31 lines: the grid has fewer than 2^31 voxels).  inv_nyb = 1 / (lines per
 // iz), correctly rounded.  Below 2^22 the FP32 quotient is within 1/2 of l /
 // nyb, so its truncation is off by at most one, which the remainder corrects.
-__device__ __forceinline__ float line_inv(const DRow& R) { return __frcp_rn((float)(R.iy1 - R.iy0 + 1)); }
-__device__ __forceinline__ void line_yz(const DRow& R, int l, float inv_nyb, int& iy, int& iz) {
-  const int nyb = R.iy1 - R.iy0 + 1;
-  int q, r;
-  if (l < (1 << 22)) {
-    q = (int)((float)l * inv_nyb);
-    r = l - q * nyb;
-    if (r < 0) { --q; r += nyb; }
-    else if (r >= nyb) { ++q; r -= nyb; }
-  } else {
-    q = (int)((unsigned)l / (unsigned)nyb);
-    r = l - q * nyb;
+// the slice of line l of a row: the last s with pre[s] <= l (nzr slices)
+__device__ __forceinline__ int line_slice(const int* __restrict__ pre, int nzr, int l) {
+  int s = 0;
+#pragma unroll 1
+  for (int step = nzr > 1 ? 1 << (31 - __clz(nzr - 1)) : 0; step > 0; step >>= 1)
+    if (s + step < nzr && pre[s + step] <= l) s += step;
+  return s;
+}
+// walks consecutive lines of a row through its slice table
+struct LineWalk {
+  const int* pre;
+  const int* lo;
+  int nzr;
+  int s = -1, first = 0, next = 0, ylo = 0;
+  __device__ LineWalk(const SliceTab& T, int row, int nzr_) : pre(T.pre + (size_t)row * T.stride),
+                                                             lo(T.lo + (size_t)row * T.stride), nzr(nzr_) {}
+  // (iy, iz) of line l; lines are visited in increasing order
+  __device__ __forceinline__ void at(const DRow& R, int l, int& iy, int& iz) {
+    if (s < 0) {
+      s = line_slice(pre, nzr, l);
+      first = pre[s];
+      next = pre[s + 1];
+      ylo = lo[s];
+    }
+    while (l >= next && s < nzr - 1) {                // also past empty slices
+      ++s;
+      first = next;
+      next = pre[s + 1];
+      ylo = lo[s];
+    }
+    iz = R.iz0 + s;
+    iy = ylo + (l - first);
   }
-  iz = R.iz0 + q;
-  iy = R.iy0 + r;
+};
+// nzr of a row as k_slices wrote its table
+__device__ __forceinline__ int row_slices(const DRow& R, int stride) {
+  const bool box = R.hit && R.ix1 >= R.ix0 && R.iy1 >= R.iy0 && R.iz1 >= R.iz0;
+  return box ? min(R.iz1 - R.iz0 + 1, stride - 1) : 0;
 }
 
 // lines of a work item: [chunk * lpc, min(+lpc, lines of the row))
 __device__ __forceinline__ int item_nlines(const DRow& R, long long chunk, int& l0) {
-  const int nlines = (R.iy1 - R.iy0 + 1) * (R.iz1 - R.iz0 + 1);
   l0 = (int)chunk * R.lpc;
-  return min(R.lpc, nlines - l0);
+  return min(R.lpc, R.nlines - l0);
 }
 
 // set up all lines of an item in shared memory (each thread takes kMaxLinesPerItem /
 // kEvalThreads consecutive lines), rebased on the item's candidate index;
 // returns the candidate count
-__device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, long long chunk) {
+__device__ int item_lines(LineSm& sm, const DRow& R, const SliceTab& T, int row, int mode, int nx, int ny,
+                          long long chunk) {
   constexpr int per = kMaxLinesPerItem / kEvalThreads;
   int l0;
   int nl = item_nlines(R, chunk, l0);
@@ -603,7 +757,7 @@ __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, l
   int len[per], lo[per], cb[per];
   long long sfl[per];
   int mine = 0;
-  const float inv_nyb = line_inv(R);
+  LineWalk walk(T, row, row_slices(R, T.stride));
 #pragma unroll
   for (int q = 0; q < per; ++q) {
     int li = t * per + q;             // consecutive lines per thread keep the scan order
@@ -613,7 +767,7 @@ __device__ int item_lines(LineSm& sm, const DRow& R, int mode, int nx, int ny, l
     sfl[q] = 0;
     if (li < nl) {
       int iy, iz;
-      line_yz(R, l0 + li, inv_nyb, iy, iz);
+      walk.at(R, l0 + li, iy, iz);
       len[q] = line_interval(R, mode, nx, iy, iz, lo[q]);
       if (len[q] > 0) {                  // an empty line's record is never read
         ff s0, x0, z0;
@@ -731,9 +885,9 @@ __global__ void k_item_rows(const long long* __restrict__ row_item_base, int nro
 // k_count: candidate pairs per work item, one warp per item
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict__ inst, const DRow* __restrict__ rows,
-                                                        const long long* __restrict__ row_item_base, int nrows,
-                                                        const long long* __restrict__ n_items, int* item_cand,
-                                                        const int* __restrict__ item_row) {
+                                                        SliceTab T, const long long* __restrict__ row_item_base,
+                                                        int nrows, const long long* __restrict__ n_items,
+                                                        int* item_cand, const int* __restrict__ item_row) {
   const long long ni = *n_items;
   const int lane = threadIdx.x & 31;
   const long long nw = (long long)gridDim.x * (kEvalThreads / 32);
@@ -744,10 +898,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
     int l0;
     int nl = item_nlines(R, item - row_item_base[row], l0);
     int cnt = 0;
-    const float inv_nyb = line_inv(R);
-    for (int li = lane; li < nl; li += 32) {
+    // each lane takes consecutive lines, so it walks its slices from one search
+    constexpr int lpl = kMaxLinesPerItem / 32;
+    LineWalk walk(T, row, row_slices(R, T.stride));
+    for (int li = lane * lpl; li < min(nl, (lane + 1) * lpl); ++li) {
       int iy, iz;
-      line_yz(R, l0 + li, inv_nyb, iy, iz);
+      walk.at(R, l0 + li, iy, iz);
       int lo;
       cnt += line_interval(R, G.cutoff_mode, G.nx, iy, iz, lo);
     }
@@ -1049,7 +1205,7 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_EVAL_MINBLOCKS) k_eval(EvalP
     // read before item_lines' barriers; thread 0 updates it after them
     const bool lut_stale = sm.lut_inst != R.inst;
 #endif
-    const int total = min(item_lines(sm, R, mode, G.nx, G.ny, item - p.row_item_base[row]),
+    const int total = min(item_lines(sm, R, p.slices, row, mode, G.nx, G.ny, item - p.row_item_base[row]),
                           (int)(p.item_off[item + 1] - a_off));   // never past the counted range
     RowConst C;
     load_row_const(C, R, G, p.tables + (size_t)row * p.table_stride);

@@ -28,7 +28,8 @@ namespace dsc {
 __global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
 __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
-__global__ void k_count(const DInst*, const DRow*, const long long*, int, const long long*, int*, const int*);
+__global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*);
+__global__ void k_slices(const DInst*, DRow*, int, int*, int*, int, int*);
 __global__ void k_item_rows(const long long*, int, int*);
 __global__ void k_tile_map(const long long*, const long long*, long long, const int*, long long*, long long*,
                            long long*, int*, int*);
@@ -49,10 +50,10 @@ __global__ void k_scan_small(const int*, const long long*, long long, long long*
 using namespace dsc;
 
 
-// The fixed working memory: 64 MiB per device.  Every call uses it from the
+// The fixed working memory: 80 MiB per device.  Every call uses it from the
 // start, so calls whose device work overlaps (different streams, or
 // different host threads) race on it; serialise them on one stream.
-static constexpr size_t kNoAllocBytes = 64ull << 20;
+static constexpr size_t kNoAllocBytes = 80ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 static std::mutex g_na_mu;
@@ -225,6 +226,10 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   DBeam* d_beams = cv.take<DBeam>(nbeams);
   DRow* d_rows = cv.take<DRow>(nrows);
   int* d_row_items = cv.take<int>(nrows);
+  const int slice_stride = std::max(2, grid->nz + 1);
+  int* d_slice_pre = cv.take<int>((size_t)nrows * slice_stride);
+  int* d_slice_lo = cv.take<int>((size_t)nrows * slice_stride);
+  const SliceTab slices{d_slice_pre, d_slice_lo, slice_stride};
   long long* d_rib = cv.take<long long>(nrows + 1);
   float* d_tables = cv.take<float>((size_t)nrows * stride);
   long long* d_scan = cv.take<long long>(kScanBlocks + 1);
@@ -285,6 +290,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   // set-up and work items
   k_setup<<<(nrows + 31) / 32, 32, 0, s>>>(d_inst, d_beams, nbeams, d_rows, nrows, d_row_items, target_cand);
   NA_LAUNCH();
+  k_slices<<<(nrows + 3) / 4, 128, 0, s>>>(d_inst, d_rows, nrows, d_slice_pre, d_slice_lo, slice_stride, d_row_items);
+  NA_LAUNCH();
   st = na_scan(d_row_items, nullptr, nrows, d_scan, d_rib, s, nrows);
   if (st != DSC_OK) return st;
   long long n_items = 0;
@@ -305,7 +312,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   NA_LAUNCH();
   k_item_rows<<<(nrows + 127) / 128, 128, 0, s>>>(d_rib, nrows, d_item_row);
   NA_LAUNCH();
-  k_count<<<grid_items, kEvalThreads, 0, s>>>(d_inst, d_rows, d_rib, nrows, n_items_dev, d_item_cand, d_item_row);
+  k_count<<<grid_items, kEvalThreads, 0, s>>>(d_inst, d_rows, slices, d_rib, nrows, n_items_dev, d_item_cand,
+                                              d_item_row);
   NA_LAUNCH();
   st = na_scan(d_item_cand, n_items_dev, 0, d_scan, d_item_off, s, n_items);
   if (st != DSC_OK) return st;
@@ -334,6 +342,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   EvalParams ep{};
   ep.inst = d_inst;
   ep.rows = d_rows;
+  ep.slices = slices;
   ep.tables = d_tables;
   ep.table_stride = stride;
   ep.row_item_base = d_rib;
