@@ -247,33 +247,51 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
 constexpr float kSliceMargin = 0.02f;
 
 // y-extent at height zc of {A_k x + B_k y <= C_k, k < 8}, from the
-// feasible pairwise intersections (within tol); false when empty
-__device__ __forceinline__ bool polygon_y_extent(const float (&A)[8], const float (&B)[8], const float (&C)[8],
-                                                 float tol, float& ymin, float& ymax) {
+// feasible pairwise intersections (within tol).  The pairs are expanded at
+// compile time, so every index is a constant and the arrays stay in
+// registers; parallel box sides (4, 5) and (6, 7) have no vertex.
+struct YExtent {
   bool any = false;
-  ymin = 3.0e38f;
-  ymax = -3.0e38f;
+  float ymin = 3.0e38f, ymax = -3.0e38f;
+};
+template <int I, int J>
+__device__ __forceinline__ void pair_vertex(const float (&A)[8], const float (&B)[8], const float (&C)[8], float tol,
+                                            YExtent& ye) {
+  if ((I == 4 && J == 5) || (I == 6 && J == 7)) return;
+  const float det = A[I] * B[J] - A[J] * B[I];
+  if (fabsf(det) < 1e-9f) return;
+  const float id = __frcp_rn(det);
+  const float x = (C[I] * B[J] - C[J] * B[I]) * id;
+  const float y = (A[I] * C[J] - A[J] * C[I]) * id;
+  bool ok = true;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-#pragma unroll
-    for (int j = i + 1; j < 8; ++j) {
-      const float det = A[i] * B[j] - A[j] * B[i];
-      if (fabsf(det) < 1e-9f) continue;
-      const float id = __frcp_rn(det);
-      const float x = (C[i] * B[j] - C[j] * B[i]) * id;
-      const float y = (A[i] * C[j] - A[j] * C[i]) * id;
-      bool ok = true;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) ok = ok && (A[k] * x + B[k] * y <= C[k] + tol);
-      if (ok) {
-        any = true;
-        ymin = fminf(ymin, y);
-        ymax = fmaxf(ymax, y);
-      }
-    }
+  for (int k = 0; k < 8; ++k) ok = ok && (A[k] * x + B[k] * y <= C[k] + tol);
+  if (ok) {
+    ye.any = true;
+    ye.ymin = fminf(ye.ymin, y);
+    ye.ymax = fmaxf(ye.ymax, y);
   }
-  return any;
 }
+template <int I, int J>
+struct PolygonPairs {
+  static __device__ __forceinline__ void run(const float (&A)[8], const float (&B)[8], const float (&C)[8], float tol,
+                                             YExtent& ye) {
+    pair_vertex<I, J>(A, B, C, tol, ye);
+    PolygonPairs<I, J + 1>::run(A, B, C, tol, ye);
+  }
+};
+template <int I>
+struct PolygonPairs<I, 8> {
+  static __device__ __forceinline__ void run(const float (&A)[8], const float (&B)[8], const float (&C)[8], float tol,
+                                             YExtent& ye) {
+    PolygonPairs<I + 1, I + 2>::run(A, B, C, tol, ye);
+  }
+};
+template <>
+struct PolygonPairs<7, 8> {
+  static __device__ __forceinline__ void run(const float (&)[8], const float (&)[8], const float (&)[8], float,
+                                             YExtent&) {}
+};
 
 __global__ void __launch_bounds__(128) k_slices(const DInst* __restrict__ inst, DRow* rows, int nrows, int* slice_pre,
                                                 int* slice_lo, int stride, int* row_items) {
@@ -316,7 +334,8 @@ __global__ void __launch_bounds__(128) k_slices(const DInst* __restrict__ inst, 
     A[6] = 0.0f;  B[6] = -1.0f; C0[6] = -yc0; Cz[6] = 0.0f;
     A[7] = 0.0f;  B[7] = 1.0f;  C0[7] = yc1;  Cz[7] = 0.0f;
   }
-  const float dyi = (float)(1.0 / G.dy), oyh = (float)(G.oy + 0.5 * G.dy);
+  const float dyi = __frcp_rn((float)G.dy), oyh = (float)G.oy + 0.5f * (float)G.dy;
+  const float ozf = (float)G.oz, dzf = (float)G.dz;
   int run = 0;
   for (int s0 = 0; s0 < nzr; s0 += 32) {               // warp-uniform
     const int s = s0 + lane;
@@ -325,15 +344,16 @@ __global__ void __launch_bounds__(128) k_slices(const DInst* __restrict__ inst, 
       if (!cut) {
         cnt = nyb;
       } else {
-        const float zc = (float)(G.oz + (R.iz0 + s + 0.5) * G.dz);
+        const float zc = fmaf((float)(R.iz0 + s) + 0.5f, dzf, ozf);
         float C[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) C[k] = C0[k] - Cz[k] * zc;
-        float ymin, ymax;
-        if (polygon_y_extent(A, B, C, kSliceMargin, ymin, ymax)) {
+        YExtent ye;
+        PolygonPairs<0, 1>::run(A, B, C, kSliceMargin, ye);
+        if (ye.any) {
           // centres y = oy + (iy + 0.5) dy within [ymin - margin, ymax + margin]
-          const int a0 = (int)ceilf((ymin - kSliceMargin - oyh) * dyi);
-          const int a1 = (int)floorf((ymax + kSliceMargin - oyh) * dyi);
+          const int a0 = (int)ceilf((ye.ymin - kSliceMargin - oyh) * dyi);
+          const int a1 = (int)floorf((ye.ymax + kSliceMargin - oyh) * dyi);
           ylo = max(a0, R.iy0);
           cnt = max(0, min(a1, R.iy1) - ylo + 1);
         }

@@ -75,10 +75,10 @@ def slice_lines(g, S, e, x, z, kx, kz, bx, bz, box):
     B += [F(0), F(0), F(-1), F(1)]
     C0 += [-xc0, xc1, -yc0, yc1]
     Cz += [F(0)] * 4
-    dyi, oyh = F(1.0 / g.dy), F(g.origin[1] + 0.5 * g.dy)
+    dyi, oyh = F(1) / F(g.dy), F(g.origin[1]) + F(0.5) * F(g.dy)
     out = {}
     for iz in range(iz0, iz1 + 1):
-        zc = F(g.origin[2] + (iz + 0.5) * g.dz)
+        zc = (F(iz) + F(0.5)) * F(g.dz) + F(g.origin[2])
         C = [C0[k] - Cz[k] * zc for k in range(8)]
         ys = []
         for i in range(8):
