@@ -178,50 +178,63 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
   R.kx = (float)kx; R.kz = (float)kz; R.bx = (float)bx; R.bz = (float)bz;
 
   // voxel box of the VOI: between the smallest and largest t of the grid
-  // corners the VOI is the hull of its two end rectangles
+  // corners the VOI is the hull of its two end rectangles.  FP32: the box
+  // has a voxel of slack on every side, far above this rounding, and only
+  // bounds the lines that are tested.
   int ix0 = 0, ix1 = G.nx - 1, iy0 = 0, iy1 = G.ny - 1, iz0 = 0, iz1 = G.nz - 1;
-  double w_mid = 0.0;
+  float w_mid = 0.0f;
   if (hit && G.cutoff_mode != 2) {
-    double tlo = CUDART_INF, thi = -CUDART_INF;
+    const float Sf[3] = {(float)S[0], (float)S[1], (float)S[2]};
+    const float ef[3] = {(float)e[0], (float)e[1], (float)e[2]};
+    const float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
+    const float zf[3] = {(float)z[0], (float)z[1], (float)z[2]};
+    const float blf[3] = {(float)blo[0], (float)blo[1], (float)blo[2]};
+    const float bhf[3] = {(float)bhi[0], (float)bhi[1], (float)bhi[2]};
+    const float kxf = (float)kx, kzf = (float)kz, bxf = (float)bx, bzf = (float)bz;
+    float tlo = CUDART_INF_F, thi = -CUDART_INF_F;
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
-      double p[3] = {(c & 1) ? bhi[0] : blo[0], (c & 2) ? bhi[1] : blo[1], (c & 4) ? bhi[2] : blo[2]};
-      double w[3] = {p[0] - S[0], p[1] - S[1], p[2] - S[2]};
-      double t = dot3(w, e);
-      tlo = fmin(tlo, t);
-      thi = fmax(thi, t);
+      const float p0 = (c & 1) ? bhf[0] : blf[0], p1 = (c & 2) ? bhf[1] : blf[1], p2 = (c & 4) ? bhf[2] : blf[2];
+      const float t = (p0 - Sf[0]) * ef[0] + (p1 - Sf[1]) * ef[1] + (p2 - Sf[2]) * ef[2];
+      tlo = fminf(tlo, t);
+      thi = fmaxf(thi, t);
     }
-    tlo = fmax(tlo, 0.0);
-    double lo3[3] = {CUDART_INF, CUDART_INF, CUDART_INF}, hi3[3] = {-CUDART_INF, -CUDART_INF, -CUDART_INF};
+    tlo = fmaxf(tlo, 0.0f);
+    float lo3[3] = {CUDART_INF_F, CUDART_INF_F, CUDART_INF_F}, hi3[3] = {-CUDART_INF_F, -CUDART_INF_F, -CUDART_INF_F};
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
-      double t = (c & 1) ? thi : tlo;
-      double hx = kx * t + bx, hz = kz * t + bz;
-      double su = (c & 2) ? hx : -hx, sv = (c & 4) ? hz : -hz;
+      const float t = (c & 1) ? thi : tlo;
+      const float hx = kxf * t + bxf, hz = kzf * t + bzf;
+      const float su = (c & 2) ? hx : -hx, sv = (c & 4) ? hz : -hz;
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
-        double p = S[k] + t * e[k] + su * x[k] + sv * z[k];
-        lo3[k] = fmin(lo3[k], p);
-        hi3[k] = fmax(hi3[k], p);
+        const float p = Sf[k] + t * ef[k] + su * xf[k] + sv * zf[k];
+        lo3[k] = fminf(lo3[k], p);
+        hi3[k] = fmaxf(hi3[k], p);
       }
     }
-    ix0 = max(ix0, (int)floor((lo3[0] - G.ox) / G.dx - 0.5) - 1);
-    ix1 = min(ix1, (int)ceil((hi3[0] - G.ox) / G.dx - 0.5) + 1);
-    iy0 = max(iy0, (int)floor((lo3[1] - G.oy) / G.dy - 0.5) - 1);
-    iy1 = min(iy1, (int)ceil((hi3[1] - G.oy) / G.dy - 0.5) + 1);
-    iz0 = max(iz0, (int)floor((lo3[2] - G.oz) / G.dz - 0.5) - 1);
-    iz1 = min(iz1, (int)ceil((hi3[2] - G.oz) / G.dz - 0.5) + 1);
-    w_mid = 2.0 * (fmax(kx, kz) * 0.5 * (tlo + thi) + fmax(bx, bz));
+    const float dxi = __frcp_rn((float)G.dx), dyi = __frcp_rn((float)G.dy), dzi = __frcp_rn((float)G.dz);
+    ix0 = max(ix0, (int)floorf((lo3[0] - blf[0]) * dxi - 0.5f) - 1);
+    ix1 = min(ix1, (int)ceilf((hi3[0] - blf[0]) * dxi - 0.5f) + 1);
+    iy0 = max(iy0, (int)floorf((lo3[1] - blf[1]) * dyi - 0.5f) - 1);
+    iy1 = min(iy1, (int)ceilf((hi3[1] - blf[1]) * dyi - 0.5f) + 1);
+    iz0 = max(iz0, (int)floorf((lo3[2] - blf[2]) * dzi - 0.5f) - 1);
+    iz1 = min(iz1, (int)ceilf((hi3[2] - blf[2]) * dzi - 0.5f) + 1);
+    w_mid = 2.0f * (fmaxf(kxf, kzf) * 0.5f * (tlo + thi) + fmaxf(bxf, bzf));
   }
   R.ix0 = ix0; R.ix1 = ix1; R.iy0 = iy0; R.iy1 = iy1; R.iz0 = iz0; R.iz1 = iz1;
   long long lines = 0;
   if (hit && ix1 >= ix0 && iy1 >= iy0 && iz1 >= iz0) lines = (long long)(iy1 - iy0 + 1) * (iz1 - iz0 + 1);
   // expected candidates on one x-line: the VOI width over the sine of the
   // angle between the axis and x, at most the box's x extent
-  double nxb = (double)(ix1 - ix0 + 1);
-  double est = nxb;
+  const float nxb = (float)(ix1 - ix0 + 1);
+  float est = nxb;
   if (G.cutoff_mode != 2) {
-    double sn = sqrt(fmax(1.0 - e[0] * e[0], 1e-6));
-    est = fmin(nxb, fmax(1.0, w_mid / (sn * G.dx)));
+    const float e0f = (float)e[0];
+    const float sn = sqrtf(fmaxf(1.0f - e0f * e0f, 1e-6f));
+    est = fminf(nxb, fmaxf(1.0f, w_mid / (sn * (float)G.dx)));
   }
-  int lpc = (int)fmin((double)kMaxLinesPerItem, fmax(1.0, (double)target_cand / est));
+  int lpc = (int)fminf((float)kMaxLinesPerItem, fmaxf(1.0f, (float)target_cand / est));
   R.lpc = lpc;
   // the box's lines; k_slices keeps only those that can meet the VOI
   R.nlines = (int)lines;
