@@ -922,29 +922,34 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
                                                         int nrows, const long long* __restrict__ n_items,
                                                         int* item_cand, const int* __restrict__ item_row) {
   const long long ni = *n_items;
-  const int lane = threadIdx.x & 31;
-  const long long nw = (long long)gridDim.x * (kEvalThreads / 32);
-  for (long long item = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5); item < ni; item += nw) {
-    int row = item_row[item];
-    const DRow& R = rows[row];
-    const DInst& G = inst[R.inst];
-    int l0;
-    int nl = item_nlines(R, item - row_item_base[row], l0);
+  const int lane = threadIdx.x & 31, half = lane >> 4, sub = lane & 15;
+  // a half-warp per item, so that two items' dependent loads are in flight
+  const long long nh = (long long)gridDim.x * (kEvalThreads / 16);
+  for (long long base = ((long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5)) * 2; base < ni;
+       base += nh) {                                   // warp-uniform
+    const long long item = base + half;
     int cnt = 0;
-    // each lane takes consecutive lines, so it walks its slices from one search
-    constexpr int lpl = kMaxLinesPerItem / 32;
-    LineWalk walk(T, row, row_slices(R, T.stride));
-    for (int li = lane * lpl; li < min(nl, (lane + 1) * lpl); ++li) {
-      int iy, iz;
-      walk.at(R, l0 + li, iy, iz);
-      int lo;
-      cnt += line_interval(R, G.cutoff_mode, G.nx, iy, iz, lo);
+    if (item < ni) {
+      const int row = item_row[item];
+      const DRow& R = rows[row];
+      const DInst& G = inst[R.inst];
+      int l0;
+      const int nl = item_nlines(R, item - row_item_base[row], l0);
+      // each lane takes consecutive lines, so it walks its slices from one search
+      constexpr int lpl = kMaxLinesPerItem / 16;
+      LineWalk walk(T, row, row_slices(R, T.stride));
+      for (int li = sub * lpl; li < min(nl, (sub + 1) * lpl); ++li) {
+        int iy, iz;
+        walk.at(R, l0 + li, iy, iz);
+        int lo;
+        cnt += line_interval(R, G.cutoff_mode, G.nx, iy, iz, lo);
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    for (int o = 8; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);   // within the half
     // items are padded to a multiple of 4 candidates (the evaluation writes
     // aligned groups of 4; padding slots hold -1, never kept)
-    if (lane == 0) item_cand[item] = (cnt + 3) & ~3;
+    if (sub == 0 && item < ni) item_cand[item] = (cnt + 3) & ~3;
   }
 }
 
