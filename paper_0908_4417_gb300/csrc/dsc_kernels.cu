@@ -142,8 +142,12 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
     // fixed-point constants of the Siddon walk: the unit 2^-q mm keeps t_B
     // (plus one plane step) below 2^60 units; q <= 48 (3.6e-15 mm)
     double tmax = R.tB + fmax(G.dx, fmax(G.dy, G.dz)) * 2.0 + 1.0;
-    int q = min(max(60 - (int)ceil(log2(tmax)), 0), 48);
-    double fx = ldexp(1.0, q);
+    // ceil(log2(tmax)) from the exponent bits (tmax >= 1): the exponent, one
+    // more when the mantissa has any bit set; 2^q built the same way
+    const long long tb = __double_as_longlong(tmax);
+    const int cl2 = (int)((tb >> 52) & 0x7ff) - 1023 + ((tb & 0xfffffffffffffll) != 0);
+    int q = min(max(60 - cl2, 0), 48);
+    double fx = __longlong_as_double((long long)(q + 1023) << 52);
     R.fix_q = q;
     R.fx_tA = __double2ll_rn(R.tA * fx);
     R.fx_tB = __double2ll_rn(R.tB * fx);
@@ -162,7 +166,7 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
     R.Zs[k] = ff_from_double(sp[k] * z[k]);
   }
   {
-    const double u = ldexp(1.0, 32) / G.hd;        // fixed-point units per mm
+    const double u = 4294967296.0 / G.hd;          // fixed-point units per mm (2^32 / h)
     R.sfx0 = __double2ll_rn((dot3(w0, e) - R.tA) * u);
     for (int k = 0; k < 3; ++k) R.sfx_s[k] = __double2ll_rn(sp[k] * e[k] * u);
   }

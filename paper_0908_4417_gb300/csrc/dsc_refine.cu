@@ -48,6 +48,8 @@ __device__ double tail2(int profile, double y) {
 // result is valid in every lane of the half; both halves must call together.
 __device__ double eval_pair64_half(const DRow& R, const DInst& G, const DBeam& B, const float* tab, int col,
                                    int sub) {
+  // reciprocals independent of the pair, off its dependency chain
+  const double ihd = 1.0 / G.hd, glut = (G.n_lut - 1) / G.d_max, isad = 1.0 / B.sad;
   const long long nxy = (long long)G.nx * G.ny;
   const int iz = (int)(col / nxy);
   const int rem = (int)(col - (long long)iz * nxy);
@@ -63,7 +65,7 @@ __device__ double eval_pair64_half(const DRow& R, const DInst& G, const DBeam& B
   double d = 0.0;
   const double s = t - R.tA;
   if (R.n_table > 0 && s > 0.0) {
-    const double f = s / G.hd, kf = floor(f);
+    const double f = s * ihd, kf = floor(f);
     if (!(kf < R.n_table - 1)) {                     // also a NaN s: the last entry
       d = tab[R.n_table - 1];
     } else {
@@ -73,7 +75,7 @@ __device__ double eval_pair64_half(const DRow& R, const DInst& G, const DBeam& B
   }
   // beam model at d: T and c3_1..3, linearly between rows, the last row beyond
   double T, c3[3];
-  double g = d * (G.n_lut - 1) / G.d_max;
+  double g = d * glut;
   if (!(g > 0.0)) g = 0.0;                            // also a NaN depth: the first row
   if (g >= G.n_lut - 1) {
     const float4 r = G.lut_rows[G.n_lut - 1];
@@ -94,7 +96,7 @@ __device__ double eval_pair64_half(const DRow& R, const DInst& G, const DBeam& B
     const int i = sub >> 2;
     const bool zax = (sub & 2) != 0, second = (sub & 1) != 0;
     const double side = zax ? B.b : B.a;
-    const double h = 0.5 * G.c2d[i] * side * t / B.sad;             // c2 a_t / 2 (b_t for Z)
+    const double h = 0.5 * G.c2d[i] * side * t * isad;              // c2 a_t / 2 (b_t for Z)
     const double sc = G.profile == 1 ? c3[i] / kSqrt2 : (G.profile == 2 ? c3[i] * kSqrt3OverPi : c3[i]);
     const double ax = fabs(zax ? zp : xp);
     const double y = second ? (ax + h) / sc : (ax - h) / sc;
