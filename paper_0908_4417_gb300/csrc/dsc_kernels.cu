@@ -1180,7 +1180,6 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
 template <int PROF, bool TS, bool SIG>
 __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm, int w0, int wl, float* out,
                                             int* outc, float& vmax, int& valid) {
-  const int nl1 = sm.nl - 1;
   for (int g = 4 * (int)threadIdx.x; g < wl; g += 4 * kEvalThreads) {
     const int jj = w0 + g;                              // item-relative index of the group's first candidate
     const unsigned mmb = *reinterpret_cast<const unsigned*>(sm.map + g);
@@ -1189,7 +1188,10 @@ __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm,
     int col[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int li = min(lidx[k], nl1);                 // entries past wl are stale: any line will do
+      // every entry holds a line of the item: position 0 of a window always
+      // starts one, and the scan carries it on (past wl: the last line); a
+      // byte index is in range of the 256-entry records in any case
+      const int li = lidx[k];
       const float4 A = sm.sx[li], B = sm.zc[li];
       const int j = jj + k;
       const int ix = __float_as_int(B.z) + j;
