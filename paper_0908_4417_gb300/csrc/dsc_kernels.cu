@@ -665,40 +665,62 @@ __device__ __forceinline__ void line_base(const DRow& R, int iy, int iz, ff& s0,
   z0 = ff_add(ff_add(R.Z0, ff_mul_i(R.Zs[1], fy)), ff_mul_i(R.Zs[2], fz));
 }
 
-// t, x', z' of x-line (iy, iz) at ix = 0 in plain FP32: the inputs of its
-// candidate interval.  Their error (about 1e-4 mm) is far inside the 1e-3 mm
-// band around the cutoff that parity leaves open, and the enumeration count
-// and the evaluation both take the interval from these, so they agree exactly.
-__device__ __forceinline__ void line_base32(const DRow& R, int iy, int iz, float& T0, float& X0, float& Z0) {
-  const float fy = (float)iy, fz = (float)iz;
-  T0 = R.tA_f + fmaf(R.Ss[2].hi, fz, fmaf(R.Ss[1].hi, fy, R.S0.hi));
-  X0 = fmaf(R.Xs[2].hi, fz, fmaf(R.Xs[1].hi, fy, R.X0.hi));
-  Z0 = fmaf(R.Zs[2].hi, fz, fmaf(R.Zs[1].hi, fy, R.Z0.hi));
-}
+// the row constants of a line's candidate interval: the FP32 bases and
+// steps of t, x', z' and the slopes c of the four lateral constraints along
+// x with their reciprocals.  A loop over a row's lines loads them once.
+struct LineCut {
+  float tA, S0, Sy, Sz, X0, Xy, Xz, Z0, Zy, Zz;
+  float kx, bx, kz, bz;
+  float c[4], rc[4];
+  float tx, rtx;
+  int mode, nx;
+  __device__ __forceinline__ LineCut(const DRow& R, int mode_, int nx_) : mode(mode_), nx(nx_) {
+    tA = R.tA_f;
+    S0 = R.S0.hi; Sy = R.Ss[1].hi; Sz = R.Ss[2].hi;
+    X0 = R.X0.hi; Xy = R.Xs[1].hi; Xz = R.Xs[2].hi;
+    Z0 = R.Z0.hi; Zy = R.Zs[1].hi; Zz = R.Zs[2].hi;
+    kx = R.kx; bx = R.bx; kz = R.kz; bz = R.bz;
+    tx = R.Ss[0].hi;
+    const float xx = R.Xs[0].hi, zx = R.Zs[0].hi;
+    c[0] = fmaf(-kx, tx, xx);
+    c[1] = fmaf(-kx, tx, -xx);
+    c[2] = fmaf(-kz, tx, zx);
+    c[3] = fmaf(-kz, tx, -zx);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rc[k] = rcp_approx(c[k]);
+    rtx = rcp_approx(tx);
+  }
+};
 
 // candidate interval [lo, lo + len) of x-line (iy, iz)
-__device__ __forceinline__ int line_interval(const DRow& R, int mode, int nx, int iy, int iz, int& lo_out) {
-  // t(i) = T0 + i tx, x'(i) = X0 + i xx, z'(i) = Z0 + i zx; constraints c i <= r
-  float T0, X0, Z0;
-  line_base32(R, iy, iz, T0, X0, Z0);
-  const float tx = R.Ss[0].hi, xx = R.Xs[0].hi, zx = R.Zs[0].hi;
-  float lo = 0.0f, hi = (float)(nx - 1);
+__device__ __forceinline__ int line_interval(const LineCut& L, int iy, int iz, int& lo_out) {
+  // t(i) = T0 + i tx, x'(i) = X0 + i xx, z'(i) = Z0 + i zx; constraints c i <= r.
+  // T0, X0, Z0 at ix = 0 in plain FP32: their error (about 1e-4 mm) is far
+  // inside the 1e-3 mm band around the cutoff that parity leaves open, and the
+  // enumeration count and the evaluation both take the interval from here, so
+  // they agree exactly
+  const float fy = (float)iy, fz = (float)iz;
+  const float T0 = L.tA + fmaf(L.Sz, fz, fmaf(L.Sy, fy, L.S0));
+  const float X0 = fmaf(L.Xz, fz, fmaf(L.Xy, fy, L.X0));
+  const float Z0 = fmaf(L.Zz, fz, fmaf(L.Zy, fy, L.Z0));
+  float lo = 0.0f, hi = (float)(L.nx - 1);
   bool empty = false;
-  auto constrain = [&](float c, float r) {
-    float q = r * rcp_approx(c);
-    if (c > 0.0f) hi = fminf(hi, q);
-    else if (c < 0.0f) lo = fmaxf(lo, q);
+  auto constrain = [&](int k, float r) {
+    const float q = r * L.rc[k];
+    if (L.c[k] > 0.0f) hi = fminf(hi, q);
+    else if (L.c[k] < 0.0f) lo = fmaxf(lo, q);
     else if (r < 0.0f) empty = true;
   };
-  if (mode != 2) {
-    constrain(fmaf(-R.kx, tx, xx), fmaf(R.kx, T0, R.bx) - X0);
-    constrain(fmaf(-R.kx, tx, -xx), fmaf(R.kx, T0, R.bx) + X0);
-    constrain(fmaf(-R.kz, tx, zx), fmaf(R.kz, T0, R.bz) - Z0);
-    constrain(fmaf(-R.kz, tx, -zx), fmaf(R.kz, T0, R.bz) + Z0);
+  if (L.mode != 2) {
+    const float rx = fmaf(L.kx, T0, L.bx), rz = fmaf(L.kz, T0, L.bz);
+    constrain(0, rx - X0);
+    constrain(1, rx + X0);
+    constrain(2, rz - Z0);
+    constrain(3, rz + Z0);
   } else {
     // t > 0 (voxels in front of the source)
-    if (tx > 0.0f) lo = fmaxf(lo, floorf(-T0 * rcp_approx(tx)) + 1.0f);
-    else if (tx < 0.0f) hi = fminf(hi, ceilf(-T0 * rcp_approx(tx)) - 1.0f);
+    if (L.tx > 0.0f) lo = fmaxf(lo, floorf(-T0 * L.rtx) + 1.0f);
+    else if (L.tx < 0.0f) hi = fminf(hi, ceilf(-T0 * L.rtx) - 1.0f);
     else if (T0 <= 0.0f) empty = true;
   }
   int ilo = (int)ceilf(lo), ihi = (int)floorf(hi);
@@ -795,6 +817,7 @@ __device__ int item_lines(LineSm& sm, const DRow& R, const SliceTab& T, int row,
   long long sfl[per];
   int mine = 0;
   LineWalk walk(T, row, row_slices(R, T.stride));
+  const LineCut L(R, mode, nx);
 #pragma unroll
   for (int q = 0; q < per; ++q) {
     int li = t * per + q;             // consecutive lines per thread keep the scan order
@@ -805,7 +828,7 @@ __device__ int item_lines(LineSm& sm, const DRow& R, const SliceTab& T, int row,
     if (li < nl) {
       int iy, iz;
       walk.at(R, l0 + li, iy, iz);
-      len[q] = line_interval(R, mode, nx, iy, iz, lo[q]);
+      len[q] = line_interval(L, iy, iz, lo[q]);
       if (len[q] > 0) {                  // an empty line's record is never read
         ff s0, x0, z0;
         line_base(R, iy, iz, s0, x0, z0);
@@ -942,11 +965,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
       // each lane takes consecutive lines, so it walks its slices from one search
       constexpr int lpl = kMaxLinesPerItem / 16;
       LineWalk walk(T, row, row_slices(R, T.stride));
+      const LineCut L(R, G.cutoff_mode, G.nx);
       for (int li = sub * lpl; li < min(nl, (sub + 1) * lpl); ++li) {
         int iy, iz;
         walk.at(R, l0 + li, iy, iz);
         int lo;
-        cnt += line_interval(R, G.cutoff_mode, G.nx, iy, iz, lo);
+        cnt += line_interval(L, iy, iz, lo);
       }
     }
 #pragma unroll

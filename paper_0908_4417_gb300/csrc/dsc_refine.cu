@@ -31,85 +31,105 @@ namespace {
 constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr double kSqrt3OverPi = 0.55132889542179204315;   // sqrt 3 / pi
 
-// 2 G(y) for y >= 0: the tail of the lateral kernel in units of its scale s
-__device__ double tail2(int profile, double y) {
-  if (profile == 1) return exp(-y);                      // Laplace
+// 2 G(u s) for u >= 0: the tail of the lateral kernel at a distance of u
+// times its scale s, from the argument w = u * kTailArg[profile]
+__device__ double tail2(int profile, double w) {
+  if (profile == 1) return exp(-w);                      // Laplace
   if (profile == 2) {                                    // logistic
-    const double e = exp(-y);
+    const double e = exp(-w);
     return 2.0 * e / (1.0 + e);
   }
-  return erfc(y / kSqrt2);                               // Gaussian: s = c3
+  return erfc(w);                                        // Gaussian: w = u / sqrt 2
 }
 
-// D for the pair (row R, voxel col) in FP64, one half-warp per pair: every
-// lane forms the geometry, depth and beam model; sub-lanes 0..11 take one
-// tail each (term i = sub / 4; 4i, 4i+1: X at y1, y2; 4i+2, 4i+3: Z), and
-// the sum of Eq. 3 is formed from the tails shuffled within the half.  The
-// result is valid in every lane of the half; both halves must call together.
+// D for the pair (row R, voxel col) in FP64, one half-warp per pair.  The
+// FP64 pipe runs two threads per cycle per SM, so each step runs on as few
+// lanes as it needs: sub-lane 0 forms the geometry, the depth and the beam
+// model, and the reciprocal scales of the three terms, and broadcasts them;
+// sub-lanes 0..11 take one tail each (term i = sub / 4; 4i, 4i+1: X at y1,
+// y2; 4i+2, 4i+3: Z); sub-lane 0 forms the sum of Eq. 3 from the tails
+// shuffled within the half.  The result is valid in sub-lane 0 of each half;
+// both halves must call together.
 __device__ double eval_pair64_half(const DRow& R, const DInst& G, const DBeam& B, const float* tab, int col,
                                    int sub) {
-  // reciprocals independent of the pair, off its dependency chain
-  const double ihd = 1.0 / G.hd, glut = (G.n_lut - 1) / G.d_max, isad = 1.0 / B.sad;
-  const long long nxy = (long long)G.nx * G.ny;
-  const int iz = (int)(col / nxy);
-  const int rem = (int)(col - (long long)iz * nxy);
-  const int iy = rem / G.nx, ix = rem - iy * G.nx;
-  // voxel centre relative to the source; t, x', z' on the beamlet frame (Fig. 1)
-  const double w0 = G.ox + (ix + 0.5) * G.dx - R.S[0];
-  const double w1 = G.oy + (iy + 0.5) * G.dy - R.S[1];
-  const double w2 = G.oz + (iz + 0.5) * G.dz - R.S[2];
-  const double t = w0 * R.e[0] + w1 * R.e[1] + w2 * R.e[2];
-  const double xp = w0 * R.x[0] + w1 * R.x[1] + w2 * R.x[2];
-  const double zp = w0 * R.z[0] + w1 * R.z[1] + w2 * R.z[2];
-  // radiological depth at O' (Section 2.2): the table, linearly
-  double d = 0.0;
-  const double s = t - R.tA;
-  if (R.n_table > 0 && s > 0.0) {
-    const double f = s * ihd, kf = floor(f);
-    if (!(kf < R.n_table - 1)) {                     // also a NaN s: the last entry
-      d = tab[R.n_table - 1];
-    } else {
-      const int k = (int)kf;
-      d = (double)tab[k] + (f - kf) * ((double)tab[k + 1] - (double)tab[k]);
+  double t = 0.0, xp = 0.0, zp = 0.0, ts = 0.0, T = 0.0, is0 = 0.0, is1 = 0.0, is2 = 0.0;
+  if (sub == 0) {
+    // reciprocals independent of the pair, off its dependency chain
+    const double ihd = 1.0 / G.hd, glut = (G.n_lut - 1) / G.d_max, isad = 1.0 / B.sad;
+    const int nxy = G.nx * G.ny;
+    const int iz = col / nxy;
+    const int rem = col - iz * nxy;
+    const int iy = rem / G.nx, ix = rem - iy * G.nx;
+    // voxel centre relative to the source; t, x', z' on the beamlet frame (Fig. 1)
+    const double w0 = G.ox + (ix + 0.5) * G.dx - R.S[0];
+    const double w1 = G.oy + (iy + 0.5) * G.dy - R.S[1];
+    const double w2 = G.oz + (iz + 0.5) * G.dz - R.S[2];
+    t = w0 * R.e[0] + w1 * R.e[1] + w2 * R.e[2];
+    xp = w0 * R.x[0] + w1 * R.x[1] + w2 * R.x[2];
+    zp = w0 * R.z[0] + w1 * R.z[1] + w2 * R.z[2];
+    ts = 0.5 * t * isad;                                 // half the field width per unit side at t
+    // radiological depth at O' (Section 2.2): the table, linearly
+    double d = 0.0;
+    const double s = t - R.tA;
+    if (R.n_table > 0 && s > 0.0) {
+      const double f = s * ihd, kf = floor(f);
+      if (!(kf < R.n_table - 1)) {                   // also a NaN s: the last entry
+        d = tab[R.n_table - 1];
+      } else {
+        const int k = (int)kf;
+        d = (double)tab[k] + (f - kf) * ((double)tab[k + 1] - (double)tab[k]);
+      }
     }
+    // beam model at d: T and c3_1..3, linearly between rows, the last row beyond
+    double c3[3];
+    double g = d * glut;
+    if (!(g > 0.0)) g = 0.0;                          // also a NaN depth: the first row
+    if (g >= G.n_lut - 1) {
+      const float4 r = G.lut_rows[G.n_lut - 1];
+      T = r.x; c3[0] = r.y; c3[1] = r.z; c3[2] = r.w;
+    } else {
+      const int k = (int)floor(g);
+      const double wt = g - k;
+      const float4 a = G.lut_rows[k], b = G.lut_rows[k + 1];
+      T = a.x + wt * ((double)b.x - a.x);
+      c3[0] = a.y + wt * ((double)b.y - a.y);
+      c3[1] = a.z + wt * ((double)b.z - a.z);
+      c3[2] = a.w + wt * ((double)b.w - a.w);
+    }
+    // the tail argument per unit distance: 1 / (s kTailArg), s the term's
+    // scale (c3 for the Gaussian, c3 / sqrt 2 Laplace, c3 sqrt 3 / pi logistic)
+    const double k = G.profile == 1 ? 1.0 / kSqrt2 : (G.profile == 2 ? kSqrt3OverPi : kSqrt2);
+    is0 = 1.0 / (c3[0] * k);
+    is1 = 1.0 / (c3[1] * k);
+    is2 = 1.0 / (c3[2] * k);
   }
-  // beam model at d: T and c3_1..3, linearly between rows, the last row beyond
-  double T, c3[3];
-  double g = d * glut;
-  if (!(g > 0.0)) g = 0.0;                            // also a NaN depth: the first row
-  if (g >= G.n_lut - 1) {
-    const float4 r = G.lut_rows[G.n_lut - 1];
-    T = r.x; c3[0] = r.y; c3[1] = r.z; c3[2] = r.w;
-  } else {
-    const int k = (int)floor(g);
-    const double wt = g - k;
-    const float4 a = G.lut_rows[k], b = G.lut_rows[k + 1];
-    T = a.x + wt * ((double)b.x - a.x);
-    c3[0] = a.y + wt * ((double)b.y - a.y);
-    c3[1] = a.z + wt * ((double)b.z - a.z);
-    c3[2] = a.w + wt * ((double)b.w - a.w);
-  }
+  t = __shfl_sync(0xffffffffu, t, 0, 16);
+  xp = __shfl_sync(0xffffffffu, xp, 0, 16);
+  zp = __shfl_sync(0xffffffffu, zp, 0, 16);
+  ts = __shfl_sync(0xffffffffu, ts, 0, 16);
+  is0 = __shfl_sync(0xffffffffu, is0, 0, 16);
+  is1 = __shfl_sync(0xffffffffu, is1, 0, 16);
+  is2 = __shfl_sync(0xffffffffu, is2, 0, 16);
   // this lane's tail: 2 G(y) with y1 = (|x| - h) / s, y2 = (|x| + h) / s,
   // 2 G(y) = 2 - 2 G(-y) for y < 0 (the tails never cancel)
   double v = 0.0;
   if (sub < 12) {
     const int i = sub >> 2;
     const bool zax = (sub & 2) != 0, second = (sub & 1) != 0;
-    const double side = zax ? B.b : B.a;
-    const double h = 0.5 * G.c2d[i] * side * t * isad;              // c2 a_t / 2 (b_t for Z)
-    const double sc = G.profile == 1 ? c3[i] / kSqrt2 : (G.profile == 2 ? c3[i] * kSqrt3OverPi : c3[i]);
+    const double h = G.c2d[i] * (zax ? B.b : B.a) * ts;           // c2 a_t / 2 (b_t for Z)
     const double ax = fabs(zax ? zp : xp);
-    const double y = second ? (ax + h) / sc : (ax - h) / sc;
-    v = y >= 0.0 ? tail2(G.profile, y) : 2.0 - tail2(G.profile, -y);
+    const double w = (second ? ax + h : ax - h) * (i == 0 ? is0 : (i == 1 ? is1 : is2));
+    const double g2 = tail2(G.profile, fabs(w));
+    v = w >= 0.0 ? g2 : 2.0 - g2;
   }
   double F = 0.0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const double X = __shfl_sync(0xffffffffu, v, 4 * i, 16) - __shfl_sync(0xffffffffu, v, 4 * i + 1, 16);
-    const double Z = __shfl_sync(0xffffffffu, v, 4 * i + 2, 16) - __shfl_sync(0xffffffffu, v, 4 * i + 3, 16);
-    F += 0.25 * G.c1d[i] * X * Z;
+    const double x1 = __shfl_sync(0xffffffffu, v, 4 * i, 16), x2 = __shfl_sync(0xffffffffu, v, 4 * i + 1, 16);
+    const double z1 = __shfl_sync(0xffffffffu, v, 4 * i + 2, 16), z2 = __shfl_sync(0xffffffffu, v, 4 * i + 3, 16);
+    if (sub == 0) F += 0.25 * G.c1d[i] * (x1 - x2) * (z1 - z2);
   }
-  if (!(t > 0.0)) return 0.0;
+  if (sub != 0 || !(t > 0.0)) return 0.0;
   // Eq. 2: A = T(d) (SAD / t)^2
   const double q = B.sad / t;
   return T * q * q * F;
