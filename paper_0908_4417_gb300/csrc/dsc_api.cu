@@ -39,8 +39,8 @@ __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
 __global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*);
 __global__ void k_slices(const DInst*, DRow*, int, int*, int*, int, int*);
 __global__ void k_item_rows(const long long*, int, int*);
-__global__ void k_tile_map(const long long*, const long long*, long long, const int*, long long*, long long*,
-                           long long*, int*, int*);
+__global__ void k_tile_map(const long long*, const long long*, const int*, int*, int*);
+__global__ void k_row_bound(const DInst*, const DRow*, int, const float*, int, SliceTab, unsigned*);
 __global__ void k_eval(EvalParams);
 __global__ void k_beam_scale(const DBeam*, int, const unsigned*, const OutSlot*);
 __global__ void k_tile_count(CompactParams, int*);
@@ -52,8 +52,8 @@ __global__ void k_dose_finish(const unsigned long long*, long long, const int*, 
 __global__ void k_beamlet_dot(const long long*, const long long*, const int*, const void*, int, const DRow*, int,
                               const float*, const float*, int, float*);
 __global__ void k_tile_write(CompactParams, const long long*);
-__global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
-                          long long, int, int, long long, int, int, const OutSlot*);
+__global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, long long, int, int,
+                          long long, int, int, const OutSlot*);
 __global__ void k_copy_stats(const unsigned*, const long long*, int, const unsigned long long*, int, const OutSlot*);
 __global__ void k_scan_partial(const int*, const long long*, long long, long long*);
 __global__ void k_scan_blocks(long long*);
@@ -153,6 +153,7 @@ struct dsc_geometry {
   double cutoff_k;
   int profile = 0;                   // DSC_PROFILE_*
   float c3max;
+  float d_peak;                      // depth of the model's largest T (the first such row), mm
   float* d_rho = nullptr;
   float4* d_lut = nullptr;            // evaluation table: (row, difference) pairs, c3 / K
   float4* d_lut_rows = nullptr;       // the model's rows as given (FP64 re-evaluation)
@@ -232,16 +233,14 @@ struct Plan {
   int* d_item_cand = nullptr;
   int* d_item_row = nullptr;
   long long* d_item_off = nullptr;
-  long long* d_item_out = nullptr;
   int* d_tile_cnt = nullptr;
   long long* d_tile_off = nullptr;   // n_tiles + 1
-  long long* d_tile_item0 = nullptr;
-  long long* d_tile_first = nullptr;
   float* d_tile_thr = nullptr;
   float* d_tile_scale = nullptr;
-  long long* d_tile_next = nullptr;
-  int* d_tile_starts = nullptr;
   int* d_tile_row = nullptr;
+  int* d_tile_item = nullptr;
+  unsigned* d_tile_meta = nullptr;   // per tile: the evaluation's count under its item's bound
+  unsigned* d_item_L = nullptr;      // per item: the bound of its row maximum it was counted against
   long long n_tiles = 0;
   float* d_vals = nullptr;
   int* d_cols = nullptr;
@@ -270,14 +269,12 @@ struct Plan {
   int kernels_per_run = 0;           // kernel launches in one computation
   std::mutex mu;                     // one computation at a time per plan
   void free_scratch() {
-    void* ps[] = {d_item_cand, d_item_off, d_tile_cnt, d_tile_off, d_item_out, d_vals, d_cols, d_item_row,
-                  d_tile_item0, d_tile_first, d_tile_thr, d_tile_scale, d_tile_next, d_tile_starts, d_rlist_u,
-                  d_tile_row};
+    void* ps[] = {d_item_cand, d_item_off, d_tile_cnt, d_tile_off, d_vals, d_cols, d_item_row, d_tile_thr,
+                  d_tile_scale, d_rlist_u, d_tile_row, d_tile_item, d_tile_meta, d_item_L};
     release_after(last_done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
-    d_item_cand = nullptr; d_item_off = nullptr; d_tile_cnt = nullptr; d_tile_off = nullptr; d_item_out = nullptr;
-    d_vals = nullptr; d_cols = nullptr; d_item_row = nullptr; d_tile_item0 = nullptr; d_tile_first = nullptr;
-    d_tile_thr = nullptr; d_tile_scale = nullptr; d_tile_next = nullptr; d_tile_starts = nullptr; d_rlist_u = nullptr;
-    d_tile_row = nullptr;
+    d_item_cand = nullptr; d_item_off = nullptr; d_tile_cnt = nullptr; d_tile_off = nullptr;
+    d_vals = nullptr; d_cols = nullptr; d_item_row = nullptr; d_tile_thr = nullptr; d_tile_scale = nullptr;
+    d_rlist_u = nullptr; d_tile_row = nullptr; d_tile_item = nullptr; d_tile_meta = nullptr; d_item_L = nullptr;
     if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
   }
   ~Plan() {
@@ -408,6 +405,7 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
   if (model->cutoff_mode < 0 || model->cutoff_mode > 2) return fail(DSC_E_INVAL, "cutoff_mode");
   if (model->profile < 0 || model->profile > 2) return fail(DSC_E_INVAL, "profile: DSC_PROFILE_ERF, _LAPLACE or _LOGISTIC");
   float c3max = 0.f;
+  int kpeak = 0;
   for (int k = 0; k < model->n; ++k) {
     for (int c = 1; c <= 3; ++c) {
       const float v = model->table4[4 * k + c];
@@ -415,6 +413,7 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
     }
     if (!std::isfinite(model->table4[4 * k])) return fail(DSC_E_INVAL, "T(d) must be finite");
     c3max = std::max(c3max, model->table4[4 * k + 1]);
+    if (model->table4[4 * k] > model->table4[4 * kpeak]) kpeak = k;
   }
   int dev;
   TRY(ensure_device(&dev));
@@ -430,6 +429,7 @@ extern "C" dsc_status dsc_create_geometry(const dsc_grid_desc* grid, const float
   g->cutoff_k = model->cutoff_k;
   g->profile = model->profile;
   g->c3max = c3max;
+  g->d_peak = (float)(kpeak * (model->d_max / (model->n - 1)));
   size_t nvox = (size_t)grid->nx * grid->ny * grid->nz;
   dsc_status st = dalloc(&g->d_rho, nvox, s);
   if (st == DSC_OK) st = dalloc(&g->d_lut, 2 * (size_t)model->n, s);
@@ -549,6 +549,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
     I.idx = 1.0 / I.dx; I.idy = 1.0 / I.dy; I.idz = 1.0 / I.dz;
     I.lut_scale = (float)((g->n_lut - 1) / g->d_max);
     I.c3max = g->c3max;
+    I.d_peak = g->d_peak;
     for (int i = 0; i < 3; ++i) { I.c1q[i] = (float)(g->c1[i] / 4.0); I.c2h[i] = (float)(g->c2[i] / 2.0); }
     I.cutoff_mode = g->cutoff_mode;
     I.cutoff_k = (float)g->cutoff_k;
@@ -628,7 +629,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_item_cand, P->n_items, s));
   TRY(dalloc(&P->d_item_row, P->n_items, s));
   TRY(dalloc(&P->d_item_off, P->n_items + 1, s));
-  TRY(dalloc(&P->d_item_out, P->n_items + 1, s));
+  TRY(dalloc(&P->d_item_L, P->n_items, s));
   int sms = 0, nb = 0;
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval, kEvalThreads, 0));
@@ -647,18 +648,16 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(scan_launch(P->d_item_cand, P->d_row_item_base + P->nrows, 0, P->d_scan, P->d_item_off, s, P->n_items));
   CU(cudaMemcpyAsync(&P->n_cand, P->d_item_off + P->n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
-  P->n_tiles = (P->n_cand + kTile - 1) / kTile;
+  P->n_tiles = P->n_cand / kTile;                     // items are whole tiles
   TRY(dalloc(&P->d_vals, P->n_cand + 4, s));
   TRY(dalloc(&P->d_cols, P->n_cand + 4, s));
   TRY(dalloc(&P->d_tile_cnt, P->n_tiles, s));
   TRY(dalloc(&P->d_tile_off, P->n_tiles + 1, s));
-  TRY(dalloc(&P->d_tile_item0, P->n_tiles, s));
-  TRY(dalloc(&P->d_tile_first, P->n_tiles, s));
   TRY(dalloc(&P->d_tile_thr, P->n_tiles, s));
   TRY(dalloc(&P->d_tile_scale, P->n_tiles, s));
-  TRY(dalloc(&P->d_tile_next, P->n_tiles, s));
-  TRY(dalloc(&P->d_tile_starts, P->n_tiles, s));
   TRY(dalloc(&P->d_tile_row, P->n_tiles, s));
+  TRY(dalloc(&P->d_tile_item, P->n_tiles, s));
+  TRY(dalloc(&P->d_tile_meta, P->n_tiles, s));
   // about 1e-5 of the candidates fall within kRefineDelta of their threshold
   P->cap_u = (int)std::min<long long>(std::max<long long>(1 << 16, P->n_cand >> 10), 1 << 28);
   TRY(dalloc(&P->d_rlist_u, P->cap_u, s));
@@ -766,6 +765,11 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   else
     k_siddon<<<P->nrows, kSiddonThreads, 0, ts>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride);
   CHECK_LAUNCH();
+  // a lower bound of each row maximum, from the voxels by the axis (the
+  // evaluation counts the tiles against it)
+  k_row_bound<<<(P->nrows + 3) / 4, 128, 0, ts>>>(P->d_inst, P->d_rows, P->nrows, P->d_tables, P->stride, slice_tab(P),
+                                                  P->d_row_max);
+  CHECK_LAUNCH();
   if (fork) CU(cudaEventRecord(P->ev_join, ts));
   TRY(record(ev, 2, s));
   // a3: candidate pairs per work item
@@ -775,8 +779,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
                                                  n_items, P->d_item_cand, P->d_item_row);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_item_cand, n_items, 0, P->d_scan, P->d_item_off, s, P->n_items));
-  k_tile_map<<<1024, 256, 0, s>>>(P->d_item_off, n_items, P->n_cand, P->d_item_row, P->d_tile_item0, P->d_tile_first,
-                                 P->d_tile_next, P->d_tile_starts, P->d_tile_row);
+  k_tile_map<<<1024, 256, 0, s>>>(P->d_item_off, n_items, P->d_item_row, P->d_tile_item, P->d_tile_row);
   CHECK_LAUNCH();
   if (fork) CU(cudaStreamWaitEvent(s, P->ev_join, 0));
   TRY(record(ev, 3, s));
@@ -797,6 +800,10 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   ep.row_max = P->d_row_max;
   ep.row_cand = P->d_row_cand;
   ep.item_counter = P->d_counter;
+  ep.tau = (float)P->opts.rel_threshold;
+  ep.inv_tau_m = ep.tau > 0.0f ? (1.0f - kRefineDelta) / ep.tau : std::numeric_limits<float>::infinity();
+  ep.tile_meta = P->d_tile_meta;
+  ep.item_L = P->d_item_L;
   k_eval<<<P->grid_eval, kEvalThreads, 0, s>>>(ep);
   CHECK_LAUNCH();
   TRY(record(ev, 4, s));
@@ -817,14 +824,12 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   cp.cols = P->d_cols;
   cp.row_max = P->d_row_max;
   cp.tau = (float)P->opts.rel_threshold;
-  cp.item_out = P->d_item_out;
-  cp.tile_item0 = P->d_tile_item0;
-  cp.tile_first = P->d_tile_first;
   cp.tile_thr = P->d_tile_thr;
   cp.tile_scale = P->d_tile_scale;
-  cp.tile_next = P->d_tile_next;
-  cp.tile_starts = P->d_tile_starts;
   cp.tile_row = P->d_tile_row;
+  cp.tile_item = P->d_tile_item;
+  cp.tile_meta = P->d_tile_meta;
+  cp.item_L = P->d_item_L;
   cp.value_dtype = P->opts.value_dtype;
   cp.slot = P->d_slot;
   cp.rlist_u = P->d_rlist_u;
@@ -845,9 +850,9 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   TRY(record(ev, 6, s));
   for (int k = 0; k < P->ninst; ++k) {
     const DInst& I = P->h_inst[k];
-    k_row_ptr<<<(I.nrows + 1 + 255) / 256, 256, 0, s>>>(P->d_row_item_base, P->d_item_off, P->d_item_out, n_items,
-                                                        P->d_tile_off + P->n_tiles, P->n_cand, I.row_base, I.nrows,
-                                                        P->rp_off[k], k, k == P->ninst - 1, P->d_slot);
+    k_row_ptr<<<(I.nrows + 1 + 255) / 256, 256, 0, s>>>(P->d_row_item_base, P->d_item_off, P->d_tile_off, n_items,
+                                                        P->n_cand, I.row_base, I.nrows, P->rp_off[k], k,
+                                                        k == P->ninst - 1, P->d_slot);
     CHECK_LAUNCH();
   }
   k_copy_stats<<<(P->nrows + 255) / 256, 256, 0, s>>>(P->d_row_max, P->d_row_cand, P->nrows, P->d_rcount, P->cap_u,
@@ -1522,6 +1527,7 @@ extern "C" dsc_status dsc_server_submit(dsc_server* S, dsc_geometry* geom, const
   q->view.cutoff_k = geom->cutoff_k;
   q->view.profile = geom->profile;
   q->view.c3max = geom->c3max;
+  q->view.d_peak = geom->d_peak;
   q->view.d_rho = geom->d_rho;
   q->view.d_lut = geom->d_lut;
   q->view.d_lut_rows = geom->d_lut_rows;

@@ -35,6 +35,7 @@ struct DInst {
   double idx, idy, idz;    // 1 / voxel sides
   float lut_scale;         // (n_lut - 1) / d_max
   float c3max;             // max of c3_1 over the table (SIGMA superset)
+  float d_peak;            // depth of the table's largest T (the first such row), mm
   float c1q[3];            // c1 / 4
   float c2h[3];            // c2 / 2
   int cutoff_mode;
@@ -116,6 +117,14 @@ struct EvalParams {
   unsigned* row_max;               // float bits, atomicMax
   long long* row_cand;             // candidates inside the cutoff per row (atomic add)
   int* item_counter;               // persistent-kernel work queue head
+  // the count of each tile taken during the evaluation: an item takes the
+  // running row maximum at its start as a lower bound L of the final one;
+  // per tile, the values at or above the kept bound L gives, and the lanes
+  // with a value in L's refinement band or near L (tile_meta: count in the
+  // low 8 bits, those lanes above)
+  float tau, inv_tau_m;
+  unsigned* tile_meta;             // n_tiles
+  unsigned* item_L;                // n_items: float bits of L
 };
 
 // Output pointers of the computation in flight.  Kernels read them from this
@@ -134,19 +143,19 @@ struct OutSlot {
                                // maximum; near-threshold pairs past the list's capacity (decided in FP32)
 };
 
-constexpr int kTilePer = 8;                       // candidates per thread of the compaction
-constexpr int kTile = 32 * kTilePer;              // candidates per compaction tile
+constexpr int kTilePer = 4;                       // candidates per thread of the compaction
+// candidates per compaction tile; every work item is padded to a whole
+// number of tiles, so a tile lies in one item, and one warp-iteration of the
+// evaluation (32 lanes x 4 candidates) writes one tile
+constexpr int kTile = 32 * kTilePer;
 #ifndef DSC_TPW
-#define DSC_TPW 1
+#define DSC_TPW 2
 #endif
 // tiles per warp in the count and write passes: a warp loads all its tiles'
 // candidates before deciding any, so more loads are in flight
 constexpr int kTilesPerWarp = DSC_TPW;
-#ifndef DSC_CTPW
-#define DSC_CTPW DSC_TPW
-#endif
-// tiles per warp in the count pass alone
-constexpr int kCountTilesPerWarp = DSC_CTPW;
+// tiles per warp in the count pass: a tile per lane
+constexpr int kCountTilesPerWarp = 32;
 // CTAs (of kEvalThreads) over n_tiles tiles, tpw tiles per warp
 inline unsigned tile_blocks(long long n_tiles, int tpw) {
   const long long warps = (n_tiles + tpw - 1) / tpw;
@@ -166,14 +175,12 @@ struct CompactParams {
   const int* cols;
   const unsigned* row_max;
   float tau;
-  long long* item_out;            // n_items: kept entries before each item's first candidate
-  const long long* tile_item0;    // per tile: item holding its first candidate
-  const long long* tile_first;    // per tile: first item starting at or after its first candidate
-  const int* tile_row;            // per tile: row of tile_item0
+  const int* tile_row;            // per tile: the row of the item holding the tile
+  const int* tile_item;           // per tile: the item holding the tile
+  const unsigned* tile_meta;      // per tile: the evaluation's count and flags (EvalParams)
+  const unsigned* item_L;         // per item: the lower bound of the row maximum it was counted against
   float* tile_thr;                // per tile: threshold of that row (written by the count pass)
   float* tile_scale;              // per tile: BF16 scale of that row's beam (written by the count pass)
-  const long long* tile_next;     // per tile: start of the item after tile_item0
-  const int* tile_starts;         // per tile: an item starts inside the tile
   int value_dtype;
   const OutSlot* slot;
   // decisions FP32 cannot settle: candidates within kRefineDelta (relative)

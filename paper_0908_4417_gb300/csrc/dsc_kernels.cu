@@ -654,6 +654,8 @@ struct LineSm {
   int row;
   int nl;
   int total;
+  float dl_ukeep, dl_bc, dl_bh, dl_mlo;   // L's kept bound, band centre and half-width, near-L bound
+  unsigned* tmeta;                    // the item's first tile's entry of tile_meta
 };
 
 // float-float s, x', z' of x-line (iy, iz) of row R at ix = 0 (the
@@ -975,9 +977,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);   // within the half
-    // items are padded to a multiple of 4 candidates (the evaluation writes
-    // aligned groups of 4; padding slots hold -1, never kept)
-    if (sub == 0 && item < ni) item_cand[item] = (cnt + 3) & ~3;
+    // items are padded to whole compaction tiles (the evaluation writes
+    // whole tiles; padding slots hold -1, never kept)
+    if (sub == 0 && item < ni) item_cand[item] = (cnt + kTile - 1) & ~(kTile - 1);
   }
 }
 
@@ -1194,13 +1196,35 @@ __device__ __forceinline__ void load_row_const(RowConst& C, const DRow& R, const
   C.cutoff_k = G.cutoff_k;
 }
 
+// The decisions a row maximum M gives, in FP32 (the evaluation's tile
+// counts and the count pass form them with this one function, so that both
+// compare the same numbers): kept is D >= thr1 = max(tau M, smallest
+// denormal); a value in the refinement window (ulo, uhi) is decided in FP64;
+// one at or above mlo is near the maximum; ukeep = uhi (1 + 2^-16) bounds the
+// window of any final maximum a little above M.  All are non-decreasing in M.
+struct Decide {
+  float thr1, ulo, uhi, mlo, ukeep;
+};
+__device__ __forceinline__ Decide decide_at(float tau, float inv_tau_m, float M) {
+  constexpr float kTiny = 1.40129846e-45f;
+  constexpr float kLo = 1.0f - kRefineDelta, kHi = 1.0f + kRefineDelta;
+  Decide d;
+  d.thr1 = fmaxf(tau * M, kTiny);
+  d.ulo = d.thr1 * kLo;
+  d.uhi = d.thr1 * kHi;
+  d.mlo = d.thr1 * inv_tau_m;
+  d.ukeep = d.uhi * 1.0000152587890625f;        // 1 + 2^-16
+  return d;
+}
+
 // the candidates [w0, w0 + wl) of an item's window (the item's first wl
 // candidates past w0 are real; the rest of the last group of 4 is padding),
 // profile PROF (block-uniform); TS: the depth table is in sm.tab; SIG: the
-// sigma cutoff.  Each thread takes groups of 4 consecutive candidates (four
-// independent chains), writes their values and columns with aligned 16-byte
-// stores (the item starts on a multiple of 4), and keeps the maximum and,
-// with SIG, the count inside the cutoff.
+// sigma cutoff.
+// Each thread takes groups of 4 consecutive candidates (four independent
+// chains; a warp's 32 groups are one tile of 128), writes their values and
+// columns with aligned 16-byte stores (the item starts on a tile), and keeps
+// the maximum and, with SIG, the count inside the cutoff.
 template <int PROF, bool TS, bool SIG>
 __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm, int w0, int wl, float* out,
                                             int* outc, float& vmax, int& valid) {
@@ -1223,15 +1247,34 @@ __device__ __forceinline__ void eval_window(const RowConst& C, const LineSm& sm,
       D[k] = eval_pair<PROF, TS, SIG>(C, small_int_to_float(ix), A, B, sm.sf[li] + (long long)j * C.dsf, sm.tab,
                                       SMLUT);
     }
-    if (g + 4 > wl) {                                   // only a window's last group holds padding
+    if (g + 4 > wl) {                                   // the last real group's padding
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         if (g + k >= wl) { D[k] = -1.0f; col[k] = 0; }
     }
     *reinterpret_cast<float4*>(out + jj) = make_float4(D[0], D[1], D[2], D[3]);
     *reinterpret_cast<int4*>(outc + jj) = make_int4(col[0], col[1], col[2], col[3]);
-    vmax = fmaxf(vmax, fmaxf(fmaxf(D[0], D[1]), fmaxf(D[2], D[3])));
+    const float lmax = fmaxf(fmaxf(D[0], D[1]), fmaxf(D[2], D[3]));
+    vmax = fmaxf(vmax, lmax);
     if (SIG) valid += (D[0] >= 0.0f) + (D[1] >= 0.0f) + (D[2] >= 0.0f) + (D[3] >= 0.0f);
+    // the tile's count under the item's bound L (thresholds in shared
+    // memory, read each time so that they hold no registers): the values at
+    // or above L's kept bound ukeep, and the lanes with a value within bh of
+    // bc (a superset of L's band (ulo, ukeep)) or at or above mlo (near L),
+    // summed over the warp in one reduction (count in the low 8 bits).  The
+    // warp's lanes in this iteration are a prefix of it (those whose group
+    // starts before wl), all in one tile.
+    const float ukeep = *(volatile const float*)&sm.dl_ukeep, bc = *(volatile const float*)&sm.dl_bc,
+                bh = *(volatile const float*)&sm.dl_bh, mlo = *(volatile const float*)&sm.dl_mlo;
+    const unsigned a = (D[0] >= ukeep) + (D[1] >= ukeep) + (D[2] >= ukeep) + (D[3] >= ukeep);
+    const float md = fminf(fminf(fabsf(D[0] - bc), fabsf(D[1] - bc)), fminf(fabsf(D[2] - bc), fabsf(D[3] - bc)));
+    unsigned v = a | (md < bh || lmax >= mlo ? 0x100u : 0u);
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned g0 = (unsigned)g - 4u * lane;        // the tile's first candidate in the window
+    const unsigned nl = ((unsigned)wl - g0 + 3u) >> 2;  // lanes of this warp in the iteration
+    v = __reduce_add_sync(nl >= 32u ? 0xffffffffu : (1u << nl) - 1u, v);
+    static_assert(kTile == 128, "tile index by shift");
+    if (lane == 0u) (*(unsigned* volatile const*)&sm.tmeta)[((unsigned)w0 + g0) >> 7] = v;
   }
 }
 
@@ -1264,17 +1307,41 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_EVAL_MINBLOCKS) k_eval(EvalP
     const long long item = sm.item;
     if (item >= ni) break;
     const int row = sm.row;
+    // the running row maximum (every value of it is a lower bound of the
+    // final one), read once for the whole item; the others read it after
+    // item_lines' barriers
+    const long long a_off = p.item_off[item];
+    if (threadIdx.x == 0) {
+      const unsigned lb = __ldcg(p.row_max + row);
+      p.item_L[item] = lb;
+      const Decide DL = decide_at(p.tau, p.inv_tau_m, __uint_as_float(lb));
+      sm.dl_ukeep = DL.ukeep;
+      // |D - bc| < bh holds for every D in (ulo, ukeep): ukeep - ulo is exact
+      // (the two are within a factor 2), and the widening covers the rounding
+      // of bc and of D - bc; an empty band (ulo = ukeep) gives bh = 0
+      sm.dl_bc = 0.5f * (DL.ulo + DL.ukeep);
+      sm.dl_bh = 0.5f * (DL.ukeep - DL.ulo) * 1.0625f;
+      sm.dl_mlo = DL.mlo;
+      sm.tmeta = p.tile_meta + a_off / kTile;
+    }
     const DRow& R = p.rows[row];
     const DInst& G = p.inst[R.inst];
     const int mode = G.cutoff_mode;
     const bool sig = mode == 1;
-    const long long a_off = p.item_off[item];
 #if DSC_LUT_SMEM
     // read before item_lines' barriers; thread 0 updates it after them
     const bool lut_stale = sm.lut_inst != R.inst;
 #endif
+    const int padded = (int)(p.item_off[item + 1] - a_off);   // the counted range, whole tiles
     const int total = min(item_lines(sm, R, p.slices, row, mode, G.nx, G.ny, item - p.row_item_base[row]),
-                          (int)(p.item_off[item + 1] - a_off));   // never past the counted range
+                          padded);                             // never past the counted range
+    // the padding past the last real group, to the end of its tile (fewer
+    // than 32 groups): -1, never kept; written first, so that padded is not
+    // held through the evaluation
+    for (int g = ((total + 3) & ~3) + 4 * (int)threadIdx.x; g < padded; g += 4 * kEvalThreads) {
+      *reinterpret_cast<float4*>(p.vals + a_off + g) = make_float4(-1.0f, -1.0f, -1.0f, -1.0f);
+      *reinterpret_cast<int4*>(p.cols + a_off + g) = make_int4(0, 0, 0, 0);
+    }
     RowConst C;
     load_row_const(C, R, G, p.tables + (size_t)row * p.table_stride);
     // the row's depth table into shared memory when it fits (block-uniform);
@@ -1297,7 +1364,7 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_EVAL_MINBLOCKS) k_eval(EvalP
     float vmax = 0.0f;
     int valid = (!sig && threadIdx.x == 0) ? total : 0;   // outside the sigma cutoff every candidate counts
     for (int w0 = 0; w0 < total; w0 += kWindow) {
-      int wl = min(kWindow, total - w0);
+      const int wl = min(kWindow, total - w0);
       item_map(sm, w0, wl);
       if (ts) {
         switch (G.profile) {
@@ -1326,6 +1393,107 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_EVAL_MINBLOCKS) k_eval(EvalP
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// k_row_bound: a lower bound of every row's maximum before the evaluation,
+// one warp per row.  Past the depth dT where the depth-dose factor T(d) of
+// the beam model peaks, every factor of Eq. 2 falls along the beamlet axis,
+// and laterally the dose is largest on the axis, so a row's maximum lies by
+// the axis at a depth below dT.  Up to 32 points of the axis, half a voxel
+// apart where they fit, span the stretch where the radiological depth (the
+// row's table) lies in [dT - 10 mm, dT + 2 mm]; the 8 voxels whose centres
+// surround each point, those that are candidates of the row, are evaluated
+// with the evaluation's own functions, (point, voxel) pairs spread over the
+// lanes.  The largest value, times
+// (1 - 2^-18) so that it stays below the evaluation's value of the same
+// voxel under any contraction of the same formulas, seeds row_max.  The
+// bound only decides which tiles the count pass takes from the evaluation's
+// counts; a bound that is too low costs their values' reads.
+// ---------------------------------------------------------------------------
+// the first k in [0, n) with a[k] >= x (n if none); a non-decreasing, the
+// warp probes 32 entries at a time
+__device__ __forceinline__ int warp_lower_bound(const float* __restrict__ a, int n, float x, int lane) {
+  int lo = 0, hi = n;                                  // a[lo - 1] < x, a[hi] >= x (or hi = n)
+#pragma unroll 1
+  while (lo < hi) {                                    // warp-uniform
+    const int step = (hi - lo + 31) / 32;
+    const int k = lo + lane * step;
+    const unsigned b = __ballot_sync(0xffffffffu, k < hi && a[k] >= x);
+    if (b == 0u) {
+      lo = min(lo + 31 * step, hi - 1) + 1;            // past the last probe below hi
+    } else {
+      const int f = __ffs(b) - 1;
+      hi = lo + f * step;
+      if (f > 0) lo = lo + (f - 1) * step + 1;
+    }
+  }
+  return lo;
+}
+
+template <int PROF, bool SIG>
+__device__ float bound_voxel(const RowConst& C, const DRow& R, int ix, int iy, int iz) {
+  ff s0, x0, z0;
+  line_base(R, iy, iz, s0, x0, z0);
+  const float4 A = make_float4(R.tA_f + s0.hi, 0.0f, x0.hi, z0.hi);
+  const float4 B = make_float4(x0.lo, z0.lo, 0.0f, 0.0f);
+  const long long sf = R.sfx0 + (long long)iy * R.sfx_s[1] + (long long)iz * R.sfx_s[2] + (long long)ix * C.dsf;
+  return eval_pair<PROF, false, SIG>(C, small_int_to_float(ix), A, B, sf, nullptr, nullptr);
+}
+
+__global__ void __launch_bounds__(128) k_row_bound(const DInst* __restrict__ inst, const DRow* __restrict__ rows,
+                                                   int nrows, const float* __restrict__ tables, int stride, SliceTab T,
+                                                   unsigned* row_max) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (row >= nrows) return;                            // warp-uniform
+  const DRow& R = rows[row];
+  const int nzr = row_slices(R, T.stride);
+  if (nzr <= 0 || R.n_table < 2) return;
+  const DInst& G = inst[R.inst];
+  const float* tab = tables + (size_t)row * stride;
+  const int k0 = warp_lower_bound(tab, R.n_table, G.d_peak - 10.0f, lane);
+  const int k1 = warp_lower_bound(tab, R.n_table, nextafterf(G.d_peak + 2.0f, CUDART_INF_F), lane) - 1;
+  if (k0 > k1) return;
+  const float hd = (float)G.hd;
+  const float ta = R.tA_f + (float)k0 * hd, span = (float)(k1 - k0) * hd;
+  const float vmin = (float)fmin(G.dx, fmin(G.dy, G.dz));
+  const int np = min(32, (int)(span / (0.5f * vmin)) + 1);
+  const float dt = np > 1 ? span / (float)(np - 1) : 0.0f;
+  const int* pre = T.pre + (size_t)row * T.stride;
+  const int* ylo = T.lo + (size_t)row * T.stride;
+  const LineCut L(R, G.cutoff_mode, G.nx);
+  RowConst C;
+  load_row_const(C, R, G, tab);
+  const bool sig = G.cutoff_mode == 1;
+  float best = 0.0f;
+  // (point, voxel) pairs over the lanes
+#pragma unroll 1
+  for (int e = lane; e < 8 * np; e += 32) {
+    const float t = ta + (float)(e >> 3) * dt;
+    const int c = e & 7;
+    const int ix = (int)floorf(((float)R.S[0] + t * (float)R.e[0] - (float)G.ox) / (float)G.dx - 0.5f) + (c & 1);
+    const int iy = (int)floorf(((float)R.S[1] + t * (float)R.e[1] - (float)G.oy) / (float)G.dy - 0.5f) + ((c >> 1) & 1);
+    const int iz = (int)floorf(((float)R.S[2] + t * (float)R.e[2] - (float)G.oz) / (float)G.dz - 0.5f) + ((c >> 2) & 1);
+    const int sl = iz - R.iz0;
+    if (ix < 0 || ix >= G.nx || iy < 0 || iy >= G.ny || sl < 0 || sl >= nzr) continue;
+    const int y0 = ylo[sl];
+    if (iy < y0 || iy >= y0 + (pre[sl + 1] - pre[sl])) continue;   // a line the row enumerates
+    int lo;
+    const int len = line_interval(L, iy, iz, lo);
+    if (ix < lo || ix >= lo + len) continue;           // a candidate of the line
+    float D;
+    switch (G.profile) {
+      case 1: D = sig ? bound_voxel<1, true>(C, R, ix, iy, iz) : bound_voxel<1, false>(C, R, ix, iy, iz); break;
+      case 2: D = sig ? bound_voxel<2, true>(C, R, ix, iy, iz) : bound_voxel<2, false>(C, R, ix, iy, iz); break;
+      default: D = sig ? bound_voxel<0, true>(C, R, ix, iy, iz) : bound_voxel<0, false>(C, R, ix, iy, iz); break;
+    }
+    best = fmaxf(best, D);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  best *= 0.99999618530273437500f;                     // 1 - 2^-18
+  if (lane == 0 && best > 0.0f) atomicMax(row_max + row, __float_as_uint(best));
 }
 
 // ---------------------------------------------------------------------------
@@ -1417,14 +1585,17 @@ __global__ void k_beam_scale(const DBeam* __restrict__ beams, int nbeams, const 
 // ---------------------------------------------------------------------------
 // compaction: kept = D > 0 and D >= tau * row max, over tiles of kTile
 // candidates, one warp per tile (kTilePer consecutive candidates per lane,
-// vector loads, no block barriers):
+// vector loads, no block barriers).  Work items are padded to whole tiles,
+// so every tile lies in one item and one row:
+//   k_tile_map    the row of every tile
 //   k_tile_count  kept entries per tile
-//   (scan)        tile output offsets
+//   (scan)        tile output offsets; an item's output starts at its first
+//                 tile's offset
 //   k_tile_write  warp scan within the tile, kept entries staged in shared
-//                 memory and written coalesced; item_out receives the kept
-//                 count before each item's start
+//                 memory and written coalesced
 // ---------------------------------------------------------------------------
 constexpr int kTileWarps = kEvalThreads / 32;
+static_assert(kTilePer == 4, "one 16-byte vector per lane and array");
 
 struct TileKeep {
   float D[kTilePer];
@@ -1433,81 +1604,41 @@ struct TileKeep {
   int cnt;            // count pass: kept entries of the lane
 };
 
-// candidates [p0, p0 + kTilePer) and their keep flags; item0 holds the
-// tile's first candidate, and each lane walks the (rare) item boundaries
-// the lane's kTilePer candidate values (and columns) from [p0, p0 + kTilePer); past the end -1
+// the lane's kTilePer candidate values (and columns) from [p0, p0 + kTilePer);
+// the candidate count is a whole number of tiles
 template <bool kCols>
 __device__ __forceinline__ void tile_load(const CompactParams& p, long long p0, TileKeep& K) {
-  const long long n = p.n_cand;
-  if (p0 + kTilePer <= n) {
-    const float4* v4 = reinterpret_cast<const float4*>(p.vals + p0);
-    const int4* c4 = reinterpret_cast<const int4*>(p.cols + p0);
-#pragma unroll
-    for (int q = 0; q < kTilePer / 4; ++q) {
-      float4 v = __ldcs(v4 + q);
-      K.D[4 * q] = v.x; K.D[4 * q + 1] = v.y; K.D[4 * q + 2] = v.z; K.D[4 * q + 3] = v.w;
-      if (kCols) {
-        int4 c = __ldcs(c4 + q);
-        K.C[4 * q] = c.x; K.C[4 * q + 1] = c.y; K.C[4 * q + 2] = c.z; K.C[4 * q + 3] = c.w;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < kTilePer; ++i) {
-      bool in = p0 + i < n;
-      K.D[i] = in ? __ldcs(p.vals + p0 + i) : -1.0f;
-      if (kCols) K.C[i] = in ? __ldcs(p.cols + p0 + i) : 0;
-    }
+  const float4 v = __ldcs(reinterpret_cast<const float4*>(p.vals + p0));
+  K.D[0] = v.x; K.D[1] = v.y; K.D[2] = v.z; K.D[3] = v.w;
+  if (kCols) {
+    const int4 c = __ldcs(reinterpret_cast<const int4*>(p.cols + p0));
+    K.C[0] = c.x; K.C[1] = c.y; K.C[2] = c.z; K.C[3] = c.w;
   }
 }
 
-// keep flags of the loaded candidates; item0 holds the tile's first
-// candidate, and each lane walks the (rare) item boundaries
+// keep flags of the lane's loaded candidates, all of the tile's row
 template <bool kCols>
 __device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0, long long tile, TileKeep& K) {
-  const long long item0 = p.tile_item0[tile];
-  const long long n = p.n_cand;
-  const long long ni = *p.n_items;
-  const long long* __restrict__ off = p.item_off;
   const bool bf16 = kCols && p.value_dtype == 1;
-  long long it = item0;
-  long long next = p.tile_next[tile];
-  float thr;
+  const int r = p.tile_row[tile];
+  float thr, scale = 1.0f;
   if (kCols) {
     thr = p.tile_thr[tile];
+    if (bf16) scale = p.tile_scale[tile];
   } else {
-    // the count pass forms the threshold of the tile's first row (the row
-    // maxima are final) and leaves it, and the BF16 scale, for the write pass
-    const int r0 = p.tile_row[tile];
-    thr = p.tau * __uint_as_float(p.row_max[r0]);
+    // the count pass forms the tile's threshold (the row maxima are final)
+    // and leaves it, and the BF16 scale, for the write pass
+    thr = p.tau * __uint_as_float(p.row_max[r]);
     if ((threadIdx.x & 31) == 0) {
       p.tile_thr[tile] = thr;
-      if (p.value_dtype == 1) p.tile_scale[tile] = p.slot->beam_scale[p.rows[r0].beam];
+      if (p.value_dtype == 1) p.tile_scale[tile] = p.slot->beam_scale[p.rows[r].beam];
     }
   }
-  float scale = bf16 ? p.tile_scale[tile] : 1.0f;
-  if (next <= p0) {                                    // this lane starts past the first boundary
-    while (next <= p0 && it + 1 < ni) {
-      ++it;
-      next = it + 1 < ni ? off[it + 1] : n;
-    }
-    const int r = p.item_row[it];
-    thr = p.tau * __uint_as_float(p.row_max[r]);
-    if (bf16) scale = p.slot->beam_scale[p.rows[r].beam];
-  }
-  // kept = D > 0 and D >= thr, i.e. D >= max(thr, smallest denormal); slots
-  // past the end hold -1.  Positions relative to p0; nx = the next item
-  // boundary inside this lane's range (kTilePer: none)
+  // kept = D > 0 and D >= thr, i.e. D >= max(thr, smallest denormal); the
+  // padding holds -1
   constexpr float kTiny = 1.40129846e-45f;
-  float thr1 = fmaxf(thr, kTiny);
-  // count pass: the refinement windows of the current row (empty when thr1 is
-  // the smallest denormal: no value lies strictly between ulo and uhi)
-  constexpr float kLo = 1.0f - kRefineDelta, kHi = 1.0f + kRefineDelta;
-  float ulo = 0.0f, uhi = 0.0f, mlo = 0.0f;
-  if (!kCols) { ulo = thr1 * kLo; uhi = thr1 * kHi; mlo = thr1 * p.inv_tau_m; }
-  int nx = next >= n ? kTilePer : (int)min(next - p0, (long long)kTilePer);
-  if (kCols && nx >= kTilePer) {
-    // write pass, the common case: one row for the lane's candidates
+  const float thr1 = fmaxf(thr, kTiny);
+  if (kCols) {
     unsigned kp = 0;
 #pragma unroll
     for (int i = 0; i < kTilePer; ++i)
@@ -1518,95 +1649,52 @@ __device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0
     K.keep = kp;
     return;
   }
-  if (!kCols && nx >= kTilePer) {
-    // count pass, the common case: one row for the lane's candidates; count
-    // them, and fall through to the per-candidate flags only when one lies
-    // in a refinement window
-    int cnt = 0;
-    bool sp = false;
-    float m = K.D[0];
-#pragma unroll
-    for (int i = 0; i < kTilePer; ++i) {
-      const float D = K.D[i];
-      const bool above = D >= uhi;
-      cnt += above;
-      sp |= D > ulo && !above;
-      m = fmaxf(m, D);
-    }
-    if (!sp && !(m >= mlo)) {
-      K.cnt = cnt;
-      return;
-    }
-  }
+  // count pass: outside the refinement window (ulo, uhi) the decision
+  // D >= thr1 is D >= uhi (the window is empty when thr1 is the smallest
+  // denormal: no value lies strictly between ulo and uhi); a value inside it,
+  // or near the row maximum, is handled after the loop
+  const Decide DM = decide_at(p.tau, p.inv_tau_m, __uint_as_float(p.row_max[r]));
+  const float ulo = DM.ulo, uhi = DM.uhi, mlo = DM.mlo;
   unsigned keep = 0, special = 0;
 #pragma unroll
   for (int i = 0; i < kTilePer; ++i) {
-    if (i >= nx) {                                     // crossing into the next item(s)
-      const long long pos = p0 + i;
-      while (next <= pos && it + 1 < ni) {
-        ++it;
-        next = it + 1 < ni ? off[it + 1] : n;
-      }
-      const int r = p.item_row[it];
-      thr1 = fmaxf(p.tau * __uint_as_float(p.row_max[r]), kTiny);
-      if (bf16) scale = p.slot->beam_scale[p.rows[r].beam];
-      if (!kCols) { ulo = thr1 * kLo; uhi = thr1 * kHi; mlo = thr1 * p.inv_tau_m; }
-      nx = next >= n ? kTilePer : (int)min(next - p0, (long long)kTilePer);
-    }
     const float D = K.D[i];
-    if (kCols) {
-      if (D >= thr1) {
-        keep |= 1u << i;
-        if (bf16) K.D[i] = __fdiv_rn(K.D[i], scale);
-      }
-    } else {
-      // count pass: outside the window (ulo, uhi) the decision D >= thr1 is
-      // D >= uhi; a value inside it is decided after the loop
-      const bool above = D >= uhi;
-      if (above) keep |= 1u << i;
-      if ((D > ulo && !above) || D >= mlo) special |= 1u << i;
-    }
+    const bool above = D >= uhi;
+    if (above) keep |= 1u << i;
+    if ((D > ulo && !above) || D >= mlo) special |= 1u << i;
   }
-  if (!kCols && special) {
-    // count pass, candidates near their threshold or their row maximum (rare).
-    // A value within kRefineDelta of its threshold does not settle the
-    // decision in FP32: it is listed for the FP64 re-evaluation, which adds
-    // it to the count if kept, and it leaves this count.  A value within
-    // kRefineDelta of the row maximum goes to the row's slots, from which the
+  if (special) {
+    // candidates near their threshold or their row maximum (rare).  A value
+    // within kRefineDelta of its threshold does not settle the decision in
+    // FP32: it is listed for the FP64 re-evaluation, which adds it to the
+    // count if kept, and it leaves this count.  A value within kRefineDelta
+    // of the row maximum goes to the row's slots, from which the
     // re-evaluation takes the FP64 maximum; a row with more such values than
     // slots is listed once, and its FP64 maximum comes from a scan of the row
     // (k_refine_rowmax).  A full list leaves the FP32 decision in place (and
-    // is counted).  The item of each position is found again from the tile's
-    // first item.
-    long long it2 = item0, next2 = p.tile_next[tile];
+    // is counted).
+    if ((unsigned)r >= (unsigned)p.nrows) {           // checked: skip and flag
+      atomicOr(p.slot->status, kStatusIndex);
+    } else {
 #pragma unroll
-    for (int i = 0; i < kTilePer; ++i) {              // static positions: K stays in registers
-      if (!(special & (1u << i))) continue;
-      const long long pos = p0 + i;
-      while (next2 <= pos && it2 + 1 < ni) {
-        ++it2;
-        next2 = it2 + 1 < ni ? off[it2 + 1] : n;
-      }
-      const int r = p.item_row[it2];
-      if ((unsigned)r >= (unsigned)p.nrows) {         // checked: skip and flag
-        atomicOr(p.slot->status, kStatusIndex);
-        continue;
-      }
-      const float t1 = fmaxf(p.tau * __uint_as_float(p.row_max[r]), kTiny);
-      const float D = K.D[i];
-      if (D > t1 * kLo && D < t1 * kHi) {
-        const unsigned long long e = atomicAdd(p.rcount, 1ull);
-        if (e < (unsigned long long)p.cap_u) p.rlist_u[e] = refine_entry(pos, r);
-        else if (D >= t1) keep |= 1u << i;            // list full: the FP32 decision
-      }
-      if (D >= t1 * p.inv_tau_m) {
-        atomicAdd(p.rcount + 1, 1ull);
-        const int k = atomicAdd(p.mcount + r, 1);
-        if (k < kMaxSlots) {
-          p.mslot[(size_t)r * kMaxSlots + k] = pos;
-        } else if (k == kMaxSlots) {                   // the row overflows its slots: list it once
-          const unsigned long long e = atomicAdd(p.rcount + 2, 1ull);
-          if (e < (unsigned long long)p.nrows) p.ovf_rows[e] = r;
+      for (int i = 0; i < kTilePer; ++i) {            // static positions: K stays in registers
+        if (!(special & (1u << i))) continue;
+        const long long pos = p0 + i;
+        const float D = K.D[i];
+        if (D > ulo && D < uhi) {
+          const unsigned long long e = atomicAdd(p.rcount, 1ull);
+          if (e < (unsigned long long)p.cap_u) p.rlist_u[e] = refine_entry(pos, r);
+          else if (D >= thr1) keep |= 1u << i;        // list full: the FP32 decision
+        }
+        if (D >= mlo) {
+          atomicAdd(p.rcount + 1, 1ull);
+          const int k = atomicAdd(p.mcount + r, 1);
+          if (k < kMaxSlots) {
+            p.mslot[(size_t)r * kMaxSlots + k] = pos;
+          } else if (k == kMaxSlots) {                 // the row overflows its slots: list it once
+            const unsigned long long e = atomicAdd(p.rcount + 2, 1ull);
+            if (e < (unsigned long long)p.nrows) p.ovf_rows[e] = r;
+          }
         }
       }
     }
@@ -1615,42 +1703,20 @@ __device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0
   K.cnt = __popc(keep);
 }
 
-// per tile, from the work decomposition alone (it runs before the
-// evaluation): the item holding the tile's first candidate (tile_item0), that
-// item's row (tile_row) and the start of the item after it (tile_next), the
-// first item starting at or after the tile's first candidate (tile_first),
-// and whether an item starts inside the tile (tile_starts), so that the
-// compaction starts from independent loads instead of a chain of dependent
-// ones; one warp per item, a tile per lane
+// the item and row of every tile, from the work decomposition alone (it
+// runs before the evaluation); one warp per item, a tile per lane
 __global__ void k_tile_map(const long long* __restrict__ item_off, const long long* __restrict__ n_items_p,
-                           long long n_cand, const int* __restrict__ item_row, long long* tile_item0,
-                           long long* tile_first, long long* tile_next, int* tile_starts, int* tile_row) {
+                           const int* __restrict__ item_row, int* tile_item, int* tile_row) {
   const long long ni = *n_items_p;
-  const long long n_tiles = (n_cand + kTile - 1) / kTile;
   const int lane = threadIdx.x & 31;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < ni; i += nw) {
-    const long long a = item_off[i], b = item_off[i + 1];
-    const long long next = i + 1 < ni ? b : n_cand;
+    const long long a = item_off[i] / kTile, b = item_off[i + 1] / kTile;
     const int r = item_row[i];
-    // tiles whose first candidate lies in item i
-    for (long long t = (a + kTile - 1) / kTile + lane; t * kTile < b && t < n_tiles; t += 32) {
-      tile_item0[t] = i;
-      tile_next[t] = next;
+    for (long long t = a + lane; t < b; t += 32) {
+      tile_item[t] = (int)i;
       tile_row[t] = r;
     }
-    // tiles whose first candidate is in (off[i-1], off[i]]: item i is the first one starting at or after it
-    const long long prev = i > 0 ? item_off[i - 1] : -1;
-    for (long long t = (prev < 0 ? 0 : prev / kTile + 1) + lane; t * kTile <= a && t < n_tiles; t += 32) {
-      tile_first[t] = i;
-      tile_starts[t] = a < min(n_cand, (t + 1) * kTile);
-    }
-    // tiles starting after the last item's start: no item starts at or after them
-    if (i == ni - 1)
-      for (long long t = a / kTile + 1 + lane; t < n_tiles; t += 32) {
-        tile_first[t] = ni;
-        tile_starts[t] = 0;
-      }
   }
 }
 
@@ -1663,20 +1729,40 @@ __global__ void k_tile_map(const long long* __restrict__ item_off, const long lo
 #define DSC_COUNT_MINB 16
 #endif
 
+// kept entries per tile.  Each lane takes one tile and forms its threshold
+// from the final row maximum M.  The evaluation counted the tile against the
+// bound L its item started with: when no value lay in L's band or near L
+// (flag clear) and M's window lies below L's kept bound (M.uhi <= L.ukeep),
+// every value is at or below L.ulo <= M.ulo (dropped) or at or above
+// L.ukeep >= M.uhi (kept), none is near M, and that count is the tile's.
+// The warp counts the other tiles from their values, one at a time.
 __global__ void __launch_bounds__(kEvalThreads, DSC_COUNT_MINB) k_tile_count(CompactParams p, int* tile_cnt) {
   const int lane = threadIdx.x & 31;
-  const long long t0 = ((long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5)) * kCountTilesPerWarp;
-  if (t0 * kTile >= p.n_cand) return;                  // warp-uniform
-  TileKeep K[kCountTilesPerWarp];
-#pragma unroll
-  for (int u = 0; u < kCountTilesPerWarp; ++u)
-    if ((t0 + u) * kTile < p.n_cand) tile_load<false>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
-#pragma unroll
-  for (int u = 0; u < kCountTilesPerWarp; ++u) {
-    const long long tile = t0 + u;
-    if (tile * kTile >= p.n_cand) break;               // warp-uniform
-    tile_decide<false>(p, tile * kTile + (long long)lane * kTilePer, tile, K[u]);
-    int c = K[u].cnt;
+  const long long n_tiles = p.n_cand / kTile;
+  const long long t0 = ((long long)blockIdx.x * kTileWarps + (threadIdx.x >> 5)) * 32;
+  if (t0 >= n_tiles) return;                           // warp-uniform
+  const long long t = t0 + lane;
+  bool slow = false;
+  if (t < n_tiles) {
+    const int r = p.tile_row[t];
+    const float M = __uint_as_float(p.row_max[r]);
+    p.tile_thr[t] = p.tau * M;
+    if (p.value_dtype == 1) p.tile_scale[t] = p.slot->beam_scale[p.rows[r].beam];
+    const unsigned meta = p.tile_meta[t];
+    const Decide DM = decide_at(p.tau, p.inv_tau_m, M);
+    const Decide DL = decide_at(p.tau, p.inv_tau_m, __uint_as_float(p.item_L[p.tile_item[t]]));
+    if ((meta >> 8) == 0u && DM.uhi <= DL.ukeep) tile_cnt[t] = (int)(meta & 0xffu);
+    else slow = true;
+  }
+  unsigned todo = __ballot_sync(0xffffffffu, slow);
+  while (todo) {                                       // warp-uniform
+    const long long tile = t0 + (__ffs(todo) - 1);
+    todo &= todo - 1u;
+    const long long p0 = tile * kTile + (long long)lane * kTilePer;
+    TileKeep K;
+    tile_load<false>(p, p0, K);
+    tile_decide<false>(p, p0, tile, K);
+    int c = K.cnt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0) tile_cnt[tile] = c;
@@ -1688,21 +1774,18 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_write(C
   __shared__ int s_col[kTileWarps][kTile];
   __shared__ float s_val[kTileWarps][kTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long n = p.n_cand;
+  const long long n_tiles = p.n_cand / kTile;
   const long long t0 = ((long long)blockIdx.x * kTileWarps + w) * kTilesPerWarp;
-  if (t0 * kTile >= n) return;                         // warp-uniform
-  const long long ni = *p.n_items;
-  const long long* __restrict__ off = p.item_off;
+  if (t0 >= n_tiles) return;                           // warp-uniform
   TileKeep K[kTilesPerWarp];
 #pragma unroll
   for (int u = 0; u < kTilesPerWarp; ++u)
-    if ((t0 + u) * kTile < n) tile_load<true>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
+    if (t0 + u < n_tiles) tile_load<true>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
 #pragma unroll
   for (int u = 0; u < kTilesPerWarp; ++u) {
     const long long tile = t0 + u;
-    if (tile * kTile >= n) break;                      // warp-uniform
-    const long long p0 = tile * kTile + (long long)lane * kTilePer;
-    tile_decide<true>(p, p0, tile, K[u]);
+    if (tile >= n_tiles) break;                        // warp-uniform
+    tile_decide<true>(p, tile * kTile + (long long)lane * kTilePer, tile, K[u]);
     const int cnt = __popc(K[u].keep);
     int incl = cnt;
 #pragma unroll
@@ -1711,19 +1794,8 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_write(C
       if (lane >= o) incl += x;
     }
     const int tot = __shfl_sync(0xffffffffu, incl, 31);
-    const int excl = incl - cnt;
     const long long prefix = tile_off[tile];
-    // kept count before each item start in this lane's range (items starting
-    // exactly at the tile's first candidate go to lane 0)
-    if (p.tile_starts[tile]) {                         // warp-uniform
-      long long j = p.tile_first[tile];
-      while (j < ni && off[j] < p0) ++j;
-      for (; j < ni && off[j] < p0 + kTilePer && off[j] < n; ++j) {
-        int r = (int)(off[j] - p0);
-        p.item_out[j] = prefix + excl + __popc(K[u].keep & ((1u << r) - 1u));
-      }
-    }
-    int q = excl;
+    int q = incl - cnt;
 #pragma unroll
     for (int i = 0; i < kTilePer; ++i) {
       if (K[u].keep & (1u << i)) {
@@ -1753,16 +1825,17 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_write(C
 
 // CSR row pointers of one instance (rows [row_base, row_base + nrows)),
 // relative to the instance's first output slot, which goes to inst_begin.
-// Row r starts at item row_item_base[r]; the kept count before it is
-// item_out of that item, or the total when the item starts past the end.
+// Row r starts at item row_item_base[r]; the kept count before it is the
+// output offset of that item's first tile, or the total when the item starts
+// past the end.
 __global__ void k_row_ptr(const long long* __restrict__ row_item_base, const long long* __restrict__ item_off,
-                          const long long* __restrict__ item_out, const long long* __restrict__ n_items_p,
-                          const long long* __restrict__ total_p, long long n_cand, int row_base, int nrows,
-                          long long rp_off, int inst, int last, const OutSlot* __restrict__ slot) {
+                          const long long* __restrict__ tile_off, const long long* __restrict__ n_items_p,
+                          long long n_cand, int row_base, int nrows, long long rp_off, int inst, int last,
+                          const OutSlot* __restrict__ slot) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const long long ni = *n_items_p, total = *total_p;
+  const long long ni = *n_items_p, total = tile_off[n_cand / kTile];
   auto kept_before = [&](long long i) -> long long {
-    return (i >= ni || item_off[i] >= n_cand) ? total : item_out[i];
+    return (i >= ni || item_off[i] >= n_cand) ? total : tile_off[item_off[i] / kTile];
   };
   const long long b = kept_before(row_item_base[row_base]);
   if (r <= nrows) slot->row_ptr[rp_off + r] = kept_before(row_item_base[row_base + r]) - b;

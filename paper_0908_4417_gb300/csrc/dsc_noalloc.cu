@@ -31,16 +31,16 @@ __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
 __global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*);
 __global__ void k_slices(const DInst*, DRow*, int, int*, int*, int, int*);
 __global__ void k_item_rows(const long long*, int, int*);
-__global__ void k_tile_map(const long long*, const long long*, long long, const int*, long long*, long long*,
-                           long long*, int*, int*);
+__global__ void k_tile_map(const long long*, const long long*, const int*, int*, int*);
+__global__ void k_row_bound(const DInst*, const DRow*, int, const float*, int, SliceTab, unsigned*);
 __global__ void k_eval(EvalParams);
 __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_lut_pairs(const float4*, int, int, float4*);
 __global__ void k_refine(RefineParams);
 __global__ void k_refine_rowmax(RefineParams);
 __global__ void k_tile_write(CompactParams, const long long*);
-__global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, const long long*,
-                          long long, int, int, long long, int, int, const OutSlot*);
+__global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, long long, int, int,
+                          long long, int, int, const OutSlot*);
 __global__ void k_scan_partial(const int*, const long long*, long long, long long*);
 __global__ void k_scan_blocks(long long*);
 __global__ void k_scan_final(const int*, const long long*, long long, const long long*, long long*);
@@ -164,6 +164,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   I.idx = 1.0 / I.dx; I.idy = 1.0 / I.dy; I.idz = 1.0 / I.dz;
   I.lut_scale = (float)((model->n - 1) / model->d_max);
   float c3max = 0.f;
+  int kpeak = 0;
   for (int k = 0; k < model->n; ++k) {
     for (int c = 1; c <= 3; ++c) {
       const float w = model->table4[4 * k + c];
@@ -172,8 +173,10 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
     if (!std::isfinite(model->table4[4 * k])) return na_fail(DSC_E_INVAL, "model: T(d) must be finite");
     float v = model->table4[4 * k + 1];
     c3max = v > c3max ? v : c3max;
+    if (model->table4[4 * k] > model->table4[4 * kpeak]) kpeak = k;
   }
   I.c3max = c3max;
+  I.d_peak = (float)(kpeak * (model->d_max / (model->n - 1)));
   for (int i = 0; i < 3; ++i) { I.c1q[i] = (float)(model->c1[i] / 4.0); I.c2h[i] = (float)(model->c2[i] / 2.0); }
   I.cutoff_mode = model->cutoff_mode;
   I.cutoff_k = (float)model->cutoff_k;
@@ -300,8 +303,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   int* d_item_cand = cv.take<int>(n_items);
   int* d_item_row = cv.take<int>(n_items);
   long long* d_item_off = cv.take<long long>(n_items + 1);
-  long long* d_item_out = cv.take<long long>(n_items + 1);
-  if (!d_item_out)
+  unsigned* d_item_L = cv.take<unsigned>(n_items);
+  if (!d_item_L)
     return na_fail(DSC_E_INVAL, "needs more than %zu bytes of working memory (the fixed maximum): %lld work items",
                    kNoAllocBytes, n_items);
   const long long* n_items_dev = d_rib + nrows;
@@ -309,6 +312,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
     k_trilinear_table<<<nrows, kSiddonThreads, 0, s>>>(d_inst, d_rows, nrows, d_tables, stride);
   else
     k_siddon<<<nrows, kSiddonThreads, 0, s>>>(d_inst, d_rows, nrows, d_tables, stride);
+  NA_LAUNCH();
+  k_row_bound<<<(nrows + 3) / 4, 128, 0, s>>>(d_inst, d_rows, nrows, d_tables, stride, slices, d_row_max);
   NA_LAUNCH();
   k_item_rows<<<(nrows + 127) / 128, 128, 0, s>>>(d_rib, nrows, d_item_row);
   NA_LAUNCH();
@@ -320,18 +325,16 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   long long n_cand = 0;
   NA_CU(cudaMemcpyAsync(&n_cand, d_item_off + n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
   NA_CU(cudaStreamSynchronize(s));
-  const long long n_tiles = (n_cand + kTile - 1) / kTile;
+  const long long n_tiles = n_cand / kTile;           // items are whole tiles
   float* d_vals = cv.take<float>(n_cand + 4);
   int* d_cols = cv.take<int>(n_cand + 4);
   int* d_tile_cnt = cv.take<int>(n_tiles);
   long long* d_tile_off = cv.take<long long>(n_tiles + 1);
-  long long* d_tile_item0 = cv.take<long long>(n_tiles);
-  long long* d_tile_first = cv.take<long long>(n_tiles);
   float* d_tile_thr = cv.take<float>(n_tiles);
   float* d_tile_scale = cv.take<float>(n_tiles);
-  long long* d_tile_next = cv.take<long long>(n_tiles);
-  int* d_tile_starts = cv.take<int>(n_tiles);
   int* d_tile_row = cv.take<int>(n_tiles);
+  int* d_tile_item = cv.take<int>(n_tiles);
+  unsigned* d_tile_meta = cv.take<unsigned>(n_tiles);
   const int cap_u = (int)std::min<long long>(std::max<long long>(1 << 16, n_cand >> 10), 1 << 28);
   unsigned long long* d_rlist_u = cv.take<unsigned long long>(cap_u);
   if (!d_rlist_u)
@@ -355,6 +358,10 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   ep.row_max = d_row_max;
   ep.row_cand = d_row_cand;
   ep.item_counter = d_counter;
+  ep.tau = (float)opts->rel_threshold;
+  ep.inv_tau_m = ep.tau > 0.0f ? (1.0f - kRefineDelta) / ep.tau : std::numeric_limits<float>::infinity();
+  ep.tile_meta = d_tile_meta;
+  ep.item_L = d_item_L;
   k_eval<<<grid_eval, kEvalThreads, 0, s>>>(ep);
   NA_LAUNCH();
   OutSlot q{};
@@ -377,14 +384,12 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.cols = d_cols;
   cp.row_max = d_row_max;
   cp.tau = (float)opts->rel_threshold;
-  cp.item_out = d_item_out;
-  cp.tile_item0 = d_tile_item0;
-  cp.tile_first = d_tile_first;
   cp.tile_thr = d_tile_thr;
   cp.tile_scale = d_tile_scale;
-  cp.tile_next = d_tile_next;
-  cp.tile_starts = d_tile_starts;
   cp.tile_row = d_tile_row;
+  cp.tile_item = d_tile_item;
+  cp.tile_meta = d_tile_meta;
+  cp.item_L = d_item_L;
   cp.value_dtype = DSC_VALUE_F32;
   cp.slot = d_slot;
   cp.rlist_u = d_rlist_u;
@@ -395,8 +400,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.cap_u = cap_u;
   cp.nrows = nrows;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
-  k_tile_map<<<1024, 256, 0, s>>>(d_item_off, n_items_dev, n_cand, d_item_row, d_tile_item0, d_tile_first, d_tile_next,
-                                 d_tile_starts, d_tile_row);
+  k_tile_map<<<1024, 256, 0, s>>>(d_item_off, n_items_dev, d_item_row, d_tile_item, d_tile_row);
   NA_LAUNCH();
   // kept count first, so the capacity is checked before any output is touched
   const unsigned tiles = compact_blocks(n_tiles);
@@ -445,8 +449,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
     return na_fail(DSC_E_INVAL, "output capacity %lld < %lld kept entries", (long long)capacity, nnz);
   k_tile_write<<<tiles, kEvalThreads, 0, s>>>(cp, d_tile_off);
   NA_LAUNCH();
-  k_row_ptr<<<(nrows + 1 + 255) / 256, 256, 0, s>>>(d_rib, d_item_off, d_item_out, n_items_dev, d_tile_off + n_tiles,
-                                                    n_cand, 0, nrows, 0, 0, 1, d_slot);
+  k_row_ptr<<<(nrows + 1 + 255) / 256, 256, 0, s>>>(d_rib, d_item_off, d_tile_off, n_items_dev, n_cand, 0, nrows, 0,
+                                                    0, 1, d_slot);
   NA_LAUNCH();
   NA_CU(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   NA_CU(cudaStreamSynchronize(s));   // the array is free for the next call once this returns
