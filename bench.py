@@ -312,6 +312,7 @@ def run_ours(args):
             if k == 0:
                 table_entries = int(dsc.dsc_get_beamlets(r, nrows)[:, 15].sum())
                 refine_nt, refine_nm, refine_fp32 = dsc.dsc_get_refine_counts(r)
+                tiles, tiles_read = dsc.dsc_get_tile_counts(r)
             dsc.dsc_release_result(r)
         # ---- timed region: K steps, device time ----
         stream.synchronize()
@@ -458,7 +459,9 @@ def run_ours(args):
                    "stage_ms": stage_ms,
                    "stage_basis": "per-stage CUDA events in separate steps after the timed region",
                    "fp64_refined_pairs": {"near_threshold": refine_nt, "near_row_max": refine_nm,
-                                          "fp32_decided_past_capacity": refine_fp32}},
+                                          "fp32_decided_past_capacity": refine_fp32},
+                   "compaction_tiles": {"tiles": tiles, "candidates_per_tile": 128,
+                                        "values_read_by_count_pass": tiles_read}},
         "e2e": {"value": whole_job_rate(pairs, e2e_steps, world, e2e_s), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps,
                 "host_wall_ms_per_step": 1e3 * wall_s / e2e_steps,

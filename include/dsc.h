@@ -297,6 +297,15 @@ dsc_status dsc_get_depth_tables(dsc_result* res, float* out, int64_t cap, int32_
  * one exact arithmetic makes. */
 dsc_status dsc_get_refine_counts(dsc_result* res, int64_t* near_threshold, int64_t* near_max,
                                  int64_t* fp32_decided);
+/* Compaction tiles of the computation (all instances of its launch; 128
+ * candidate slots each, work items padded to whole tiles), and those whose
+ * values the count pass read.  The others took the count the evaluation
+ * formed against a lower bound of their row maximum (the running maximum
+ * when their work item started, seeded from the voxels by the beamlet axis),
+ * which is the tile's exact count whenever the final threshold lies within
+ * 2^-16 of that bound's and no value of the tile lies near either; a tile
+ * read or not gives the same CSR. */
+dsc_status dsc_get_tile_counts(dsc_result* res, int64_t* tiles, int64_t* tiles_read);
 /* Per row: max D over the row's candidates and the candidate count. */
 dsc_status dsc_get_row_stats(dsc_result* res, float* row_max, int64_t* row_cand);
 /* Milliseconds per stage (needs DSC_FLAG_TIMING): [set-up + item scan, Siddon

@@ -165,6 +165,7 @@ struct OutBufs {
   int device = 0;
   cudaEvent_t done = nullptr;        // end of the computation that writes these buffers
   OutSlot slot{};                    // row_ptr, col, val, beam_scale, row_max, row_cand, inst_begin, status
+  long long n_tiles = 0;             // compaction tiles of the launch
   ~OutBufs() {
     void* ps[] = {slot.row_ptr, slot.col, slot.val, slot.beam_scale, slot.row_max, slot.row_cand, slot.inst_begin,
                   slot.status, slot.refine};
@@ -250,7 +251,7 @@ struct Plan {
   int* d_counter = nullptr;
   // decisions the FP32 values cannot settle (the count pass lists them)
   unsigned long long* d_rlist_u = nullptr;   // near a threshold: cap_u entries
-  unsigned long long* d_rcount = nullptr;    // [3] listed counts
+  unsigned long long* d_rcount = nullptr;    // [4] listed counts, tiles counted from their values
   int* d_mcount = nullptr;                   // per row: near-maximum candidates seen
   long long* d_mslot = nullptr;              // per row: kMaxSlots near-maximum candidates
   int* d_ovf_rows = nullptr;                 // rows that overflowed their near-maximum slots
@@ -601,7 +602,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_scan, kScanBlocks + 1, s));
   TRY(dalloc(&P->d_counter, 4, s));
   if (P->nrows >= (1 << 24)) return fail(DSC_E_INVAL, "too many beamlets in one launch (%d)", P->nrows);
-  TRY(dalloc(&P->d_rcount, 3, s));
+  TRY(dalloc(&P->d_rcount, 4, s));
   TRY(dalloc(&P->d_mcount, P->nrows, s));
   TRY(dalloc(&P->d_ovf_rows, P->nrows, s));
   TRY(dalloc(&P->d_row_max64, P->nrows, s));
@@ -739,7 +740,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   CU(cudaMemsetAsync(P->d_row_max, 0, sizeof(unsigned) * P->nrows, s));
   CU(cudaMemsetAsync(P->d_row_cand, 0, sizeof(long long) * P->nrows, s));
   CU(cudaMemsetAsync(P->d_counter, 0, sizeof(int) * 4, s));
-  CU(cudaMemsetAsync(P->d_rcount, 0, sizeof(unsigned long long) * 3, s));
+  CU(cudaMemsetAsync(P->d_rcount, 0, sizeof(unsigned long long) * 4, s));
   CU(cudaMemsetAsync(P->d_mcount, 0, sizeof(int) * P->nrows, s));
   // a1: beamlet frames, entry/exit, VOI box, work items
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
@@ -883,7 +884,8 @@ static dsc_status alloc_outputs(Plan* P, cudaStream_t s, std::shared_ptr<OutBufs
   TRY(dalloc(&q.row_max, P->nrows, s));
   TRY(dalloc(&q.row_cand, P->nrows, s));
   TRY(dalloc(&q.inst_begin, P->ninst + 1, s));
-  TRY(dalloc(&q.refine, 3, s));
+  TRY(dalloc(&q.refine, 4, s));
+  O->n_tiles = P->n_tiles;
   TRY(dalloc(&q.status, 1, s));
   CU(cudaMemsetAsync(q.status, 0, sizeof(int), s));
   if (P->opts.value_dtype != DSC_VALUE_BF16) {
@@ -1261,6 +1263,16 @@ extern "C" dsc_status dsc_get_refine_counts(dsc_result* r, int64_t* near_thresho
   *near_threshold = (int64_t)c[0];
   *near_max = (int64_t)c[1];
   if (fp32_decided) *fp32_decided = (int64_t)c[2];
+  return DSC_OK;
+}
+
+extern "C" dsc_status dsc_get_tile_counts(dsc_result* r, int64_t* tiles, int64_t* tiles_read) {
+  if (!r || !tiles || !tiles_read) return fail(DSC_E_INVAL, "null argument");
+  CU(cudaEventSynchronize(r->done));
+  unsigned long long c[4] = {0, 0, 0, 0};
+  CU(cudaMemcpy(c, r->out->slot.refine, sizeof c, cudaMemcpyDeviceToHost));
+  *tiles = r->out->n_tiles;
+  *tiles_read = (int64_t)c[3];
   return DSC_OK;
 }
 

@@ -139,8 +139,9 @@ struct OutSlot {
   long long* row_cand;     // per row
   long long* inst_begin;   // per instance: first output slot; [ninst] = total
   int* status;             // nonzero: kStatusWait (a bounded device wait expired) or kStatusIndex
-  unsigned long long* refine;  // [3] pairs listed for the FP64 re-evaluation: near a threshold, near a row
-                               // maximum; near-threshold pairs past the list's capacity (decided in FP32)
+  unsigned long long* refine;  // [4] pairs listed for the FP64 re-evaluation: near a threshold, near a row
+                               // maximum; near-threshold pairs past the list's capacity (decided in FP32);
+                               // compaction tiles whose values the count pass read
 };
 
 constexpr int kTilePer = 4;                       // candidates per thread of the compaction
@@ -189,7 +190,8 @@ struct CompactParams {
   // slots (kMaxSlots per row)
   unsigned long long* rlist_u;   // refine_entry(candidate, row)
   unsigned long long* rcount;     // [0] entries listed in rlist_u, [1] near-maximum candidates (may exceed capacities),
-                                  // [2] rows with more than kMaxSlots near-maximum candidates (listed in ovf_rows)
+                                  // [2] rows with more than kMaxSlots near-maximum candidates (listed in ovf_rows),
+                                  // [3] tiles counted from their values
   int* mcount;                    // per row: near-maximum candidates seen
   long long* mslot;               // per row: kMaxSlots candidate indices
   int* ovf_rows;                  // rows whose near-maximum candidates overflowed their slots (nrows entries)

@@ -1755,6 +1755,7 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COUNT_MINB) k_tile_count(Com
     else slow = true;
   }
   unsigned todo = __ballot_sync(0xffffffffu, slow);
+  if (lane == 0 && todo) atomicAdd(p.rcount + 3, (unsigned long long)__popc(todo));
   while (todo) {                                       // warp-uniform
     const long long tile = t0 + (__ffs(todo) - 1);
     todo &= todo - 1u;
@@ -1847,7 +1848,8 @@ __global__ void k_row_ptr(const long long* __restrict__ row_item_base, const lon
 
 // per-row statistics into the result; refine = {pairs listed near a
 // threshold (within the list's capacity), near-maximum candidates, listed
-// pairs past the capacity (their decision stayed FP32)}
+// pairs past the capacity (their decision stayed FP32), tiles counted from
+// their values}
 __global__ void k_copy_stats(const unsigned* __restrict__ row_max, const long long* __restrict__ row_cand, int nrows,
                              const unsigned long long* __restrict__ rcount, int cap_u,
                              const OutSlot* __restrict__ slot) {
@@ -1861,6 +1863,7 @@ __global__ void k_copy_stats(const unsigned* __restrict__ row_max, const long lo
     slot->refine[0] = n0 < cap ? n0 : cap;
     slot->refine[1] = rcount[1];
     slot->refine[2] = n0 > cap ? n0 - cap : 0ull;
+    slot->refine[3] = rcount[3];
   }
 }
 

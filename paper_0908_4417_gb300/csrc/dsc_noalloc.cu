@@ -243,7 +243,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   float* d_scale = cv.take<float>(1);
   int* d_status = cv.take<int>(1);
   long long* d_inst_begin = cv.take<long long>(2);
-  unsigned long long* d_rcount = cv.take<unsigned long long>(3);
+  unsigned long long* d_rcount = cv.take<unsigned long long>(4);
   int* d_mcount = cv.take<int>(nrows);
   long long* d_mslot = cv.take<long long>((size_t)nrows * kMaxSlots);
   int* d_ovf_rows = cv.take<int>(nrows);
@@ -261,7 +261,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   I.d_max = model->d_max;
   for (int i = 0; i < 3; ++i) { I.c1d[i] = model->c1[i]; I.c2d[i] = model->c2[i]; }
   NA_CU(cudaMemcpyAsync(d_inst, &I, sizeof(DInst), cudaMemcpyHostToDevice, s));
-  NA_CU(cudaMemsetAsync(d_rcount, 0, sizeof(unsigned long long) * 3, s));
+  NA_CU(cudaMemsetAsync(d_rcount, 0, sizeof(unsigned long long) * 4, s));
   NA_CU(cudaMemsetAsync(d_mcount, 0, sizeof(int) * nrows, s));
   for (int b = 0, row = 0; b < nbeams; ++b) {
     DBeam D{};

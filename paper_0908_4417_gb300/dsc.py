@@ -36,7 +36,7 @@ EXPORTS = [
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
     "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune", "dsc_dose", "dsc_beamlet_dot",
     "dsc_measure_alu_peaks", "dsc_probe_tail", "dsc_get_refine_counts", "dsc_get_server_timing",
-    "dsc_measure_host_link",
+    "dsc_measure_host_link", "dsc_get_tile_counts",
 ]
 
 
@@ -127,6 +127,7 @@ def lib():
             "dsc_measure_host_link": (C.c_int, [I64, I32, C.POINTER(C.c_double), I32, P]),
             "dsc_probe_tail": (C.c_int, [I32, P, I64, P, P, P]),
             "dsc_get_refine_counts": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
+            "dsc_get_tile_counts": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64)]),
             "dsc_get_server_timing": (C.c_int, [P, C.POINTER(I32), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
@@ -290,6 +291,14 @@ def dsc_get_refine_counts(res) -> tuple:
     a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
     _check(lib().dsc_get_refine_counts(res, C.byref(a), C.byref(b), C.byref(c)))
     return int(a.value), int(b.value), int(c.value)
+
+
+def dsc_get_tile_counts(res) -> tuple:
+    """(compaction tiles of the launch, tiles whose values the count pass
+    read; the others took the evaluation's own count)."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().dsc_get_tile_counts(res, C.byref(a), C.byref(b)))
+    return int(a.value), int(b.value)
 
 
 def dsc_get_server_timing(res) -> tuple:

@@ -61,6 +61,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.dsc_probe_tail(0, None, 0, None, None, None) == 0       # nothing to do
     a, b = C.c_int64(), C.c_int64()
     assert lib.dsc_get_refine_counts(None, C.byref(a), C.byref(b), C.byref(a)) == 1
+    assert lib.dsc_get_tile_counts(None, C.byref(a), C.byref(b)) == 1
 
 
 def test_struct_layouts_match_header():

@@ -5,6 +5,7 @@ Acceptance: CSR structure identical outside the oracle's ambiguity bands
 values within 1e-4 maximum relative error; BF16 values (scaled per beam)
 within 2^-8 relative.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -58,7 +59,11 @@ def test_prostate_full_matrix(dsc):
     orc = O.compute_workload(w)
     st = compare(gpu_rows(csr, range(w.nrows)), orc, TOL)
     assert abs(csr.pairs - orc.pairs) <= len(orc.amb_row)
-    print("prostate full", st)
+    # the row bounds by the axis are the rows' maxima here: the count pass
+    # reads few tiles (those holding a value near a threshold or a maximum)
+    tiles, read = dsc.dsc_get_tile_counts(res)
+    assert tiles * 128 >= csr.pairs and 0 <= read < 0.05 * tiles, (tiles, read)
+    print("prostate full", st, "tiles", tiles, "read", read)
     cleanup(dsc, res, g)
 
 
@@ -71,6 +76,24 @@ def test_water_32_full(dsc):
     assert abs(csr.pairs - orc.pairs) <= len(orc.amb_row)
     print("water_32", st)
     cleanup(dsc, res, g)
+
+
+def test_tile_counts_without_a_threshold(dsc):
+    """tau = 0 keeps every positive value: the evaluation's count of every
+    tile is its count (no refinement window, nothing near a maximum to
+    decide), the count pass reads no value, and the CSR is the oracle's."""
+    w = dataclasses.replace(P.water_32(), tau=0.0)
+    csr, res, g = run(dsc, w)
+    try:
+        tiles, read = dsc.dsc_get_tile_counts(res)
+        assert tiles > 0 and read == 0, (tiles, read)
+        orc = O.compute_workload(w)
+        st = compare(gpu_rows(csr, range(w.nrows)), orc, TOL)
+        assert abs(csr.pairs - orc.pairs) <= len(orc.amb_row)
+        assert 0 < csr.nnz <= csr.pairs
+        print("water_32 tau 0", st)
+    finally:
+        cleanup(dsc, res, g)
 
 
 def test_slabs_128_fp32_full(dsc):
