@@ -1400,7 +1400,7 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_EVAL_MINBLOCKS) k_eval(EvalP
 // one warp per row.  Past the depth dT where the depth-dose factor T(d) of
 // the beam model peaks, every factor of Eq. 2 falls along the beamlet axis,
 // and laterally the dose is largest on the axis, so a row's maximum lies by
-// the axis at a depth below dT.  Up to 32 points of the axis, half a voxel
+// the axis at a depth below dT.  Up to 32 points of the axis, a voxel
 // apart where they fit, span the stretch where the radiological depth (the
 // row's table) lies in [dT - 10 mm, dT + 2 mm]; the 8 voxels whose centres
 // surround each point, those that are candidates of the row, are evaluated
@@ -1458,7 +1458,7 @@ __global__ void __launch_bounds__(128) k_row_bound(const DInst* __restrict__ ins
   const float hd = (float)G.hd;
   const float ta = R.tA_f + (float)k0 * hd, span = (float)(k1 - k0) * hd;
   const float vmin = (float)fmin(G.dx, fmin(G.dy, G.dz));
-  const int np = min(32, (int)(span / (0.5f * vmin)) + 1);
+  const int np = min(32, (int)(span / vmin) + 1);
   const float dt = np > 1 ? span / (float)(np - 1) : 0.0f;
   const int* pre = T.pre + (size_t)row * T.stride;
   const int* ylo = T.lo + (size_t)row * T.stride;
@@ -1778,14 +1778,20 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_write(C
   const long long n_tiles = p.n_cand / kTile;
   const long long t0 = ((long long)blockIdx.x * kTileWarps + w) * kTilesPerWarp;
   if (t0 >= n_tiles) return;                           // warp-uniform
+  // the tiles' output offsets first: a tile that keeps nothing is not read
+  static_assert(kTilesPerWarp == 2, "three offsets");
+  const long long o0 = tile_off[t0], o1 = tile_off[min(t0 + 1, n_tiles)], o2 = tile_off[min(t0 + 2, n_tiles)];
   TileKeep K[kTilesPerWarp];
 #pragma unroll
-  for (int u = 0; u < kTilesPerWarp; ++u)
-    if (t0 + u < n_tiles) tile_load<true>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
+  for (int u = 0; u < kTilesPerWarp; ++u) {
+    if (t0 + u < n_tiles && (u == 0 ? o1 > o0 : o2 > o1)) tile_load<true>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
+    else K[u] = TileKeep{};                             // not read: defined on every path, so K stays in registers
+  }
 #pragma unroll
   for (int u = 0; u < kTilesPerWarp; ++u) {
     const long long tile = t0 + u;
-    if (tile >= n_tiles) break;                        // warp-uniform
+    const long long prefix = u == 0 ? o0 : o1;
+    if (tile >= n_tiles || (u == 0 ? o1 : o2) == prefix) continue;   // warp-uniform: past the end, or nothing kept
     tile_decide<true>(p, tile * kTile + (long long)lane * kTilePer, tile, K[u]);
     const int cnt = __popc(K[u].keep);
     int incl = cnt;
@@ -1795,7 +1801,6 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_write(C
       if (lane >= o) incl += x;
     }
     const int tot = __shfl_sync(0xffffffffu, incl, 31);
-    const long long prefix = tile_off[tile];
     int q = incl - cnt;
 #pragma unroll
     for (int i = 0; i < kTilePer; ++i) {
