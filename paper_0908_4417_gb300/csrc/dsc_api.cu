@@ -33,7 +33,7 @@
 
 namespace dsc {
 // kernels (dsc_kernels.cu)
-__global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int);
+__global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int, StepClear);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
 __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
 __global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*);
@@ -619,7 +619,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
 
   // sizes: items (from the set-up) and candidates (from the count)
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
-                                                 P->d_row_items, P->target_cand);
+                                                 P->d_row_items, P->target_cand, StepClear{});
   CHECK_LAUNCH();
   k_slices<<<(P->nrows + 3) / 4, 128, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_slice_pre, P->d_slice_lo,
                                               P->slice_stride, P->d_row_items);
@@ -737,14 +737,9 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   int k0 = (int)g_launches.load();
   const long long* n_items = P->d_row_item_base + P->nrows;
   TRY(record(ev, 0, s));
-  CU(cudaMemsetAsync(P->d_row_max, 0, sizeof(unsigned) * P->nrows, s));
-  CU(cudaMemsetAsync(P->d_row_cand, 0, sizeof(long long) * P->nrows, s));
-  CU(cudaMemsetAsync(P->d_counter, 0, sizeof(int) * 4, s));
-  CU(cudaMemsetAsync(P->d_rcount, 0, sizeof(unsigned long long) * 4, s));
-  CU(cudaMemsetAsync(P->d_mcount, 0, sizeof(int) * P->nrows, s));
-  // a1: beamlet frames, entry/exit, VOI box, work items
+  const StepClear clr{P->d_row_max, P->d_row_cand, P->d_mcount, P->d_counter, P->d_rcount};
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
-                                                 P->d_row_items, P->target_cand);
+                                                 P->d_row_items, P->target_cand, clr);
   CHECK_LAUNCH();
   k_slices<<<(P->nrows + 3) / 4, 128, 0, s>>>(P->d_inst, P->d_rows, P->nrows, P->d_slice_pre, P->d_slice_lo,
                                               P->slice_stride, P->d_row_items);

@@ -24,6 +24,17 @@ constexpr long long kSmallScan = 4096;   // inputs up to this length use the one
 // float-float value: hi + lo with |lo| <= ulp(hi)/2 (compensated FP32)
 struct ff { float hi, lo; };
 
+// The accumulators of one computation, cleared by k_setup (one thread per
+// row; thread 0 the counters) instead of separate memsets: null pointers are
+// left alone.
+struct StepClear {
+  unsigned* row_max;               // nrows
+  long long* row_cand;             // nrows
+  int* mcount;                     // nrows
+  int* counter;                    // 4
+  unsigned long long* rcount;      // 4
+};
+
 // One geometry of a launch.
 struct DInst {
   const float* rho;        // density [nz][ny][nx]

@@ -81,9 +81,16 @@ __device__ inline void normalize3(double* v) {
 __device__ inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
 __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict__ beams, int nbeams, DRow* rows,
-                        int nrows, int* row_items, int target_cand) {
+                        int nrows, int* row_items, int target_cand, StepClear clr) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrows) return;
+  if (clr.row_max) {
+    clr.row_max[r] = 0u;
+    clr.row_cand[r] = 0;
+    clr.mcount[r] = 0;
+    if (r == 0)
+      for (int k = 0; k < 4; ++k) { clr.counter[k] = 0; clr.rcount[k] = 0ull; }
+  }
   int lo = 0, hi = nbeams - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;

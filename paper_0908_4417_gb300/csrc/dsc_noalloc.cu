@@ -25,7 +25,7 @@
 #include <mutex>
 
 namespace dsc {
-__global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int);
+__global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int, StepClear);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
 __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
 __global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*);
@@ -291,7 +291,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   const int grid_items = (nb > 0 ? nb : 1) * sms;
 
   // set-up and work items
-  k_setup<<<(nrows + 31) / 32, 32, 0, s>>>(d_inst, d_beams, nbeams, d_rows, nrows, d_row_items, target_cand);
+  k_setup<<<(nrows + 31) / 32, 32, 0, s>>>(d_inst, d_beams, nbeams, d_rows, nrows, d_row_items, target_cand,
+                                           StepClear{});
   NA_LAUNCH();
   k_slices<<<(nrows + 3) / 4, 128, 0, s>>>(d_inst, d_rows, nrows, d_slice_pre, d_slice_lo, slice_stride, d_row_items);
   NA_LAUNCH();
