@@ -36,10 +36,11 @@ namespace dsc {
 __global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int, StepClear);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
 __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
-__global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*);
+__global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*,
+                        int*, int*, int);
 __global__ void k_slices(const DInst*, DRow*, int, int*, int*, int, int*);
 __global__ void k_item_rows(const long long*, int, int*);
-__global__ void k_tile_map(const long long*, const long long*, const int*, int*, int*);
+__global__ void k_tile_map(const long long*, const long long*, const int*, int*, int*, const int*, const int*, int*);
 __global__ void k_row_bound(const DInst*, const DRow*, int, const float*, int, SliceTab, unsigned*);
 __global__ void k_eval(EvalParams);
 __global__ void k_beam_scale(const DBeam*, int, const unsigned*, const OutSlot*);
@@ -233,6 +234,9 @@ struct Plan {
   float* d_tables = nullptr;
   int* d_item_cand = nullptr;
   int* d_item_row = nullptr;
+  int* d_ord_cnt = nullptr;          // kOrderClasses: items per size class (the evaluation's queue order)
+  int* d_item_crank = nullptr;       // per item: its size class and rank in it
+  int* d_item_ord = nullptr;         // the evaluation queue's order of the items
   long long* d_item_off = nullptr;
   int* d_tile_cnt = nullptr;
   long long* d_tile_off = nullptr;   // n_tiles + 1
@@ -271,11 +275,13 @@ struct Plan {
   std::mutex mu;                     // one computation at a time per plan
   void free_scratch() {
     void* ps[] = {d_item_cand, d_item_off, d_tile_cnt, d_tile_off, d_vals, d_cols, d_item_row, d_tile_thr,
-                  d_tile_scale, d_rlist_u, d_tile_row, d_tile_item, d_tile_meta, d_item_L};
+                  d_tile_scale, d_rlist_u, d_tile_row, d_tile_item, d_tile_meta, d_item_L, d_ord_cnt,
+                  d_item_crank, d_item_ord};
     release_after(last_done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
     d_item_cand = nullptr; d_item_off = nullptr; d_tile_cnt = nullptr; d_tile_off = nullptr;
     d_vals = nullptr; d_cols = nullptr; d_item_row = nullptr; d_tile_thr = nullptr; d_tile_scale = nullptr;
     d_rlist_u = nullptr; d_tile_row = nullptr; d_tile_item = nullptr; d_tile_meta = nullptr; d_item_L = nullptr;
+    d_ord_cnt = nullptr; d_item_crank = nullptr; d_item_ord = nullptr;
     if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }
   }
   ~Plan() {
@@ -631,6 +637,10 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   TRY(dalloc(&P->d_item_row, P->n_items, s));
   TRY(dalloc(&P->d_item_off, P->n_items + 1, s));
   TRY(dalloc(&P->d_item_L, P->n_items, s));
+  TRY(dalloc(&P->d_ord_cnt, kOrderClasses, s));
+  TRY(dalloc(&P->d_item_crank, P->n_items, s));
+  TRY(dalloc(&P->d_item_ord, P->n_items, s));
+  if (P->n_items >= (1ll << kOrderRankBits)) return fail(DSC_E_INVAL, "too many work items (%lld)", P->n_items);
   int sms = 0, nb = 0;
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval, kEvalThreads, 0));
@@ -644,7 +654,7 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   CHECK_LAUNCH();
   k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, slice_tab(P.get()), P->d_row_item_base,
                                                  P->nrows, P->d_row_item_base + P->nrows, P->d_item_cand,
-                                                 P->d_item_row);
+                                                 P->d_item_row, nullptr, nullptr, P->target_cand);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_item_cand, P->d_row_item_base + P->nrows, 0, P->d_scan, P->d_item_off, s, P->n_items));
   CU(cudaMemcpyAsync(&P->n_cand, P->d_item_off + P->n_items, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -737,7 +747,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   int k0 = (int)g_launches.load();
   const long long* n_items = P->d_row_item_base + P->nrows;
   TRY(record(ev, 0, s));
-  const StepClear clr{P->d_row_max, P->d_row_cand, P->d_mcount, P->d_counter, P->d_rcount};
+  const StepClear clr{P->d_row_max, P->d_row_cand, P->d_mcount, P->d_counter, P->d_rcount, P->d_ord_cnt};
   k_setup<<<(P->nrows + 31) / 32, 32, 0, s>>>(P->d_inst, P->d_beams, P->nbeams, P->d_rows, P->nrows,
                                                  P->d_row_items, P->target_cand, clr);
   CHECK_LAUNCH();
@@ -772,10 +782,12 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   k_item_rows<<<(P->nrows + 127) / 128, 128, 0, s>>>(P->d_row_item_base, P->nrows, P->d_item_row);
   CHECK_LAUNCH();
   k_count<<<P->grid_items, kEvalThreads, 0, s>>>(P->d_inst, P->d_rows, slice_tab(P), P->d_row_item_base, P->nrows,
-                                                 n_items, P->d_item_cand, P->d_item_row);
+                                                 n_items, P->d_item_cand, P->d_item_row, P->d_ord_cnt,
+                                                 P->d_item_crank, P->target_cand);
   CHECK_LAUNCH();
   TRY(scan_launch(P->d_item_cand, n_items, 0, P->d_scan, P->d_item_off, s, P->n_items));
-  k_tile_map<<<1024, 256, 0, s>>>(P->d_item_off, n_items, P->d_item_row, P->d_tile_item, P->d_tile_row);
+  k_tile_map<<<1024, 256, 0, s>>>(P->d_item_off, n_items, P->d_item_row, P->d_tile_item, P->d_tile_row,
+                                 P->d_ord_cnt, P->d_item_crank, P->d_item_ord);
   CHECK_LAUNCH();
   if (fork) CU(cudaStreamWaitEvent(s, P->ev_join, 0));
   TRY(record(ev, 3, s));
@@ -796,6 +808,7 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   ep.row_max = P->d_row_max;
   ep.row_cand = P->d_row_cand;
   ep.item_counter = P->d_counter;
+  ep.item_ord = P->d_item_ord;
   ep.tau = (float)P->opts.rel_threshold;
   ep.inv_tau_m = ep.tau > 0.0f ? (1.0f - kRefineDelta) / ep.tau : std::numeric_limits<float>::infinity();
   ep.tile_meta = P->d_tile_meta;

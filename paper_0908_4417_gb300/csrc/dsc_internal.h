@@ -33,6 +33,7 @@ struct StepClear {
   int* mcount;                     // nrows
   int* counter;                    // 4
   unsigned long long* rcount;      // 4
+  int* ord_cnt;                    // kOrderClasses
 };
 
 // One geometry of a launch.
@@ -128,6 +129,9 @@ struct EvalParams {
   unsigned* row_max;               // float bits, atomicMax
   long long* row_cand;             // candidates inside the cutoff per row (atomic add)
   int* item_counter;               // persistent-kernel work queue head
+  // the queue hands out the items largest first (its tail holds the small
+  // ones), in this order (k_tile_map); null: index order
+  const int* item_ord;
   // the count of each tile taken during the evaluation: an item takes the
   // running row maximum at its start as a lower bound L of the final one;
   // per tile, the values at or above the kept bound L gives, and the lanes
@@ -154,6 +158,17 @@ struct OutSlot {
                                // maximum; near-threshold pairs past the list's capacity (decided in FP32);
                                // compaction tiles whose values the count pass read
 };
+
+// size classes of the work items for the evaluation's queue order, the
+// largest first: class 0 holds items of at least 15/8 of the target size,
+// class 15 those below 1/8 of it
+constexpr int kOrderClasses = 16;
+constexpr int kOrderRankBits = 27;    // an item's class and rank in one int (fewer than 2^27 items)
+__host__ __device__ __forceinline__ int order_class(long long n, int target_cand) {
+  const long long unit = target_cand >= 8 ? target_cand / 8 : 1;
+  const long long q = n / unit;
+  return kOrderClasses - 1 - (int)(q < kOrderClasses - 1 ? q : kOrderClasses - 1);
+}
 
 constexpr int kTilePer = 4;                       // candidates per thread of the compaction
 // candidates per compaction tile; every work item is padded to a whole

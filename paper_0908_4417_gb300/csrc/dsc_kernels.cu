@@ -88,8 +88,11 @@ __global__ void k_setup(const DInst* __restrict__ inst, const DBeam* __restrict_
     clr.row_max[r] = 0u;
     clr.row_cand[r] = 0;
     clr.mcount[r] = 0;
-    if (r == 0)
+    if (r == 0) {
       for (int k = 0; k < 4; ++k) { clr.counter[k] = 0; clr.rcount[k] = 0ull; }
+      if (clr.ord_cnt)
+        for (int k = 0; k < kOrderClasses; ++k) clr.ord_cnt[k] = 0;
+    }
   }
   int lo = 0, hi = nbeams - 1;
   while (lo < hi) {
@@ -956,7 +959,8 @@ __global__ void k_item_rows(const long long* __restrict__ row_item_base, int nro
 __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict__ inst, const DRow* __restrict__ rows,
                                                         SliceTab T, const long long* __restrict__ row_item_base,
                                                         int nrows, const long long* __restrict__ n_items,
-                                                        int* item_cand, const int* __restrict__ item_row) {
+                                                        int* item_cand, const int* __restrict__ item_row,
+                                                        int* ord_cnt, int* item_crank, int target_cand) {
   const long long ni = *n_items;
   const int lane = threadIdx.x & 31, half = lane >> 4, sub = lane & 15;
   // a half-warp per item, so that two items' dependent loads are in flight
@@ -985,8 +989,16 @@ __global__ void __launch_bounds__(kEvalThreads) k_count(const DInst* __restrict_
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);   // within the half
     // items are padded to whole compaction tiles (the evaluation writes
-    // whole tiles; padding slots hold -1, never kept)
-    if (sub == 0 && item < ni) item_cand[item] = (cnt + kTile - 1) & ~(kTile - 1);
+    // whole tiles; padding slots hold -1, never kept); each takes a rank in
+    // its size class for the evaluation's queue order (k_tile_map)
+    if (sub == 0 && item < ni) {
+      const int n = (cnt + kTile - 1) & ~(kTile - 1);
+      item_cand[item] = n;
+      if (item_crank) {
+        const int c = order_class(n, target_cand);
+        item_crank[item] = (c << kOrderRankBits) | atomicAdd(ord_cnt + c, 1);
+      }
+    }
   }
 }
 
@@ -1307,8 +1319,11 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_EVAL_MINBLOCKS) k_eval(EvalP
   for (;;) {
     if (threadIdx.x == 0) {
       long long it = atomicAdd(p.item_counter, 1);
+      if (it < ni) {
+        if (p.item_ord) it = p.item_ord[it];
+        sm.row = p.item_row[it];
+      }
       sm.item = it;
-      if (it < ni) sm.row = p.item_row[it];
     }
     __syncthreads();
     const long long item = sm.item;
@@ -1711,13 +1726,34 @@ __device__ __forceinline__ void tile_decide(const CompactParams& p, long long p0
 }
 
 // the item and row of every tile, from the work decomposition alone (it
-// runs before the evaluation); one warp per item, a tile per lane
+// runs before the evaluation), and the evaluation queue's order of the items
+// (item_ord: the size classes from the largest, each item at its class's
+// first position plus its rank in the class, from k_count; none when null);
+// one warp per item, a tile per lane
 __global__ void k_tile_map(const long long* __restrict__ item_off, const long long* __restrict__ n_items_p,
-                           const int* __restrict__ item_row, int* tile_item, int* tile_row) {
+                           const int* __restrict__ item_row, int* tile_item, int* tile_row,
+                           const int* __restrict__ ord_cnt, const int* __restrict__ item_crank, int* item_ord) {
   const long long ni = *n_items_p;
   const int lane = threadIdx.x & 31;
+  // the classes' first positions: an exclusive scan of the class counts
+  int pre = 0;
+  if (item_ord) {
+    const int v = lane < kOrderClasses ? ord_cnt[lane] : 0;
+    pre = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += x;
+    }
+    pre -= v;
+  }
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < ni; i += nw) {
+    if (item_ord) {
+      const int cr = item_crank[i];
+      const int first = __shfl_sync(0xffffffffu, pre, cr >> kOrderRankBits);
+      if (lane == 0) item_ord[first + (cr & ((1 << kOrderRankBits) - 1))] = (int)i;
+    }
     const long long a = item_off[i] / kTile, b = item_off[i + 1] / kTile;
     const int r = item_row[i];
     for (long long t = a + lane; t < b; t += 32) {
@@ -1791,7 +1827,8 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_write(C
   TileKeep K[kTilesPerWarp];
 #pragma unroll
   for (int u = 0; u < kTilesPerWarp; ++u) {
-    if (t0 + u < n_tiles && (u == 0 ? o1 > o0 : o2 > o1)) tile_load<true>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
+    if (t0 + u < n_tiles && (u == 0 ? o1 > o0 : o2 > o1))
+      tile_load<true>(p, (t0 + u) * kTile + (long long)lane * kTilePer, K[u]);
     else K[u] = TileKeep{};                             // not read: defined on every path, so K stays in registers
   }
 #pragma unroll

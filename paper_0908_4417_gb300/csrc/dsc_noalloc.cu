@@ -28,10 +28,11 @@ namespace dsc {
 __global__ void k_setup(const DInst*, const DBeam*, int, DRow*, int, int*, int, StepClear);
 __global__ void k_siddon(const DInst*, const DRow*, int, float*, int);
 __global__ void k_trilinear_table(const DInst*, const DRow*, int, float*, int);
-__global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*);
+__global__ void k_count(const DInst*, const DRow*, SliceTab, const long long*, int, const long long*, int*, const int*,
+                        int*, int*, int);
 __global__ void k_slices(const DInst*, DRow*, int, int*, int*, int, int*);
 __global__ void k_item_rows(const long long*, int, int*);
-__global__ void k_tile_map(const long long*, const long long*, const int*, int*, int*);
+__global__ void k_tile_map(const long long*, const long long*, const int*, int*, int*, const int*, const int*, int*);
 __global__ void k_row_bound(const DInst*, const DRow*, int, const float*, int, SliceTab, unsigned*);
 __global__ void k_eval(EvalParams);
 __global__ void k_tile_count(CompactParams, int*);
@@ -319,7 +320,7 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   k_item_rows<<<(nrows + 127) / 128, 128, 0, s>>>(d_rib, nrows, d_item_row);
   NA_LAUNCH();
   k_count<<<grid_items, kEvalThreads, 0, s>>>(d_inst, d_rows, slices, d_rib, nrows, n_items_dev, d_item_cand,
-                                              d_item_row);
+                                              d_item_row, nullptr, nullptr, target_cand);
   NA_LAUNCH();
   st = na_scan(d_item_cand, n_items_dev, 0, d_scan, d_item_off, s, n_items);
   if (st != DSC_OK) return st;
@@ -401,7 +402,8 @@ extern "C" dsc_status dsc_compute_dij_noalloc(const dsc_grid_desc* grid, const f
   cp.cap_u = cap_u;
   cp.nrows = nrows;
   cp.inv_tau_m = cp.tau > 0.0f ? (1.0f - kRefineDelta) / cp.tau : std::numeric_limits<float>::infinity();
-  k_tile_map<<<1024, 256, 0, s>>>(d_item_off, n_items_dev, d_item_row, d_tile_item, d_tile_row);
+  k_tile_map<<<1024, 256, 0, s>>>(d_item_off, n_items_dev, d_item_row, d_tile_item, d_tile_row, nullptr, nullptr,
+                                 nullptr);
   NA_LAUNCH();
   // kept count first, so the capacity is checked before any output is touched
   const unsigned tiles = compact_blocks(n_tiles);
