@@ -53,9 +53,9 @@ __global__ void k_dose_finish(const unsigned long long*, long long, const int*, 
 __global__ void k_beamlet_dot(const long long*, const long long*, const int*, const void*, int, const DRow*, int,
                               const float*, const float*, int, float*);
 __global__ void k_tile_write(CompactParams, const long long*);
-__global__ void k_row_ptr(const long long*, const long long*, const long long*, const long long*, long long, int, int,
-                          long long, int, int, const OutSlot*);
-__global__ void k_copy_stats(const unsigned*, const long long*, int, const unsigned long long*, int, const OutSlot*);
+__global__ void k_finish(const long long*, const long long*, const long long*, const long long*, long long,
+                         const long long*, int, const unsigned*, const long long*, int, const unsigned long long*, int,
+                         const OutSlot*);
 __global__ void k_scan_partial(const int*, const long long*, long long, long long*);
 __global__ void k_scan_blocks(long long*);
 __global__ void k_scan_final(const int*, const long long*, long long, const long long*, long long*);
@@ -221,6 +221,7 @@ struct Plan {
   std::vector<DInst> h_inst;
   std::vector<DBeam> h_beams;
   std::vector<long long> rp_off;     // per instance offset into the row_ptr output
+  long long* d_inst_rp = nullptr;    // rp_off on the device, and rp_total
   long long rp_total = 0;
   // device scratch
   DInst* d_inst = nullptr;
@@ -288,7 +289,7 @@ struct Plan {
     free_scratch();
     void* ps[] = {d_inst, d_beams, d_rows, d_row_items, d_slice_pre, d_slice_lo, d_row_item_base, d_tables, d_row_max,
                   d_row_cand, d_scan,
-                  d_counter, d_slot, d_rcount, d_mcount, d_mslot, d_ovf_rows, d_row_max64};
+                  d_counter, d_slot, d_rcount, d_mcount, d_mslot, d_ovf_rows, d_row_max64, d_inst_rp};
     release_after(last_done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
     if (last_done) cudaEventDestroy(last_done);
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -594,6 +595,13 @@ static dsc_status plan_build(dsc_geometry* const* geoms, int n, const dsc_comput
   if (P->nrows == 0) return fail(DSC_E_STATE, "no beams");
   P->stride = (P->stride + 3) & ~3;
   TRY(dalloc(&P->d_inst, n, s));
+  TRY(dalloc(&P->d_inst_rp, n + 1, s));
+  {
+    std::vector<long long> rp(P->rp_off);
+    rp.push_back(P->rp_total);
+    // pageable source: staged before the call returns
+    CU(cudaMemcpyAsync(P->d_inst_rp, rp.data(), sizeof(long long) * rp.size(), cudaMemcpyHostToDevice, s));
+  }
   TRY(dalloc(&P->d_beams, P->nbeams, s));
   TRY(dalloc(&P->d_rows, P->nrows, s));
   TRY(dalloc(&P->d_row_items, P->nrows, s));
@@ -857,15 +865,11 @@ static dsc_status enqueue(Plan* P, cudaStream_t s, EventSet* ev, int* nk) {
   k_tile_write<<<tiles, kEvalThreads, 0, s>>>(cp, P->d_tile_off);
   CHECK_LAUNCH();
   TRY(record(ev, 6, s));
-  for (int k = 0; k < P->ninst; ++k) {
-    const DInst& I = P->h_inst[k];
-    k_row_ptr<<<(I.nrows + 1 + 255) / 256, 256, 0, s>>>(P->d_row_item_base, P->d_item_off, P->d_tile_off, n_items,
-                                                        P->n_cand, I.row_base, I.nrows, P->rp_off[k], k,
-                                                        k == P->ninst - 1, P->d_slot);
-    CHECK_LAUNCH();
-  }
-  k_copy_stats<<<(P->nrows + 255) / 256, 256, 0, s>>>(P->d_row_max, P->d_row_cand, P->nrows, P->d_rcount, P->cap_u,
-                                                     P->d_slot);
+  // row pointers of every instance, row statistics and counts, one launch
+  k_finish<<<(unsigned)((P->rp_total + 255) / 256), 256, 0, s>>>(P->d_row_item_base, P->d_item_off, P->d_tile_off,
+                                                                 n_items, P->n_cand, P->d_inst_rp, P->ninst,
+                                                                 P->d_row_max, P->d_row_cand, P->nrows, P->d_rcount,
+                                                                 P->cap_u, P->d_slot);
   CHECK_LAUNCH();
   TRY(record(ev, 7, s));
   if (nk) *nk = (int)(g_launches.load() - k0);

@@ -1873,41 +1873,67 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_write(C
   }
 }
 
+// the kept count before work item i: the output offset of its first tile, or
+// the total when it starts past the end
+__device__ __forceinline__ long long kept_before_item(const long long* __restrict__ item_off,
+                                                      const long long* __restrict__ tile_off, long long ni,
+                                                      long long n_cand, long long total, long long i) {
+  return (i >= ni || item_off[i] >= n_cand) ? total : tile_off[item_off[i] / kTile];
+}
+
 // CSR row pointers of one instance (rows [row_base, row_base + nrows)),
 // relative to the instance's first output slot, which goes to inst_begin.
-// Row r starts at item row_item_base[r]; the kept count before it is the
-// output offset of that item's first tile, or the total when the item starts
-// past the end.
+// Row r starts at item row_item_base[r].
 __global__ void k_row_ptr(const long long* __restrict__ row_item_base, const long long* __restrict__ item_off,
                           const long long* __restrict__ tile_off, const long long* __restrict__ n_items_p,
                           long long n_cand, int row_base, int nrows, long long rp_off, int inst, int last,
                           const OutSlot* __restrict__ slot) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const long long ni = *n_items_p, total = tile_off[n_cand / kTile];
-  auto kept_before = [&](long long i) -> long long {
-    return (i >= ni || item_off[i] >= n_cand) ? total : tile_off[item_off[i] / kTile];
-  };
-  const long long b = kept_before(row_item_base[row_base]);
-  if (r <= nrows) slot->row_ptr[rp_off + r] = kept_before(row_item_base[row_base + r]) - b;
+  const long long b = kept_before_item(item_off, tile_off, ni, n_cand, total, row_item_base[row_base]);
+  if (r <= nrows)
+    slot->row_ptr[rp_off + r] =
+        kept_before_item(item_off, tile_off, ni, n_cand, total, row_item_base[row_base + r]) - b;
   if (r == 0) {
     slot->inst_begin[inst] = b;
     if (last) slot->inst_begin[inst + 1] = total;
   }
 }
 
-// per-row statistics into the result; refine = {pairs listed near a
-// threshold (within the list's capacity), near-maximum candidates, listed
-// pairs past the capacity (their decision stayed FP32), tiles counted from
-// their values}
-__global__ void k_copy_stats(const unsigned* __restrict__ row_max, const long long* __restrict__ row_cand, int nrows,
-                             const unsigned long long* __restrict__ rcount, int cap_u,
-                             const OutSlot* __restrict__ slot) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < nrows) {
-    slot->row_max[r] = row_max[r];
-    slot->row_cand[r] = row_cand[r];
+// the end of a computation, one thread per entry of the launch's row
+// pointers (all instances) and per row: each instance's row pointers, as
+// k_row_ptr forms them (instance k holds entries [inst_rp[k], inst_rp[k + 1]),
+// nrows_k + 1 of them, and its first row is inst_rp[k] - k); the per-row
+// statistics; and refine = {pairs listed near a threshold (within the list's
+// capacity), near-maximum candidates, listed pairs past the capacity (their
+// decision stayed FP32), tiles counted from their values}
+__global__ void k_finish(const long long* __restrict__ row_item_base, const long long* __restrict__ item_off,
+                         const long long* __restrict__ tile_off, const long long* __restrict__ n_items_p,
+                         long long n_cand, const long long* __restrict__ inst_rp, int ninst,
+                         const unsigned* __restrict__ row_max, const long long* __restrict__ row_cand, int nrows,
+                         const unsigned long long* __restrict__ rcount, int cap_u, const OutSlot* __restrict__ slot) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < inst_rp[ninst]) {
+    int lo = 0, hi = ninst - 1;                         // the instance: inst_rp[k] <= t < inst_rp[k + 1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (inst_rp[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const long long ni = *n_items_p, total = tile_off[n_cand / kTile];
+    const long long r = t - inst_rp[lo];
+    const long long row_base = inst_rp[lo] - lo;
+    const long long b = kept_before_item(item_off, tile_off, ni, n_cand, total, row_item_base[row_base]);
+    slot->row_ptr[t] = kept_before_item(item_off, tile_off, ni, n_cand, total, row_item_base[row_base + r]) - b;
+    if (r == 0) {
+      slot->inst_begin[lo] = b;
+      if (lo == ninst - 1) slot->inst_begin[ninst] = total;
+    }
   }
-  if (r == 0 && slot->refine) {
+  if (t < nrows) {
+    slot->row_max[t] = row_max[t];
+    slot->row_cand[t] = row_cand[t];
+  }
+  if (t == 0 && slot->refine) {
     const unsigned long long cap = (unsigned long long)cap_u, n0 = rcount[0];
     slot->refine[0] = n0 < cap ? n0 : cap;
     slot->refine[1] = rcount[1];
