@@ -374,7 +374,35 @@ def run_ours(args):
 
         e2e_s, wall_s = end_to_end(plain)
         # the same with BF16 storage (per-beam scale): 6 instead of 8 bytes per kept entry read back
-        e2e16_s, wall16_s = end_to_end(dsc.compute_opts(w.tau, dsc.DSC_VALUE_BF16, w.h_frac, 0))
+        opts16 = dsc.compute_opts(w.tau, dsc.DSC_VALUE_BF16, w.h_frac, 0)
+        e2e16_s, wall16_s = end_to_end(opts16)
+
+        def copies_alone(opts_e, reps=3):
+            """A step's own read-back and upload, each alone on an idle GPU (the
+            same pinned buffers and calls as the pipelined loop; shortest of
+            reps): the bound of the pipelined end-to-end step."""
+            r = dsc.dsc_compute_dij(g, opts_e, sp)
+            dsc.dsc_result_wait(r)
+            down, up = [], []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(cstream)
+                dsc.dsc_copy_csr_to_host(r, h_rp.data_ptr(), h_col.data_ptr(), h_val.data_ptr(), h_sc.data_ptr(),
+                                         csp)
+                b.record(cstream)
+                cstream.synchronize()
+                down.append(a.elapsed_time(b))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                dsc.dsc_upload_density(g, host_rho.data_ptr(), False, sp)
+                b.record(stream)
+                stream.synchronize()
+                up.append(a.elapsed_time(b))
+            dsc.dsc_release_result(r)
+            return min(down), min(up)
+
+        copy_ms = copies_alone(plain)
+        copy16_ms = copies_alone(opts16)
 
         # ---- the ALU denominators measured on this GPU (outside the timed region) ----
         pclk = Clocks(gpu_id(props, local if world > 1 else 0))
@@ -409,14 +437,18 @@ def run_ours(args):
     d2h = int((nrows + 1) * 8 + nnz * 4 + nnz * vsize + nbeams * 4)
     d2h16 = int((nrows + 1) * 8 + nnz * 4 + nnz * 2 + nbeams * 4)
 
-    def link_bound(d2h_bytes, e2e_ms):
+    def link_bound(d2h_bytes, e2e_ms, copies):
         # a step's result down and (pipelined, the other direction) the next
-        # step's density up: the slower of the two at the measured rates
-        ms = 1e3 * max(d2h_bytes / (link["d2h_gbs"] * 1e9), h2d / (link["h2d_gbs"] * 1e9))
-        return {"d2h_gbs": link["d2h_gbs"], "h2d_gbs": link["h2d_gbs"], "bound_ms_per_step": ms,
-                "frac_of_bound": ms / e2e_ms,
-                "basis": "pinned cudaMemcpyAsync of the step's CSR size each way, shortest of 3 "
-                         "(dsc_measure_host_link); bound = max(d2h bytes / d2h rate, h2d bytes / h2d rate)"}
+        # step's density up: the slower of the two, each timed alone with the
+        # step's own buffers and calls
+        down_ms, up_ms = copies
+        ms = max(down_ms, up_ms)
+        return {"bound_ms_per_step": ms, "frac_of_bound": ms / e2e_ms,
+                "d2h_gbs_of_read_back": d2h_bytes / (down_ms * 1e6), "h2d_gbs_of_upload": h2d / (up_ms * 1e6),
+                "link_gbs_one_copy": {"d2h": link["d2h_gbs"], "h2d": link["h2d_gbs"]},
+                "basis": "the step's CSR read-back (dsc_copy_csr_to_host) and density upload, each alone on an "
+                         "idle GPU with the same pinned buffers, shortest of 3; bound = the slower of the two. "
+                         "link_gbs_one_copy: one pinned copy of the CSR's size each way (dsc_measure_host_link)"}
     sms = props.multi_processor_count
     hbm_meas = None
     try:
@@ -465,12 +497,12 @@ def run_ours(args):
         "e2e": {"value": whole_job_rate(pairs, e2e_steps, world, e2e_s), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps,
                 "host_wall_ms_per_step": 1e3 * wall_s / e2e_steps,
-                "host_link": link_bound(d2h, 1e3 * e2e_s / e2e_steps)},
+                "host_link": link_bound(d2h, 1e3 * e2e_s / e2e_steps, copy_ms)},
         "e2e_bf16": {"value": whole_job_rate(pairs, e2e_steps, world, e2e16_s), "unit": "pairs/s",
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h16,
                      "ms_per_step": 1e3 * e2e16_s / e2e_steps, "host_wall_ms_per_step": 1e3 * wall16_s / e2e_steps,
                      "value_dtype": "bf16 with per-beam scale",
-                     "host_link": link_bound(d2h16, 1e3 * e2e16_s / e2e_steps)},
+                     "host_link": link_bound(d2h16, 1e3 * e2e16_s / e2e_steps, copy16_ms)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": KEVAL_DRAM_BYTES_PER_PAIR * pairs,
