@@ -179,6 +179,12 @@ def test_prostate_full_size_sampled_rows(dsc):
     assert np.allclose(rm[rows], orc.row_max, rtol=TOL)
     assert np.all(np.abs(rc[rows] - orc.row_cand) <= 64)
     assert rc.sum() == csr.pairs
+    # every row maximum is the evaluation's own, bit for bit: the largest kept
+    # value of its row (the maximum is always kept and never rewritten), so the
+    # lower bounds that seed the maxima before the evaluation stay below them
+    nz = np.diff(csr.row_ptr) > 0
+    assert nz.sum() > 0.9 * w.nrows
+    assert np.array_equal(rm[nz], np.maximum.reduceat(csr.val, csr.row_ptr[:-1][nz]))
     cleanup(dsc, res, g)
 
 
