@@ -357,7 +357,7 @@ dsc_status dsc_get_server_timing(dsc_result* res, int32_t* slot, double* start_m
  * Working memory is a fixed array of 80 MiB inside the library's device
  * image, present on every GPU that loads the library until the process
  * exits.  A request whose working set (set-up, depth tables, line tables,
- * work items, 8 bytes per candidate pair and 36 bytes per tile of 128
+ * work items, 8 bytes per candidate pair and 32 bytes per tile of 128
  * candidates) exceeds it fails with DSC_E_INVAL and says so in
  * dsc_last_error(); so does an output capacity below the kept count
  * (nothing is written to the outputs then).  The first call on a device
