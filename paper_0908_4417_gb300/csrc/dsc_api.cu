@@ -46,6 +46,7 @@ __global__ void k_eval(EvalParams);
 __global__ void k_beam_scale(const DBeam*, int, const unsigned*, const OutSlot*);
 __global__ void k_tile_count(CompactParams, int*);
 __global__ void k_lut_pairs(const float4*, int, int, float4*);
+__global__ void k_out_init(OutSlot*, OutSlot, int, int, int);
 __global__ void k_dose_scale(const unsigned*, const float*, int, int*);
 __global__ void k_dose_scatter(const long long*, const long long*, const int*, const void*, int, const DRow*, int,
                                const float*, const float*, int, const int*, unsigned long long*);
@@ -166,10 +167,12 @@ struct OutBufs {
   int device = 0;
   cudaEvent_t done = nullptr;        // end of the computation that writes these buffers
   OutSlot slot{};                    // row_ptr, col, val, beam_scale, row_max, row_cand, inst_begin, status
+  int ninst = 0;                     // instances of the launch (entries of slot.summary: 1 + 2 ninst)
   long long n_tiles = 0;             // compaction tiles of the launch
   ~OutBufs() {
+    // the status word lives in the summary's first entry
     void* ps[] = {slot.row_ptr, slot.col, slot.val, slot.beam_scale, slot.row_max, slot.row_cand, slot.inst_begin,
-                  slot.status, slot.refine};
+                  slot.summary, slot.refine};
     release_after(done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
     if (done) cudaEventDestroy(done);
   }
@@ -192,7 +195,7 @@ struct dsc_result {
   long long ncols = 0;
   int value_dtype = 0;
   cudaEvent_t done = nullptr;
-  bool have_counts = false;
+  bool have_counts = false, have_pairs = false;
   long long out_begin = 0, nnz = 0, pairs = 0;
   // served results: the server slot and the device interval of the launch
   // that computed it (ms after the server's creation; -1: not served)
@@ -898,13 +901,11 @@ static dsc_status alloc_outputs(Plan* P, cudaStream_t s, std::shared_ptr<OutBufs
   TRY(dalloc(&q.inst_begin, P->ninst + 1, s));
   TRY(dalloc(&q.refine, 4, s));
   O->n_tiles = P->n_tiles;
-  TRY(dalloc(&q.status, 1, s));
-  CU(cudaMemsetAsync(q.status, 0, sizeof(int), s));
-  if (P->opts.value_dtype != DSC_VALUE_BF16) {
-    // FP32 values carry no scale (pageable source: staged before the call returns)
-    std::vector<float> ones(P->nbeams, 1.0f);
-    CU(cudaMemcpyAsync(q.beam_scale, ones.data(), sizeof(float) * P->nbeams, cudaMemcpyHostToDevice, s));
-  }
+  O->ninst = P->ninst;
+  TRY(dalloc(&q.summary, 1 + 2 * (size_t)P->ninst, s));
+  q.status = reinterpret_cast<int*>(q.summary);
+  // cleared (and, for FP32 values, which carry no scale, the beam scales set
+  // to 1) by k_out_init at the head of the computation
   return DSC_OK;
 }
 
@@ -913,7 +914,8 @@ static dsc_status run_plan(const std::shared_ptr<Plan>& P, cudaStream_t s, bool 
   P->last_stream = s;
   std::shared_ptr<OutBufs> O;
   TRY(alloc_outputs(P.get(), s, O));
-  CU(cudaMemcpyAsync(P->d_slot, &O->slot, sizeof(OutSlot), cudaMemcpyHostToDevice, s));
+  k_out_init<<<1, 256, 0, s>>>(P->d_slot, O->slot, P->ninst, P->nbeams, P->opts.value_dtype != DSC_VALUE_BF16);
+  CHECK_LAUNCH();
   std::shared_ptr<EventSet> ev;
   if (timing) {
     ev = std::make_shared<EventSet>();
@@ -1098,13 +1100,17 @@ extern "C" dsc_status dsc_autotune(dsc_geometry* const* geoms, int32_t n, const 
 // ---------------------------------------------------------------------------
 // results
 // ---------------------------------------------------------------------------
+static dsc_status status_error(int st) {
+  if (st & kStatusIndex) return fail(DSC_E_CUDA, "a kernel found an index out of range (status %d); the result is invalid", st);
+  if (st) return fail(DSC_E_TIMEOUT, "a bounded device wait expired (status %d); the result is invalid", st);
+  return DSC_OK;
+}
+
 static dsc_status check_status(dsc_result* r) {
   int st = 0;
   CU(cudaEventSynchronize(r->done));
   CU(cudaMemcpy(&st, r->out->slot.status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (st & kStatusIndex) return fail(DSC_E_CUDA, "a kernel found an index out of range (status %d); the result is invalid", st);
-  if (st) return fail(DSC_E_TIMEOUT, "a bounded device wait expired (status %d); the result is invalid", st);
-  return DSC_OK;
+  return status_error(st);
 }
 
 extern "C" dsc_status dsc_result_wait(dsc_result* r) {
@@ -1112,20 +1118,38 @@ extern "C" dsc_status dsc_result_wait(dsc_result* r) {
   return check_status(r);
 }
 
+// the result's status, first output entry and kept count: one copy of the
+// summary's head (the status word, then two entries per instance)
 static dsc_status fetch_counts(dsc_result* r) {
   if (r->have_counts) return DSC_OK;
-  TRY(check_status(r));
-  long long be[2];
-  CU(cudaMemcpy(&be[0], r->out->slot.inst_begin + r->inst, sizeof(long long), cudaMemcpyDeviceToHost));
-  CU(cudaMemcpy(&be[1], r->out->slot.row_ptr + r->rp_off + r->nrows, sizeof(long long), cudaMemcpyDeviceToHost));
+  CU(cudaEventSynchronize(r->done));
+  const size_t n = 3 + 2 * (size_t)r->inst;
+  long long sm[3 + 2 * 64];
+  std::vector<long long> big;
+  long long* h = sm;
+  if (n > sizeof(sm) / sizeof(sm[0])) {
+    big.resize(n);
+    h = big.data();
+  }
+  CU(cudaMemcpy(h, r->out->slot.summary, sizeof(long long) * n, cudaMemcpyDeviceToHost));
+  TRY(status_error((int)(h[0] & 0xffffffffll)));
+  r->out_begin = h[1 + 2 * r->inst];
+  r->nnz = h[2 + 2 * r->inst];
+  r->have_counts = true;
+  return DSC_OK;
+}
+
+// candidate pairs of the result's rows (read when asked for: the read-back
+// does not need them)
+static dsc_status fetch_pairs(dsc_result* r) {
+  if (r->have_pairs) return DSC_OK;
+  TRY(fetch_counts(r));
   std::vector<long long> rc(r->nrows);
   CU(cudaMemcpy(rc.data(), r->out->slot.row_cand + r->row_base, sizeof(long long) * r->nrows, cudaMemcpyDeviceToHost));
-  r->out_begin = be[0];
-  r->nnz = be[1];
   long long p = 0;
   for (auto v : rc) p += v;
   r->pairs = p;
-  r->have_counts = true;
+  r->have_pairs = true;
   return DSC_OK;
 }
 
@@ -1133,7 +1157,7 @@ static size_t val_size(int dt) { return dt == DSC_VALUE_BF16 ? 2 : 4; }
 
 extern "C" dsc_status dsc_get_csr(dsc_result* r, int32_t copy_to_host, dsc_csr_view* v) {
   if (!r || !v) return fail(DSC_E_INVAL, "null argument");
-  TRY(fetch_counts(r));
+  TRY(fetch_pairs(r));
   const OutSlot& q = r->out->slot;
   v->nrows = r->nrows;
   v->ncols = r->ncols;
@@ -1399,7 +1423,7 @@ static size_t estimate_footprint(const dsc_geometry& g, const dsc_compute_opts& 
   return (size_t)bytes;
 }
 
-static dsc_status fetch_counts(dsc_result* r);
+static dsc_status fetch_pairs(dsc_result* r);
 
 // options compared field by field (the struct has padding bytes)
 static bool same_opts(const dsc_compute_opts& a, const dsc_compute_opts& b) {
@@ -1424,7 +1448,7 @@ static void srv_finish_slot(dsc_server* S, SrvSlot& sl) {
     q->state = 2;
     S->lat_ms.push_back(1e3 * (t - q->t_submit));
     S->n_done++;
-    if (q->result && fetch_counts(q->result) == DSC_OK) S->pairs_done += q->result->pairs;
+    if (q->result && fetch_pairs(q->result) == DSC_OK) S->pairs_done += q->result->pairs;
   }
   S->used -= sl.footprint;
   if (sl.plan) {

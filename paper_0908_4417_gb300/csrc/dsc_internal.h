@@ -154,6 +154,9 @@ struct OutSlot {
   long long* row_cand;     // per row
   long long* inst_begin;   // per instance: first output slot; [ninst] = total
   int* status;             // nonzero: kStatusWait (a bounded device wait expired) or kStatusIndex
+  long long* summary;      // null, or [0]: the status word (status points at it), then per instance k
+                           // [1 + 2k] its first output entry and [2 + 2k] its kept count (k_finish), so
+                           // that the host reads all it needs to size a read-back in one copy
   unsigned long long* refine;  // [4] pairs listed for the FP64 re-evaluation: near a threshold, near a row
                                // maximum; near-threshold pairs past the list's capacity (decided in FP32);
                                // compaction tiles whose values the count pass read

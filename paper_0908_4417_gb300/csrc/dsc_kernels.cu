@@ -1900,6 +1900,22 @@ __global__ void k_row_ptr(const long long* __restrict__ row_item_base, const lon
   }
 }
 
+// the start of a computation: its output pointers into the plan's slot, the
+// status and the summary cleared and, for FP32 values, the per-beam scales
+// set to 1.  The pointers travel as the launch's argument, so the host
+// stages nothing (a copy from pageable host memory may wait on the stream).
+__global__ void k_out_init(OutSlot* __restrict__ d_slot, OutSlot q, int ninst, int nbeams, int unit_scale) {
+  const int t = threadIdx.x;
+  if (t == 0) *d_slot = q;
+  if (q.summary) {
+    for (int k = t; k < 1 + 2 * ninst; k += blockDim.x) q.summary[k] = 0;
+  } else if (t == 0) {
+    *q.status = 0;
+  }
+  if (unit_scale)
+    for (int b = t; b < nbeams; b += blockDim.x) q.beam_scale[b] = 1.0f;
+}
+
 // the end of a computation, one thread per entry of the launch's row
 // pointers (all instances) and per row: each instance's row pointers, as
 // k_row_ptr forms them (instance k holds entries [inst_rp[k], inst_rp[k + 1]),
@@ -1923,11 +1939,14 @@ __global__ void k_finish(const long long* __restrict__ row_item_base, const long
     const long long r = t - inst_rp[lo];
     const long long row_base = inst_rp[lo] - lo;
     const long long b = kept_before_item(item_off, tile_off, ni, n_cand, total, row_item_base[row_base]);
-    slot->row_ptr[t] = kept_before_item(item_off, tile_off, ni, n_cand, total, row_item_base[row_base + r]) - b;
+    const long long v = kept_before_item(item_off, tile_off, ni, n_cand, total, row_item_base[row_base + r]) - b;
+    slot->row_ptr[t] = v;
     if (r == 0) {
       slot->inst_begin[lo] = b;
       if (lo == ninst - 1) slot->inst_begin[ninst] = total;
+      if (slot->summary) slot->summary[1 + 2 * lo] = b;
     }
+    if (t == inst_rp[lo + 1] - 1 && slot->summary) slot->summary[2 + 2 * lo] = v;   // the last entry: the kept count
   }
   if (t < nrows) {
     slot->row_max[t] = row_max[t];
