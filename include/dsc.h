@@ -228,6 +228,16 @@ dsc_status dsc_get_csr(dsc_result* res, int32_t copy_to_host, dsc_csr_view* out)
  * row_ptr nrows+1, col nnz, val nnz * (4 or 2) bytes, beam_scale nbeams (may be NULL). */
 dsc_status dsc_copy_csr_to_host(dsc_result* res, int64_t* row_ptr, int32_t* col, void* val, float* beam_scale,
                                 void* stream);
+/* The same copies, queued on `stream` without waiting for them: the call
+ * waits on the host for the computation to finish (its counts size the
+ * copies), queues the copies and returns.  The host buffers hold the CSR once
+ * `stream` has passed the copies (synchronise it or an event recorded after
+ * the call); with pinned buffers the copies overlap other work, so the read-back
+ * of one result can be queued behind another's.  The result's device buffers
+ * are kept until the copies have run, also when the result is released before
+ * that.  Errors as for dsc_copy_csr_to_host. */
+dsc_status dsc_copy_csr_to_host_async(dsc_result* res, int64_t* row_ptr, int32_t* col, void* val, float* beam_scale,
+                                      void* stream);
 void dsc_release_result(dsc_result* res);
 
 /* --- products with the resident D_ij (no copy to the host) -------------- */

@@ -120,9 +120,11 @@ static cudaStream_t free_stream(int dev) {
   return s;
 }
 
-static void release_after(cudaEvent_t ev, int dev, void* const* ps, int n) {
+static void release_after(cudaEvent_t ev, int dev, void* const* ps, int n, const std::vector<cudaEvent_t>* also = nullptr) {
   cudaStream_t fs = free_stream(dev);
   if (ev) cudaStreamWaitEvent(fs, ev, 0);
+  if (also)
+    for (cudaEvent_t e : *also) cudaStreamWaitEvent(fs, e, 0);
   for (int i = 0; i < n; ++i)
     if (ps[i]) cudaFreeAsync(ps[i], fs);
 }
@@ -169,11 +171,16 @@ struct OutBufs {
   OutSlot slot{};                    // row_ptr, col, val, beam_scale, row_max, row_cand, inst_begin, status
   int ninst = 0;                     // instances of the launch (entries of slot.summary: 1 + 2 ninst)
   long long n_tiles = 0;             // compaction tiles of the launch
+  // ends of the asynchronous read-backs queued from these buffers: they are
+  // freed only after those too
+  std::mutex readers_mu;
+  std::vector<cudaEvent_t> readers;
   ~OutBufs() {
     // the status word lives in the summary's first entry
     void* ps[] = {slot.row_ptr, slot.col, slot.val, slot.beam_scale, slot.row_max, slot.row_cand, slot.inst_begin,
                   slot.summary, slot.refine};
-    release_after(done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])));
+    release_after(done, device, ps, (int)(sizeof(ps) / sizeof(ps[0])), &readers);
+    for (cudaEvent_t e : readers) cudaEventDestroy(e);
     if (done) cudaEventDestroy(done);
   }
 };
@@ -1188,10 +1195,10 @@ extern "C" dsc_status dsc_get_csr(dsc_result* r, int32_t copy_to_host, dsc_csr_v
   return DSC_OK;
 }
 
-extern "C" dsc_status dsc_copy_csr_to_host(dsc_result* r, int64_t* row_ptr, int32_t* col, void* val, float* beam_scale,
-                                           void* stream) {
+extern "C" dsc_status dsc_copy_csr_to_host_async(dsc_result* r, int64_t* row_ptr, int32_t* col, void* val,
+                                                 float* beam_scale, void* stream) {
   if (!r || !row_ptr || !col || !val) return fail(DSC_E_INVAL, "null argument");
-  TRY(fetch_counts(r));
+  TRY(fetch_counts(r));                                // the computation has finished: its counts size the copies
   cudaStream_t s = (cudaStream_t)stream;
   const OutSlot& q = r->out->slot;
   CU(cudaMemcpyAsync(row_ptr, q.row_ptr + r->rp_off, sizeof(long long) * (r->nrows + 1), cudaMemcpyDeviceToHost, s));
@@ -1202,7 +1209,23 @@ extern "C" dsc_status dsc_copy_csr_to_host(dsc_result* r, int64_t* row_ptr, int3
   }
   if (beam_scale)
     CU(cudaMemcpyAsync(beam_scale, q.beam_scale + r->beam_base, sizeof(float) * r->nbeams, cudaMemcpyDeviceToHost, s));
-  CU(cudaStreamSynchronize(s));
+  // the device buffers outlive these copies, also when the result is released first
+  cudaEvent_t e = nullptr;
+  CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaError_t err = cudaEventRecord(e, s);
+  if (err != cudaSuccess) {
+    cudaEventDestroy(e);
+    return fail(DSC_E_CUDA, "cudaEventRecord: %s", cudaGetErrorString(err));
+  }
+  std::lock_guard<std::mutex> lk(r->out->readers_mu);
+  r->out->readers.push_back(e);
+  return DSC_OK;
+}
+
+extern "C" dsc_status dsc_copy_csr_to_host(dsc_result* r, int64_t* row_ptr, int32_t* col, void* val, float* beam_scale,
+                                           void* stream) {
+  TRY(dsc_copy_csr_to_host_async(r, row_ptr, col, val, beam_scale, stream));
+  CU(cudaStreamSynchronize((cudaStream_t)stream));
   return DSC_OK;
 }
 

@@ -32,6 +32,7 @@ EXPORTS = [
     "dsc_status_str", "dsc_last_error", "dsc_abi_version", "dsc_launch_count",
     "dsc_create_geometry", "dsc_upload_density", "dsc_add_beam", "dsc_clear_beams", "dsc_destroy_geometry",
     "dsc_compute_dij", "dsc_compute_dij_batch", "dsc_result_wait", "dsc_get_csr", "dsc_copy_csr_to_host",
+    "dsc_copy_csr_to_host_async",
     "dsc_release_result", "dsc_get_beamlets", "dsc_get_depth_tables", "dsc_get_row_stats", "dsc_get_stage_times",
     "dsc_server_create", "dsc_server_submit", "dsc_server_poll", "dsc_server_stats", "dsc_server_destroy",
     "dsc_compute_dij_noalloc", "dsc_set_tuning", "dsc_get_tuning", "dsc_autotune", "dsc_dose", "dsc_beamlet_dot",
@@ -104,6 +105,7 @@ def lib():
             "dsc_result_wait": (C.c_int, [P]),
             "dsc_get_csr": (C.c_int, [P, I32, C.POINTER(CsrView)]),
             "dsc_copy_csr_to_host": (C.c_int, [P, P, P, P, P, P]),
+            "dsc_copy_csr_to_host_async": (C.c_int, [P, P, P, P, P, P]),
             "dsc_release_result": (None, [P]),
             "dsc_get_beamlets": (C.c_int, [P, P, I64]),
             "dsc_get_depth_tables": (C.c_int, [P, P, I64, C.POINTER(I32)]),
@@ -319,13 +321,22 @@ def dsc_get_csr(res, copy_to_host: bool = False) -> CsrView:
     return v
 
 
+def _host_ptr(a):
+    if a is None:
+        return None
+    return a if isinstance(a, int) else (a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+
+
 def dsc_copy_csr_to_host(res, row_ptr, col, val, beam_scale=None, stream=0):
     """Arguments are host buffers (numpy arrays or pinned torch tensors: pass data pointers as ints)."""
-    def ptr(a):
-        if a is None:
-            return None
-        return a if isinstance(a, int) else (a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
-    _check(lib().dsc_copy_csr_to_host(res, ptr(row_ptr), ptr(col), ptr(val), ptr(beam_scale), stream))
+    _check(lib().dsc_copy_csr_to_host(res, _host_ptr(row_ptr), _host_ptr(col), _host_ptr(val), _host_ptr(beam_scale),
+                                      stream))
+
+
+def dsc_copy_csr_to_host_async(res, row_ptr, col, val, beam_scale=None, stream=0):
+    """The copies queued on `stream` (returns before they run); buffers as for dsc_copy_csr_to_host."""
+    _check(lib().dsc_copy_csr_to_host_async(res, _host_ptr(row_ptr), _host_ptr(col), _host_ptr(val),
+                                            _host_ptr(beam_scale), stream))
 
 
 def dsc_release_result(res):

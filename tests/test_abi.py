@@ -62,6 +62,8 @@ def test_null_arguments_are_rejected(lib):
     a, b = C.c_int64(), C.c_int64()
     assert lib.dsc_get_refine_counts(None, C.byref(a), C.byref(b), C.byref(a)) == 1
     assert lib.dsc_get_tile_counts(None, C.byref(a), C.byref(b)) == 1
+    assert lib.dsc_copy_csr_to_host(None, None, None, None, None, None) == 1
+    assert lib.dsc_copy_csr_to_host_async(None, None, None, None, None, None) == 1
 
 
 def test_struct_layouts_match_header():

@@ -452,6 +452,48 @@ def test_repeat_is_bit_identical_and_graph_replay(dsc):
     dsc.dsc_destroy_geometry(g)
 
 
+def test_async_read_back_matches_and_outlives_release(dsc):
+    """dsc_copy_csr_to_host_async gives the blocking read-back's CSR, also
+    when the result is released before its copies run: the copies are held
+    behind a long fill on another stream, the result is released, and new
+    computations (another threshold, so other contents) allocate meanwhile;
+    the device buffers must be kept until the copies have run."""
+    import torch
+    w = P.slabs_128(value_dtype=P.VALUE_F32)
+    g = dsc.geometry_from_workload(w)
+    opts = dsc.compute_opts(w.tau, 0, w.h_frac)
+    ref = dsc.dsc_compute_dij(g, opts)
+    cref = dsc.HostCSR(ref)
+    dsc.dsc_release_result(ref)
+    r = dsc.dsc_compute_dij(g, opts)
+    v = dsc.dsc_get_csr(r, False)
+    nnz, nrows, nbeams = int(v.nnz), int(v.nrows), int(v.nbeams)
+    h_rp = torch.zeros(nrows + 1, dtype=torch.int64).pin_memory()
+    h_col = torch.zeros(nnz, dtype=torch.int32).pin_memory()
+    h_val = torch.zeros(nnz, dtype=torch.float32).pin_memory()
+    h_sc = torch.zeros(nbeams, dtype=torch.float32).pin_memory()
+    cs, other = torch.cuda.Stream(), torch.cuda.Stream()
+    big = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(other):
+        for k in range(32):                              # about 5 ms of writes
+            big.fill_(k)
+    hold = torch.cuda.Event()
+    hold.record(other)
+    cs.wait_event(hold)
+    dsc.dsc_copy_csr_to_host_async(r, h_rp, h_col, h_val, h_sc, cs.cuda_stream)
+    dsc.dsc_release_result(r)                            # before the copies have run
+    others = [dsc.dsc_compute_dij(g, dsc.compute_opts(0.0, 0, w.h_frac)) for _ in range(2)]
+    cs.synchronize()
+    assert np.array_equal(h_rp.numpy(), cref.row_ptr)
+    assert np.array_equal(h_col.numpy(), cref.col)
+    assert np.array_equal(h_val.numpy(), cref.val)
+    assert np.all(h_sc.numpy() == 1.0)                  # FP32 values carry no scale
+    for x in others:
+        dsc.dsc_release_result(x)
+    dsc.dsc_destroy_geometry(g)
+    torch.cuda.synchronize()
+
+
 def small_instances(n):
     out = []
     for k in range(n):
