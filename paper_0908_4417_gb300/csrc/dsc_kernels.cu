@@ -1148,9 +1148,10 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 A
   // radiological depth at O' (Section 2.2): linear interpolation of the
   // table; s = t - tA in fixed point (units of h 2^-32): the cell is the
   // high word, the fraction the low word.  s <= 0 gives depth 0 (cell 0,
-  // fraction 0), past the last entry the last value.
+  // fraction 0: s = 0 does so on the general path, so the test is the
+  // cell's sign), past the last entry the last value.
   const int cell = (int)(s >> 32);
-  const bool neg = s <= 0;
+  const bool neg = cell < 0;
   const bool past = cell >= C.n_table - 1;
   const int k = neg ? 0 : (past ? C.n_table - 2 : cell);
   const float f = neg ? 0.0f : __uint_as_float(((unsigned)s >> 9) | 0x3f800000u) - 1.0f;   // low word / 2^32
@@ -1159,13 +1160,14 @@ __device__ __forceinline__ float eval_pair(const RowConst& C, float fi, float4 A
 
   // beam-model table: T(d), c3_1..3(d) / K (K = Prof<PROF>::K, folded in
   // when the table was built); past the end, the last row.  g is clamped to
-  // [0, last] (a NaN depth maps to 0); its row is the truncation of
-  // min(g, last - 1), a conversion on the MUFU pipe (less busy than the FMA
-  // pipe and the ALU, which the same floor from 2^23 + g rounding would use),
-  // and w = 1 at g = last.
+  // [0, last] (a NaN depth maps to 0); its row is the truncation of g, a
+  // conversion on the MUFU pipe (less busy than the FMA pipe and the ALU,
+  // which the same floor from 2^23 + g rounding would use).  At g = last the
+  // row is the last one, whose difference to the next is 0, and w = 0: the
+  // last row exactly.
   const float g = fminf(fmaxf(d * C.lut_scale, 0.0f), C.lut_last);
-  const int kk = __float2int_rz(fminf(g, C.lut_last - 1.0f));   // g >= 0: the floor
-  const float w = g - small_int_to_float(kk);   // in [0, 1], exact
+  const int kk = __float2int_rz(g);   // g >= 0: the floor
+  const float w = g - small_int_to_float(kk);   // in [0, 1), exact
 #if DSC_LUT_SMEM
   const float4 L = TS ? slut[2 * kk] : __ldg(C.lut + 2 * kk);                 // row kk
   const float4 dL = TS ? slut[2 * kk + 1] : __ldg(C.lut + 2 * kk + 1);        // row kk+1 - row kk
