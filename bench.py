@@ -51,9 +51,9 @@ MUFU_PAIR = {0: {"rcp": 16, "ex2": 12}, 1: {"rcp": 4, "ex2": 12}, 2: {"rcp": 16,
 HBM_NOMINAL_GBS = 7900.0
 # DRAM bytes (read + write) of the evaluation kernel per candidate pair, from
 # one Nsight Compute capture of the kernel as built on the 2-field prostate
-# (27.85 M pairs, 3.7 MB read + 168.6 MB written); the full workload's
+# (27.85 M pairs, 2.8 MB read + 165.7 MB written); the full workload's
 # traffic is this times its pairs
-KEVAL_DRAM_BYTES_PER_PAIR = 6.186
+KEVAL_DRAM_BYTES_PER_PAIR = 6.051
 
 
 def parse():
