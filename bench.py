@@ -490,6 +490,10 @@ def run_ours(args):
     step_bytes = nnz * (4 + vsize) + 8 * (nrows + 1) + 4 * nbeams + h2d + 2 * 4 * table_entries
     step_gbs = step_bytes / (ms / 1e3) / 1e9
     eval_gbs = KEVAL_DRAM_BYTES_PER_PAIR * pairs / (eval_ms / 1e3) / 1e9
+    # the step's roofline: the largest of its arithmetic (FP32, MUFU) and
+    # algorithmic-byte times at the measured rates, against the step's time
+    step_hbm_ms = 1e3 * step_bytes / (hbm_meas * 1e9) if hbm_meas else 0.0
+    t_roof = max((fp32_ms, "fp32"), (mufu_ms, "mufu"), (step_hbm_ms, "hbm"))
     out = {
         "metric": "voxel-beamlet pairs/s",
         "value": value,
@@ -562,7 +566,12 @@ def run_ours(args):
                              "k_eval_frac_of_nominal": eval_gbs / HBM_NOMINAL_GBS,
                              "step_bytes_basis": "CSR (col + value + row pointers + beam scales) + density once "
                                                  "+ depth tables written and read"},
-                     "measured_alu": alu},
+                     "measured_alu": alu,
+                     "step": {"t_roof_ms": t_roof[0], "resource": t_roof[1], "frac": t_roof[0] / ms,
+                              "fp32_ms": fp32_ms, "mufu_ms": mufu_ms, "hbm_ms": step_hbm_ms,
+                              "basis": "T_roof = max(pairs x F_pair / measured FP32 rate, the pairs' MUFU operations "
+                                       "at the measured rates, the step's algorithmic bytes / measured HBM copy "
+                                       "bandwidth); frac = T_roof / the step's time"}},
         "clocks": clocks,
     }
     if cpu is not None:
