@@ -452,7 +452,8 @@ def test_repeat_is_bit_identical_and_graph_replay(dsc):
     dsc.dsc_destroy_geometry(g)
 
 
-def test_async_read_back_matches_and_outlives_release(dsc):
+@pytest.mark.parametrize("value_dtype", [0, 1], ids=["f32", "bf16"])
+def test_async_read_back_matches_and_outlives_release(dsc, value_dtype):
     """dsc_copy_csr_to_host_async gives the blocking read-back's CSR, also
     when the result is released before its copies run: the copies are held
     behind a long fill on another stream, the result is released, and new
@@ -461,7 +462,7 @@ def test_async_read_back_matches_and_outlives_release(dsc):
     import torch
     w = P.slabs_128(value_dtype=P.VALUE_F32)
     g = dsc.geometry_from_workload(w)
-    opts = dsc.compute_opts(w.tau, 0, w.h_frac)
+    opts = dsc.compute_opts(w.tau, value_dtype, w.h_frac)
     ref = dsc.dsc_compute_dij(g, opts)
     cref = dsc.HostCSR(ref)
     dsc.dsc_release_result(ref)
@@ -470,7 +471,7 @@ def test_async_read_back_matches_and_outlives_release(dsc):
     nnz, nrows, nbeams = int(v.nnz), int(v.nrows), int(v.nbeams)
     h_rp = torch.zeros(nrows + 1, dtype=torch.int64).pin_memory()
     h_col = torch.zeros(nnz, dtype=torch.int32).pin_memory()
-    h_val = torch.zeros(nnz, dtype=torch.float32).pin_memory()
+    h_val = torch.zeros(nnz, dtype=torch.int16 if value_dtype else torch.float32).pin_memory()
     h_sc = torch.zeros(nbeams, dtype=torch.float32).pin_memory()
     cs, other = torch.cuda.Stream(), torch.cuda.Stream()
     big = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
@@ -486,8 +487,12 @@ def test_async_read_back_matches_and_outlives_release(dsc):
     cs.synchronize()
     assert np.array_equal(h_rp.numpy(), cref.row_ptr)
     assert np.array_equal(h_col.numpy(), cref.col)
-    assert np.array_equal(h_val.numpy(), cref.val)
-    assert np.all(h_sc.numpy() == 1.0)                  # FP32 values carry no scale
+    if value_dtype:
+        assert np.array_equal(h_val.numpy().view(np.uint16), cref.raw)
+        assert np.array_equal(h_sc.numpy(), cref.beam_scale[:nbeams]) and np.all(h_sc.numpy() > 0)
+    else:
+        assert np.array_equal(h_val.numpy(), cref.val)
+        assert np.all(h_sc.numpy() == 1.0)              # FP32 values carry no scale
     for x in others:
         dsc.dsc_release_result(x)
     dsc.dsc_destroy_geometry(g)
