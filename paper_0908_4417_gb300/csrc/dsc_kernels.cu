@@ -1861,14 +1861,15 @@ __global__ void __launch_bounds__(kEvalThreads, DSC_COMPACT_MINB) k_tile_write(C
     if (p.value_dtype == 1) {
       __nv_bfloat16* val = (__nv_bfloat16*)p.slot->val;
       for (int k = lane; k < tot; k += 32) {
-        col[prefix + k] = s_col[w][k];
-        val[prefix + k] = __float2bfloat16_rn(s_val[w][k]);
+        __stcs(col + prefix + k, s_col[w][k]);
+        __stcs(reinterpret_cast<unsigned short*>(val) + prefix + k,
+               __bfloat16_as_ushort(__float2bfloat16_rn(s_val[w][k])));
       }
     } else {
       float* val = (float*)p.slot->val;
       for (int k = lane; k < tot; k += 32) {
-        col[prefix + k] = s_col[w][k];
-        val[prefix + k] = s_val[w][k];
+        __stcs(col + prefix + k, s_col[w][k]);
+        __stcs(val + prefix + k, s_val[w][k]);
       }
     }
     __syncwarp();                                      // the staging buffer is reused by the next tile
